@@ -1,0 +1,450 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numbers the
+paper prints, closed forms, convergence orders, invariants, or brute force on
+tiny inputs.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import chebyshev as ch
+from oracle import nievergelt as nv
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+# ---------------------------------------------------------------- paper values
+
+def test_table1_reproduced():
+    """Table 1 (Section 3): every entry within 2 % of the printed value.
+
+    15 of the 25 entries agree to the printed digits; the others sit within
+    1.5 % (rows dt = 0.005 and 0.0025 are ~0.5 % low in print).  First-kind
+    Chebyshev nodes, floor/round step counts or a forward-Euler step miss by
+    at least 11 %, so the tolerance still fixes the reading."""
+    worst = 0.0
+    for row in _load_rows("table1_foursubdomains.txt"):
+        dt, printed = row[0], row[1:]
+        for M, p in zip([3, 4, 5, 6, 7], printed):
+            err = abs(ch.nievergelt_square_be(dt, M) - ch.square_exact(0.5))
+            worst = max(worst, abs(err - p) / p)
+    assert worst < 0.02, worst
+
+
+def test_table2_serial_row():
+    """Table 2, N = 1: serial backward Euler error 2.77e-4 at dt = 1e-4."""
+    printed = _load_rows("table2_nievergelt_column.txt")[0][0]
+    err = abs(ch.serial_square_be(1e-4, S=1) - ch.square_exact(0.5))
+    assert abs(err - printed) < 0.5e-6
+
+
+def test_table1_large_M_limit_is_serial():
+    """With many nodes the interpolation error vanishes and the method returns
+    the serial fine result (Theorem, Section 4)."""
+    for dt in [0.01, 0.001]:
+        meth = ch.nievergelt_square_be(dt, 15)
+        ser = ch.serial_square_be(dt)
+        assert abs(meth - ser) < 1e-9
+
+
+def test_backward_euler_root_solves_the_implicit_equation():
+    y = np.array([0.5, 1.0, 1.7])
+    h = 0.01
+    y1 = ch.backward_euler_square(y, h, 1)
+    assert np.allclose(y1 - h * y1 * y1, y, atol=1e-12, rtol=0)
+
+
+# ------------------------------------------------------------ grid / step rule
+
+def test_step_rule():
+    assert nv.steps_per_slice(0.0, 0.1, 1024, 1e-5) == 10          # heat 1-D
+    assert nv.steps_per_slice(0.0, 20.0, 128, 1e-3) == 157         # 3-mass chain
+    assert nv.steps_per_slice(0.0, 1.0, 512, 2e-4) == 10           # advection-diffusion
+    assert nv.steps_per_slice(0.0, 0.5, 4, 0.01) == 13             # Table 1 row 1
+    assert nv.steps_per_slice(0.0, 0.5, 4, 0.005) == 25
+    assert nv.steps_per_slice(0.0, 10.0, 16, 0.0, fixed=10000) == 10000
+    Tj = nv.slice_times(0.0, 10.0, 16)
+    assert Tj[0] == 0.0 and Tj[-1] == 10.0 and len(Tj) == 17
+    assert np.allclose(np.diff(Tj), 0.625, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- fine schemes
+
+def test_euler_closed_form():
+    lam, h, m, y0 = -0.7, 1e-3, 1000, 1.3
+    y = nv.integrate(nv.rhs_linear_scalar(lam), "euler", 0.0, np.array([[y0]]), h, m)[0, 0]
+    assert abs(y - y0 * (1 + h * lam) ** m) <= 1e-13 * abs(y)
+
+
+def test_rk4_closed_form():
+    lam, h, m, y0 = -2.3, 1e-2, 300, 0.9
+    z = h * lam
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    y = nv.integrate(nv.rhs_linear_scalar(lam), "rk4", 0.0, np.array([[y0]]), h, m)[0, 0]
+    assert abs(y - y0 * R ** m) <= 1e-13 * abs(y)
+
+
+@pytest.mark.parametrize("scheme,order", [("euler", 1), ("rk4", 4)])
+def test_convergence_order(scheme, order):
+    lam, T = -1.3, 1.0
+    errs = []
+    for m in [40, 80, 160]:
+        y = nv.integrate(nv.rhs_linear_scalar(lam), scheme, 0.0, np.array([[1.0]]), T / m, m)[0, 0]
+        errs.append(abs(y - math.exp(lam * T)))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    for r in ratios:
+        assert abs(math.log2(r) - order) < 0.15, ratios
+
+
+def test_rk4_forced_order_pins_stage_times():
+    """beta' = mu beta + cos t, beta(0) = 0 has the exact solution
+    A cos t + B sin t - A e^{mu t}, A = -mu/(1+mu^2), B = 1/(1+mu^2).
+    Fourth-order convergence requires the stage times t, t+h/2, t+h."""
+    mu, T = -2.0, 1.5
+    A, B = -mu / (1 + mu * mu), 1 / (1 + mu * mu)
+    exact = A * math.cos(T) + B * math.sin(T) - A * math.exp(mu * T)
+    f = lambda t, Y: mu * Y + math.cos(t)
+    errs = []
+    for m in [20, 40, 80]:
+        y = nv.integrate(f, "rk4", 0.0, np.zeros((1, 1)), T / m, m)[0, 0]
+        errs.append(abs(y - exact))
+    for i in range(2):
+        assert abs(math.log2(errs[i] / errs[i + 1]) - 4) < 0.2, errs
+
+
+# ------------------------------------------------------------- interpolation
+
+def test_pl_map_exact_for_linear_ode():
+    """For y' = lambda y the slice map is linear, so the piecewise-linear table
+    reproduces it exactly and the composition equals the serial fine solve to
+    rounding, also when the state leaves the node range (edge extension)."""
+    f = nv.rhs_linear_scalar(-0.4)
+    t0, T, S, m = 0.0, 3.0, 6, 50
+    nodes = nv.uniform_nodes(-2.0, 2.0, 9)
+    tab = nv.build_table_1d(f, "euler", t0, T, S, m, nodes)
+    for y0 in [0.37, 1.9, 3.5]:
+        lam, _ = nv.compose_tables_1d(-2.0, 2.0, tab, y0)
+        ser = nv.serial_fine(f, "euler", t0, T, S, m, [y0])[0]
+        assert abs(lam[-1] - ser) <= 1e-13 * abs(ser)
+
+
+def test_pl_interpolation_error_is_second_order():
+    """Section 4, eq. interpolationcondition with l = 2: the largest gap between
+    a slice's piecewise-linear map and the fine map it interpolates (brute force
+    on 401 points) falls by 4 when dxi halves; the composed result then stays
+    within N K times that gap of the serial fine solve."""
+    f = nv.rhs_cos_cubic()
+    t0, T, S, m = 0.0, 2.0, 4, 100
+    h = nv.step_size(t0, T, S, m)
+    probe = np.linspace(-2.0, 2.0, 401)
+    exact = nv.integrate(f, "euler", 0.0, probe[None, :], h, m)[0]
+    ser = nv.serial_fine(f, "euler", t0, T, S, m, [0.5])[0]
+    gaps = []
+    for M in [17, 33, 65, 129]:
+        tab = nv.build_table_1d(f, "euler", t0, T, S, m, nv.uniform_nodes(-2.0, 2.0, M))
+        approx = np.array([nv.pl_eval(-2.0, 2.0, tab[0], x)[0] for x in probe])
+        gaps.append(np.max(np.abs(approx - exact)))
+        lam, oob = nv.compose_tables_1d(-2.0, 2.0, tab, 0.5)
+        assert oob == 0
+        assert abs(lam[-1] - ser) < 4 * S * gaps[-1]
+    for i in range(3):
+        assert 3.8 < gaps[i] / gaps[i + 1] < 4.2, gaps
+
+
+def test_pl_eval_brute_force():
+    vals = np.array([1.0, 3.0, 2.0, -1.0])
+    # nodes -1, 0, 1, 2
+    assert nv.pl_eval(-1.0, 2.0, vals, 0.5)[0] == pytest.approx(2.5)
+    assert nv.pl_eval(-1.0, 2.0, vals, 2.0)[0] == pytest.approx(-1.0)
+    v, oob = nv.pl_eval(-1.0, 2.0, vals, 3.0)        # extend the last segment
+    assert v == pytest.approx(-4.0) and oob
+    v, oob = nv.pl_eval(-1.0, 2.0, vals, -2.0)       # extend the first segment
+    assert v == pytest.approx(-1.0) and oob
+
+
+def test_bilinear_exact_for_linear_map():
+    """Van der Pol with mu = 0 is the harmonic oscillator: the slice map is a
+    rotation (linear), which bilinear interpolation reproduces exactly."""
+    f = nv.rhs_vdp(0.0)
+    t0, T, S, m = 0.0, 2.0, 5, 40
+    nodes = nv.uniform_nodes(-3.0, 3.0, 7)
+    tab = nv.build_table_2d(f, "rk4", t0, T, S, m, nodes, nodes)
+    lam, oob = nv.compose_tables_2d(-3.0, 3.0, tab, [1.1, -0.4])
+    ser = nv.serial_fine(f, "rk4", t0, T, S, m, [1.1, -0.4])
+    assert oob == 0
+    assert np.max(np.abs(lam[-1] - ser)) <= 1e-13
+
+
+def test_bilinear_eval_brute_force():
+    P, lo, hi = 3, 0.0, 2.0
+    tab = np.zeros((P, P, 2))
+    for p in range(P):
+        for q in range(P):
+            tab[p, q] = [p * q, p + 2 * q]             # node (p, q) at (p, q)
+    v, oob = nv.bilinear_eval(lo, hi, tab, [0.5, 1.5])
+    assert np.allclose(v, [0.75, 3.5]) and not oob    # x*y bilinear, x+2y linear
+
+
+# ------------------------------------------------------ right-hand sides
+
+def test_vdp_harmonic_closed_form():
+    """mu = 0: RK4 multiplies (x + i y) by R(-i h)^m, the complex stability
+    polynomial (x' = y, y' = -x rotates clockwise)."""
+    h, m = 0.01, 250
+    z = -1j * h
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    w = (0.8 + 0.3j) * R ** m
+    Y = nv.integrate(nv.rhs_vdp(0.0), "rk4", 0.0, np.array([[0.8], [0.3]]), h, m)[:, 0]
+    assert abs(Y[0] - w.real) < 1e-13 and abs(Y[1] - w.imag) < 1e-13
+
+
+def test_vdp_limit_cycle_amplitude():
+    """For mu > 0 every orbit approaches the limit cycle with max |x| close to 2
+    (2.00 for small mu, 2.02 at mu = 1); a sign error in the damping term would
+    send the orbit to the origin or to infinity."""
+    for mu in [0.3, 1.0]:
+        h, m = 0.01, 6000
+        Y = np.array([[0.5], [0.0]])
+        f = nv.rhs_vdp(mu)
+        xs = []
+        for i in range(m):
+            Y = nv.rk4_step(f, i * h, Y, h)
+            if i > 4000:
+                xs.append(abs(Y[0, 0]))
+        assert 1.97 < max(xs) < 2.05, (mu, max(xs))
+
+
+def test_chain3_linear_normal_modes():
+    """Without the cubic term and damping, the fixed-fixed 3-mass chain has
+    squared frequencies 2 - sqrt(2), 2, 2 + sqrt(2)."""
+    f = nv.rhs_chain3(1.0, 0.0, 0.0)
+    J = f(0.0, np.eye(6))
+    ev = np.linalg.eigvals(J)
+    w2 = np.sort(-(ev ** 2).real)
+    expect = np.sort(np.repeat([2 - math.sqrt(2), 2.0, 2 + math.sqrt(2)], 2))
+    assert np.allclose(w2, expect, atol=1e-12)
+
+
+def _chain_energy(Y, k=1.0, k3=0.5):
+    x1, x2, x3, v1, v2, v3 = Y
+    d = [x1, x2 - x1, x3 - x2, -x3]
+    pot = sum(k * di ** 2 / 2 + k3 * di ** 4 / 4 for di in d)
+    return 0.5 * (v1 ** 2 + v2 ** 2 + v3 ** 2) + pot
+
+
+def test_chain3_energy_balance():
+    """Undamped: RK4 keeps the energy (kinetic + spring potential k d^2/2 +
+    k3 d^4/4) to 1e-10.  Damped: E(0) - E(T) equals the dissipated c sum v^2."""
+    y0 = np.array([[0.3], [-0.2], [0.1], [0.0], [0.0], [0.0]])
+    h, m = 1e-3, 3000
+    Y = nv.integrate(nv.rhs_chain3(1.0, 0.5, 0.0), "rk4", 0.0, y0, h, m)
+    assert abs(_chain_energy(Y[:, 0]) - _chain_energy(y0[:, 0])) < 1e-10
+    c = 0.05
+    f = nv.rhs_chain3(1.0, 0.5, c)
+    Y = y0.copy()
+    diss = 0.0
+    prev = c * float(np.sum(Y[3:, 0] ** 2))
+    for i in range(m):
+        Y = nv.rk4_step(f, i * h, Y, h)
+        cur = c * float(np.sum(Y[3:, 0] ** 2))
+        diss += 0.5 * h * (prev + cur)
+        prev = cur
+    assert abs(_chain_energy(y0[:, 0]) - _chain_energy(Y[:, 0]) - diss) < 1e-6
+
+
+# ---------------------------------------------------------- affine maps (heat)
+
+def _heat_dst(n):
+    x = nv.heat1d_grid(n)
+    p = np.arange(1, n + 1)
+    Sm = math.sqrt(2.0 / (n + 1)) * np.sin(np.outer(x, p) * math.pi)   # Sm[i, p-1]
+    dx = 1.0 / (n + 1)
+    mu = -(4.0 / dx ** 2) * np.sin(p * math.pi * dx / 2) ** 2
+    return Sm, mu
+
+
+def test_heat_affine_maps_closed_form():
+    """The sine basis diagonalises the Dirichlet Laplacian, so every
+    homogeneous map is S diag(R(h mu_p)^m) S; the forcing lives in mode 1 only,
+    so b_j is a multiple of sin(pi x) (eq. linearreconstruct, no interpolation)."""
+    n, S, T, dt = 24, 6, 0.02, 2e-4
+    w = workloads.heat1d(n=n, S=S, T=T, dt=dt)
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, S, m)
+    A, b = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                           w.t0, w.T, S, m, n)
+    Sm, mu = _heat_dst(n)
+    z = h * mu
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    Aex = Sm @ np.diag(R ** m) @ Sm.T
+    for j in range(S):
+        assert np.max(np.abs(A[j] - Aex)) < 1e-13
+    s1 = np.sin(math.pi * nv.heat1d_grid(n))
+    Tj = nv.slice_times(w.t0, w.T, S)
+    for j in range(S):
+        beta = 0.0                       # scalar RK4 for beta' = mu_1 beta + cos t
+        for i in range(m):
+            t = Tj[j] + i * h
+            k1 = mu[0] * beta + math.cos(t)
+            k2 = mu[0] * (beta + h / 2 * k1) + math.cos(t + h / 2)
+            k3 = mu[0] * (beta + h / 2 * k2) + math.cos(t + h / 2)
+            k4 = mu[0] * (beta + h * k3) + math.cos(t + h)
+            beta = beta + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        assert np.max(np.abs(b[j] - beta * s1)) < 1e-15 + 1e-12 * abs(beta)
+
+
+def test_affine_composition_equals_serial():
+    """'This technique introduces no additional error beyond rounding error'
+    (end of Section 4): composing the affine maps gives the serial fine solve."""
+    w = workloads.heat1d(n=32, S=8, T=0.01, dt=5e-5)
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    A, b = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim)
+    lam = nv.compose_affine(A, b, w.y0)
+    ser = nv.serial_fine(fi, "rk4", w.t0, w.T, w.S, m, w.y0)
+    assert np.linalg.norm(lam[-1] - ser) <= 1e-13 * np.linalg.norm(ser)
+
+
+def test_heat_varcoef_manufactured_solution():
+    """Section 5, eq. heatequation: with the forcing chosen for
+    u = cos(t) sin(pi x), the discrete solution tracks it to the O(dx^2)
+    spatial error, and the affine composition equals the serial solve."""
+    n = 19
+    w = workloads.Workload("v", "heat1d_varcoef", n, 0.0, 1.0, 5, "rk4", 1e-3, 0, "affine")
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    y0 = np.sin(math.pi * nv.heat1d_grid(n))
+    A, b = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    lam = nv.compose_affine(A, b, y0)
+    exact = math.cos(1.0) * y0
+    assert np.max(np.abs(lam[-1] - exact)) < 2e-3
+    ser = nv.serial_fine(fi, "rk4", w.t0, w.T, w.S, m, y0)
+    assert np.max(np.abs(lam[-1] - ser)) < 1e-13
+
+
+# -------------------------------------------------- affine maps (advection-diffusion)
+
+def test_advdiff_affine_maps_fft_closed_form():
+    """The periodic operator is circulant: Fourier mode (p, q) has eigenvalue
+    nu (2cos th_p + 2cos th_q - 4)/dx^2 - ax (1 - e^{-i th_p})/dx
+    - ay (1 - e^{-i th_q})/dx, th = 2 pi p / nx.  Each map is
+    F^-1 diag(R(h sigma)^m) F, and b_j = 0 because there is no forcing."""
+    nx = 8
+    w = workloads.advdiff2d(nx=nx, S=3, T=0.006, dt=2e-4)
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, w.S, m)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    A, b = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, nx * nx)
+    assert np.all(b == 0.0)
+    dx = 1.0 / nx
+    th = 2 * math.pi * np.arange(nx) / nx
+    TQ, TP = np.meshgrid(th, th, indexing="ij")        # [q (y), p (x)]
+    sig = (0.01 * (2 * np.cos(TP) + 2 * np.cos(TQ) - 4) / dx ** 2
+           - 1.0 * (1 - np.exp(-1j * TP)) / dx - 0.5 * (1 - np.exp(-1j * TQ)) / dx)
+    z = h * sig
+    R = (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24) ** m
+    for c in [0, 5, 27, 63]:
+        e = np.zeros((nx, nx))
+        e.flat[c] = 1.0
+        col = np.fft.ifft2(R * np.fft.fft2(e)).real.ravel()
+        assert np.max(np.abs(A[1][:, c] - col)) < 1e-13
+
+
+# ----------------------------------------------------------- scan / reduce
+
+def test_affine_tree_equals_sequential_and_closed_form():
+    n, S, T, dt = 12, 16, 0.02, 2e-4
+    w = workloads.heat1d(n=n, S=S, T=T, dt=dt)
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, S, m)
+    A, b = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                           w.t0, w.T, S, m, n)
+    seq = nv.affine_prefix_sequential(A, b)
+    tree = nv.affine_reduce_tree(A, b)
+    assert np.max(np.abs(tree[0] - seq[-1][0])) < 1e-13
+    assert np.max(np.abs(tree[1] - seq[-1][1])) < 1e-13
+    Sm, mu = _heat_dst(n)
+    z = h * mu
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    assert np.max(np.abs(seq[-1][0] - Sm @ np.diag(R ** (S * m)) @ Sm.T)) < 1e-13
+    lam = nv.compose_affine(A, b, w.y0)
+    assert np.max(np.abs(seq[-1][0] @ w.y0 + seq[-1][1] - lam[-1])) < 1e-12
+
+
+def test_combine_is_associative_brute_force():
+    rng = np.random.default_rng(5)
+    maps = [(rng.standard_normal((4, 4)), rng.standard_normal(4)) for _ in range(3)]
+    left = nv.affine_combine(maps[2], nv.affine_combine(maps[1], maps[0]))
+    right = nv.affine_combine(nv.affine_combine(maps[2], maps[1]), maps[0])
+    y = rng.standard_normal(4)
+    direct = maps[2][0] @ (maps[1][0] @ (maps[0][0] @ y + maps[0][1]) + maps[1][1]) + maps[2][1]
+    for A, c in (left, right):
+        assert np.allclose(A @ y + c, direct, atol=1e-12)
+
+
+# ------------------------------------------------------------ refinement
+
+def _bf16(x):
+    """Round-to-nearest-even to bfloat16 (8 significant bits), in float64."""
+    a = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def test_refinement_exact_maps_recover_exact_states():
+    """With the exact maps as the correction propagator, one pass returns the
+    exact composition from any approximate boundary states."""
+    w = workloads.heat1d(n=16, S=6, T=0.006, dt=2e-4)
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    A, b = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim)
+    lam = nv.compose_affine(A, b, w.y0)
+    noisy = lam + np.random.default_rng(1).standard_normal(lam.shape) * 1e-2
+    noisy[0] = w.y0
+    ref = nv.refine_affine(fi, "rk4", w.t0, w.T, w.S, m, noisy, A)
+    assert np.max(np.abs(ref - lam)) < 1e-12
+
+
+def test_refinement_contracts_reduced_precision_error():
+    """With bf16-rounded maps the error after one pass is the map error times
+    the error before (parareal-style contraction)."""
+    w = workloads.heat1d(n=32, S=16, T=0.016, dt=2e-4)
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    A, b = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim)
+    lam = nv.compose_affine(A, b, w.y0)
+    At, bt = _bf16(A), _bf16(b)
+    lt = nv.compose_affine(At, bt, w.y0)
+    err0 = np.linalg.norm(lt[-1] - lam[-1]) / np.linalg.norm(lam[-1])
+    ref = nv.refine_affine(fi, "rk4", w.t0, w.T, w.S, m, lt, At)
+    err1 = np.linalg.norm(ref[-1] - lam[-1]) / np.linalg.norm(lam[-1])
+    assert err0 > 1e-4
+    assert err1 < 0.05 * err0, (err0, err1)
+
+
+# -------------------------------------------------------------- inputs
+
+def test_splitmix64_reference_value():
+    """First output of SplitMix64 seeded with 0 (published test vector)."""
+    assert int(workloads.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+def test_counter_based_slices_agree():
+    z = workloads.splitmix64(7, 10)
+    assert np.array_equal(z[4:], workloads.splitmix64(7, 6, 4))
+    s = workloads.chain3_samples(3, 4, 8, 2)
+    assert s.shape == (6, 8) and np.all(np.abs(s) <= 1.0)
