@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the propagator build + composition (one step = the whole path).
+
+Workload: linear 1-D heat equation u_t = u_xx + sin(pi x) cos t, n = 256
+interior points, t in [0, 0.1], S = 1024 slices, RK4 with dt = 1e-5 (m = 10
+steps per slice), exact affine slice maps from n + 1 = 257 basis solves,
+composed into the final state.  One step = build all maps (computation phase)
++ compose them from u0 (communication phase).
+
+Prints ONE JSON line.  The headline is the float64 method; the float32 and
+tensor-core variants and their errors are listed under "variants".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nvpit|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "propagator-build trajectory-steps/s + time-to-solution vs plain at fixed error"
+UNIT = "trajectory-steps/s"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+FP64_PEAK_NOMINAL = 1.25e12          # FLOP/s, FMA = 2 (GB300 FP64)
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9
+FLOP_PER_COMPONENT_STEP = 20         # Horner-form RK4 step of the 3-point stencil
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nvpit", choices=["nvpit", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="fp32,tf32_refine")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def traj_steps(w, m):
+    """Trajectory-steps of one build: every basis column of every slice, m steps."""
+    return w.S * (w.dim + 1) * m
+
+
+# --------------------------------------------------------------- oracle legs
+
+def oracle_sample(w, m, budget_s=10.0, min_slices=4):
+    """The FP64 oracle's map build timed on host cores over a bounded sample of
+    slices (as many as fit in budget_s, at least min_slices)."""
+    from oracle import nievergelt as nv
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    t0 = time.perf_counter()
+    done = 0
+    while done < w.S and (done < min_slices or time.perf_counter() - t0 < budget_s):
+        nv.build_affine_slice(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim, done)
+        done += 1
+    el = time.perf_counter() - t0
+    return done, el
+
+
+def oracle_serial(w, m):
+    from oracle import nievergelt as nv
+    t0 = time.perf_counter()
+    y = nv.serial_fine(nv.workload_rhs(w, True), "rk4", w.t0, w.T, w.S, m, w.y0)
+    return y, time.perf_counter() - t0
+
+
+def run_reference(args):
+    """--impl reference: the oracle itself, timed as it stands on host cores."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import workloads
+    from oracle import nievergelt as nv
+    w = workloads.heat1d()
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    per_step = 8                                   # slices per reference step (bounded sample)
+
+    def step(i):
+        for k in range(per_step):
+            nv.build_affine_slice(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim, (i * per_step + k) % w.S)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    el = time.perf_counter() - t0
+    units = per_step * (w.dim + 1) * m * args.steps
+    val = units / el
+    sample = f"{per_step} of {w.S} slices' maps per step (257 RK4 basis solves of n=256 each)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.dim, "S": w.S, "steps_per_slice": m},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU legs
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def time_variant(nvp, torch, w, prec, K, W, flush, stream):
+    """W untimed steps, then K timed steps; L2 flushed (untimed) before each.
+    Returns per-step build / compose / total device times in ms and the result."""
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    smp = nvp.samples("affine")
+    st = nvp.steps("rk4", w.dt, 0, prec)
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    yT = torch.empty_like(y0)
+    with torch.cuda.stream(stream):
+        maps = nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, stream=stream)
+        for _ in range(W):
+            nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, maps=maps, stream=stream)
+            nvp.compose(maps, y0, yT, stream=stream)
+        nvp.maps_check(maps, stream=stream)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, maps=maps, stream=stream)
+            ev[k][1].record(stream)
+            nvp.compose(maps, y0, yT, stream=stream)
+            ev[k][2].record(stream)
+        stream.synchronize()
+    nvp.maps_check(maps, stream=stream)
+    build = [e[0].elapsed_time(e[1]) for e in ev]
+    comp = [e[1].elapsed_time(e[2]) for e in ev]
+    tot = [a + b for a, b in zip(build, comp)]
+    m = nvp.maps_info(maps).steps_per_slice
+    maps.destroy()
+    return {"build_ms": build, "compose_ms": comp, "step_ms": tot, "yT": yT.cpu().numpy(), "m": m}
+
+
+def time_e2e(nvp, torch, w, K, W, stream):
+    """End to end through nv_solve (allocates, builds, composes, frees) with
+    pinned host buffers copied in and out every step."""
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    smp = nvp.samples("affine")
+    st = nvp.steps("rk4", w.dt, 0, "fp64")
+    y0_h = torch.tensor(w.y0, dtype=torch.float64).pin_memory()
+    yT_h = torch.empty_like(y0_h).pin_memory()
+    y0_d = torch.empty(w.dim, dtype=torch.float64, device="cuda")
+    yT_d = torch.empty_like(y0_d)
+    times = []
+    with torch.cuda.stream(stream):
+        for k in range(W + K):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            y0_d.copy_(y0_h, non_blocking=True)
+            nvp.solve(r, w.t0, w.T, w.S, smp, st, y0_d, yT_d, stream=stream)
+            yT_h.copy_(yT_d, non_blocking=True)
+            stream.synchronize()
+            if k >= W:
+                times.append(time.perf_counter() - t0)
+    return times, y0_h.numel() * 8, yT_h.numel() * 8
+
+
+def gpu_peak_probe(torch):
+    """Library FP64/FP32 GEMM rates on this GPU (context for the ALU roofline)."""
+    out = {}
+    for name, dt, n in (("fp64_dgemm_tflops", torch.float64, 4096), ("fp32_sgemm_tflops", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        if dt == torch.float32:
+            prev = torch.backends.cuda.matmul.allow_tf32
+            torch.backends.cuda.matmul.allow_tf32 = False
+        for _ in range(2):
+            torch.matmul(a, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 2 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        if dt == torch.float32:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1304_6514_gb300 as nvp
+    import workloads
+
+    w = workloads.heat1d()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, max(3, args.warmup)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: float64 plain method
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    wall0 = time.perf_counter()
+    res = time_variant(nvp, torch, w, "fp64", K, W, flush, stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    m = res["m"]
+    units = traj_steps(w, m)
+    dev_s = sum(res["step_ms"]) * 1e-3
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = units * K * world / dev_s
+    build_s = statistics.mean(res["build_ms"]) * 1e-3
+    flop = FLOP_PER_COMPONENT_STEP * units * w.dim
+    achieved = flop / build_s
+
+    # ---- variants
+    variants = {"fp64": {"ms_per_step": statistics.mean(res["step_ms"]),
+                         "build_ms": statistics.mean(res["build_ms"]),
+                         "compose_ms": statistics.mean(res["compose_ms"]),
+                         "traj_steps_per_s": units / (statistics.mean(res["step_ms"]) * 1e-3),
+                         "build_tflops": achieved / 1e12,
+                         "build_frac_of_fp64_nominal": achieved / FP64_PEAK_NOMINAL}}
+    results = {"fp64": res["yT"]}
+    for v in [x for x in args.variants.split(",") if x]:
+        try:
+            rv = time_variant(nvp, torch, w, v, K, W, flush, stream)
+        except nvp.NvError as e:
+            variants[v] = {"unavailable": str(e)}
+            continue
+        results[v] = rv["yT"]
+        bs = statistics.mean(rv["build_ms"]) * 1e-3
+        variants[v] = {"ms_per_step": statistics.mean(rv["step_ms"]),
+                       "build_ms": statistics.mean(rv["build_ms"]),
+                       "compose_ms": statistics.mean(rv["compose_ms"]),
+                       "traj_steps_per_s": units / (statistics.mean(rv["step_ms"]) * 1e-3),
+                       "build_tflops": flop / bs / 1e12,
+                       "build_frac_of_fp32_nominal": flop / bs / FP32_PEAK_NOMINAL,
+                       "speedup_vs_fp64_plain": statistics.mean(res["step_ms"]) / statistics.mean(rv["step_ms"])}
+        ref = results["fp64"]
+        variants[v]["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(rv["yT"] - ref) / np.linalg.norm(ref))
+
+    # ---- end to end through the one-call API with host buffers
+    e2e_t, h2d, d2h = time_e2e(nvp, torch, w, max(3, K // 4), 2, stream)
+    e2e_val = units / statistics.mean(e2e_t)
+
+    peaks_probe = gpu_peak_probe(torch)
+    peaks, peaks_src = read_peaks()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": statistics.mean(res["step_ms"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.dim, "S": w.S, "steps_per_slice": m,
+                   "basis_columns_per_slice": w.dim + 1, "t": [w.t0, w.T], "dt": w.dt,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_solution_ms": statistics.mean(res["step_ms"]),
+        "wall_s_timed_region": wall,
+        "roofline": {"bound": "alu", "kernel": "heat_affine_build_kernel<double,8>",
+                     "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)",
+                     "flop_per_launch": flop},
+        "gpu_launches": 2 * K,
+        "clocks": clocks,
+        "variants": variants,
+        "gpu_library_rates": peaks_probe,
+        "peaks_file": peaks_src,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "nv_solve (allocates, builds, composes, frees) + pinned host copies",
+                "ms_per_step": statistics.mean(e2e_t) * 1e3},
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, el = oracle_sample(w, m)
+        serial, serial_s = oracle_serial(w, m)
+        line["cpu_baseline"] = {
+            "value": done * (w.dim + 1) * m / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle map build of {done} of {w.S} slices ({el:.1f} s); "
+                      f"serial fine solve of the whole problem {serial_s:.2f} s"}
+        line["rel_err_vs_oracle"] = {k: float(np.linalg.norm(v - serial) / np.linalg.norm(serial))
+                                     for k, v in results.items()}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

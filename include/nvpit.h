@@ -1,0 +1,211 @@
+/*
+ * nvpit.h - Nievergelt parallel-in-time propagators on GB300 (sm_103a).
+ *
+ * C ABI of the library libnvpit.so.  The calls follow the paper's statement of
+ * the problem (Barker, "A minimal communication approach to parallel time
+ * integration", Figure "pseudocode"): given an initial value problem
+ * y' = f(t, y), a sample Xi_h of the initial value space, a final time T and a
+ * number of time slices S,
+ *   - the computation phase builds, for every slice [T_{j-1}, T_j], a map
+ *     phi^j from initial to final states (nv_build_propagators), and
+ *   - the communication phase composes the maps, lambda_j = phi^j(lambda_{j-1})
+ *     (nv_compose).
+ *
+ * Conventions shared by every call
+ *   - Pointers named *_dev are CUDA device pointers on the current device;
+ *     everything else is host memory.  The caller owns every buffer it passes.
+ *   - Maps (nv_maps) are library-owned device memory, created by
+ *     nv_build_propagators and released by nv_maps_destroy.
+ *   - Every call is asynchronous on the CUDA stream given as `stream`
+ *     (a cudaStream_t; NULL = legacy default stream) unless it says otherwise.
+ *   - No C++ exception and no exit() crosses this ABI.  Every call returns an
+ *     nv_status; nv_last_error() gives the message of the calling thread's
+ *     last failure.  CUDA launch/runtime errors map to NV_ECUDA.
+ *   - Errors found on the device (a bounded wait that gave up, an evaluation
+ *     outside Xi under NV_OOB_ERROR) are recorded in a device status word of the
+ *     maps object and returned by nv_maps_check after it synchronises.
+ *   - Time slices: T_j = t0 + j (T - t0)/S (Figure "pseudocode", Initialize).
+ *     Fine steps per slice: m = steps_per_slice if > 0, else ceil(H/dt) with
+ *     H = (T - t0)/S (a guard of 1e-9 keeps integer ratios exact), step size
+ *     h = H/m, step i of slice j starts at T_{j-1} + i h.
+ */
+#ifndef NVPIT_H
+#define NVPIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NVPIT_VERSION 1
+
+typedef enum {
+  NV_OK = 0,
+  NV_EINVAL = 1,    /* an argument is invalid; nothing was launched        */
+  NV_ENOMEM = 2,    /* a device allocation failed                           */
+  NV_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed          */
+  NV_EDOMAIN = 4,   /* an evaluation left Xi under NV_OOB_ERROR             */
+  NV_EBADMAP = 5,   /* maps missing, of the wrong kind, or holding NaN/Inf  */
+  NV_ETIMEOUT = 6,  /* a bounded device-side wait gave up                   */
+  NV_ENOTSUP = 7    /* valid request this build does not implement          */
+} nv_status;
+
+/* Right-hand sides f(t, y) compiled into the library.  `dim` must match. */
+typedef enum {
+  NV_RHS_LINEAR_SCALAR = 0,   /* y' = p0 y;                         dim 1, params {p0}            */
+  NV_RHS_SQUARE = 1,          /* y' = y^2 (Section 3, eq. scalarmodel); dim 1                   */
+  NV_RHS_COS_CUBIC = 2,       /* y' = cos(t) y - y^3;               dim 1                         */
+  NV_RHS_HEAT1D = 3,          /* u_t = k u_xx + a sin(pi x) cos t, Dirichlet 0, central
+                                 differences, x_i = i/(n+1);        dim n, params {k, a} (1, 1)  */
+  NV_RHS_VDP = 4,             /* x' = y, y' = mu (1 - x^2) y - x;   dim 2, params {mu}            */
+  NV_RHS_CHAIN3 = 5,          /* wall-m1-m2-m3-wall, tension k d + k3 d^3, damping c;
+                                 state (x1,x2,x3,v1,v2,v3);         dim 6, params {k, k3, c}      */
+  NV_RHS_ADVDIFF2D = 6,       /* u_t = nu lap5(u) - (ax D-x u + ay D-y u), periodic nx*nx grid,
+                                 spacing 1/nx, index iy*nx+ix;      dim nx*nx, params {nu, ax, ay} */
+  NV_RHS_HEAT1D_VARCOEF = 7   /* Section 5, eq. heatequation: u_t = (1 + sin(t)/4) u_xx + b(t,x),
+                                 b making cos(t) sin(pi x) exact;   dim n                         */
+} nv_rhs_kind;
+
+typedef struct {
+  int32_t kind;            /* nv_rhs_kind                                   */
+  int32_t dim;             /* state dimension d                             */
+  const double* params;    /* host array of nparams values (may be NULL)    */
+  int32_t nparams;
+} nv_rhs;
+
+typedef enum { NV_EULER = 0, NV_RK4 = 1 } nv_scheme;
+
+typedef enum {
+  NV_MAP_PL1D = 0,         /* d = 1: piecewise-linear table on M equispaced nodes      */
+  NV_MAP_BILINEAR2D = 1,   /* d = 2: bilinear table on a P x P equispaced grid         */
+  NV_MAP_AFFINE = 2        /* linear systems: y_end = A_j y0 + b_j from d+1 basis solves */
+} nv_map_kind;
+
+typedef enum {
+  NV_FP64 = 0,             /* integrate and store in float64                           */
+  NV_FP32 = 1,             /* integrate and store in float32                           */
+  NV_TF32_REFINE = 2       /* affine only: float32 maps, composition on tcgen05 tensor
+                              cores in TF32 with float32 accumulation, then one float64
+                              residual-correction pass                                  */
+} nv_precision;
+
+typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;
+
+/* Xi_h (Section 3: "sample points inside Xi to get a discrete set Xi_h").
+ * PL1D: nodes lo[0] + k (hi[0]-lo[0])/(per_dim-1), k = 0..per_dim-1.
+ * BILINEAR2D: grid (lo[0] + p dx, lo[1] + q dy), p, q = 0..per_dim-1.
+ * AFFINE: the d+1 basis {0 (with forcing), e_1..e_d (homogeneous)} of eq.
+ *   linearreconstruct; per_dim, lo, hi are ignored.
+ * Evaluation outside [lo, hi] extends the edge segment/cell (EXTRAPOLATE, and
+ * is counted) or additionally records NV_EDOMAIN (ERROR). */
+typedef struct {
+  int32_t map;             /* nv_map_kind     */
+  int32_t per_dim;
+  double lo[2];
+  double hi[2];
+  int32_t oob_policy;      /* nv_oob_policy   */
+} nv_samples;
+
+typedef struct {
+  int32_t scheme;          /* nv_scheme                              */
+  double dt;               /* target fine step (used when steps == 0) */
+  int64_t steps_per_slice; /* m; 0 => ceil(H/dt)                      */
+  int32_t prec;            /* nv_precision                           */
+} nv_steps;
+
+typedef struct nv_maps nv_maps;   /* opaque, library-owned */
+
+/* Layout description of built maps (nv_maps_info).
+ *   PL1D        data[j*M + k]                        (value from node k, slice j)
+ *   BILINEAR2D  data[((j*P + q)*P + p)*2 + c]        (component c from node (p, q))
+ *   AFFINE      data[j*d*(d+1) + col*d + i]          column-major d x (d+1) per slice:
+ *               col 0 = b_j, col c >= 1 = A_j e_c  (eq. linearreconstruct)
+ * Element type: double for NV_FP64, float otherwise. */
+typedef struct {
+  int32_t map, prec, scheme, S, dim, per_dim;
+  int64_t steps_per_slice;
+  double h;                /* fine step size                 */
+  int64_t elems_per_slice;
+  int64_t bytes;           /* total bytes of map data        */
+  int32_t elem_bytes;      /* 8 (double) or 4 (float)        */
+} nv_maps_desc;
+
+/* Computation phase (Figure "pseudocode"; eqs. lineardiscrete and
+ * linearreconstruct for NV_MAP_AFFINE).  For every slice j and every sample
+ * xi_k, integrates the fine scheme over [T_{j-1}, T_j] from xi_k and stores
+ * the final states as the slice map.
+ * If *maps is non-NULL it must come from an earlier call with the same sizes,
+ * map kind and precision; its storage is reused and nothing is allocated.
+ * Otherwise a new object is allocated and returned in *maps.
+ * Returns NV_EINVAL for inconsistent arguments (nothing launched), NV_ENOMEM,
+ * NV_ENOTSUP for map/rhs combinations not built, NV_ECUDA on launch failure. */
+nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T, int32_t S,
+                               const nv_samples* samples, const nv_steps* steps,
+                               nv_maps** maps, void* stream);
+
+/* Communication phase (Figure "pseudocode"): lambda_0 = y0,
+ * lambda_j = phi^j(lambda_{j-1}), j = 1..S, evaluated in float64.
+ *   y0_dev       d doubles (input)
+ *   yT_dev       d doubles (output, lambda_S)
+ *   lambdas_dev  (S+1) x d doubles (output, may be NULL): every boundary state.
+ * Tables: one sequential chain of S lookups.  AFFINE NV_FP64 / NV_FP32: a
+ * chain of S matrix-vector products on all SMs (cooperative launch, bounded
+ * grid barrier; NV_ETIMEOUT is recorded if a barrier wait gives up).
+ * AFFINE NV_TF32_REFINE: blocked scan of the affine maps on tcgen05 tensor
+ * cores, then one float64 residual-correction pass with float64 fine solves
+ * from the approximate boundary states.  Buffers must not overlap. */
+nv_status nv_compose(const nv_maps* maps, const double* y0_dev, double* yT_dev,
+                     double* lambdas_dev, void* stream);
+
+/* Build followed by compose (Figure "pseudocode" end to end).  Allocates and
+ * frees its own maps; y0_dev / yT_dev as in nv_compose.  Synchronises the
+ * stream before freeing, so it returns after the result is written. */
+nv_status nv_solve(const nv_rhs* rhs, double t0, double T, int32_t S,
+                   const nv_samples* samples, const nv_steps* steps,
+                   const double* y0_dev, double* yT_dev, void* stream);
+
+/* Serial fine solve over all slices from y0 with the same step size and step
+ * times as the slices: the "plain" reference the method is judged against
+ * (Section 4, Theorem).  One thread per component group; latency-bound. */
+nv_status nv_serial_fine(const nv_rhs* rhs, double t0, double T, int32_t S,
+                         const nv_steps* steps, const double* y0_dev, double* yT_dev,
+                         void* stream);
+
+/* Releases maps (NULL is accepted).  Synchronises the device first. */
+nv_status nv_maps_destroy(nv_maps* maps);
+
+/* Describes built maps (host-side, no synchronisation). */
+nv_status nv_maps_info(const nv_maps* maps, nv_maps_desc* out);
+
+/* Copies the map data (nv_maps_desc.bytes bytes, layout above) to dst, a host
+ * or device pointer, asynchronously on `stream`. */
+nv_status nv_maps_copy_out(const nv_maps* maps, void* dst, int64_t bytes, void* stream);
+
+/* Synchronises `stream`, then returns the device status recorded by this
+ * maps object's kernels (NV_OK, NV_EDOMAIN, NV_ETIMEOUT) and, if oob_count is
+ * non-NULL, the number of evaluations outside Xi since the last compose. */
+nv_status nv_maps_check(const nv_maps* maps, void* stream, int64_t* oob_count);
+
+/* Message of the calling thread's last failure ("" if none).  Valid until the
+ * thread's next failing call. */
+const char* nv_last_error(void);
+
+/* NVPIT_VERSION of the built library. */
+int32_t nv_version(void);
+
+/* Launch-shape tunables, process-wide (host only; set by the autotuner).
+ *   key 0: threads per CTA of the table build (32..256, default 64)
+ *   key 1: rows of each chain product owned by one CTA (default 16)
+ *   key 2: warps per CTA of the affine build (default 8)
+ * A value <= 0 restores the default.  Returns NV_EINVAL for an unknown key. */
+nv_status nv_tune_set(int32_t key, int32_t value);
+
+/* Fine steps per slice and step size by the rule stated above (host only). */
+nv_status nv_plan_steps(double t0, double T, int32_t S, double dt, int64_t steps_per_slice,
+                        int64_t* m, double* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NVPIT_H */

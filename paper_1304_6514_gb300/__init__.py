@@ -1,0 +1,246 @@
+"""Python binding of libnvpit.so: Nievergelt parallel-in-time propagators on GB300.
+
+Argument marshalling only.  Every step of the method runs in the CUDA kernels
+behind the C ABI declared in include/nvpit.h; the functions here have the same
+names without the ``nv_`` prefix.  Device buffers are torch CUDA tensors
+(float64, contiguous); the stream defaults to torch's current stream.
+
+The library must have been built (``paper_1304_6514_gb300._build.build()``);
+importing a function that needs it raises if it is missing.  There is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnvpit.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "nvpit.h")
+
+# enums (include/nvpit.h)
+NV_OK, NV_EINVAL, NV_ENOMEM, NV_ECUDA, NV_EDOMAIN, NV_EBADMAP, NV_ETIMEOUT, NV_ENOTSUP = range(8)
+RHS = {"linear_scalar": 0, "square": 1, "cos_cubic": 2, "heat1d": 3, "vdp": 4, "chain3": 5,
+       "advdiff2d": 6, "heat1d_varcoef": 7}
+SCHEME = {"euler": 0, "rk4": 1}
+MAP = {"pl1d": 0, "bilinear2d": 1, "affine": 2}
+PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2}
+OOB = {"extrapolate": 0, "error": 1}
+
+
+class NvRhs(Structure):
+    _fields_ = [("kind", c_int32), ("dim", c_int32), ("params", POINTER(c_double)),
+                ("nparams", c_int32)]
+
+
+class NvSamples(Structure):
+    _fields_ = [("map", c_int32), ("per_dim", c_int32), ("lo", c_double * 2),
+                ("hi", c_double * 2), ("oob_policy", c_int32)]
+
+
+class NvSteps(Structure):
+    _fields_ = [("scheme", c_int32), ("dt", c_double), ("steps_per_slice", c_int64),
+                ("prec", c_int32)]
+
+
+class NvMapsDesc(Structure):
+    _fields_ = [("map", c_int32), ("prec", c_int32), ("scheme", c_int32), ("S", c_int32),
+                ("dim", c_int32), ("per_dim", c_int32), ("steps_per_slice", c_int64),
+                ("h", c_double), ("elems_per_slice", c_int64), ("bytes", c_int64),
+                ("elem_bytes", c_int32)]
+
+
+class NvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"nvpit status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnvpit.so and declare its prototypes.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1304_6514_gb300._build.build()"
+                           " (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "nv_build_propagators": [POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSamples),
+                                 POINTER(NvSteps), POINTER(c_void_p), P],
+        "nv_compose": [P, P, P, P, P],
+        "nv_solve": [POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSamples),
+                     POINTER(NvSteps), P, P, P],
+        "nv_serial_fine": [POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), P, P, P],
+        "nv_maps_destroy": [P],
+        "nv_maps_info": [P, POINTER(NvMapsDesc)],
+        "nv_maps_copy_out": [P, P, c_int64, P],
+        "nv_maps_check": [P, P, POINTER(c_int64)],
+        "nv_tune_set": [c_int32, c_int32],
+        "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
+                          POINTER(c_double)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = c_int32
+    lib.nv_last_error.argtypes = []
+    lib.nv_last_error.restype = ctypes.c_char_p
+    lib.nv_version.argtypes = []
+    lib.nv_version.restype = c_int32
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER_PATH) -> list[str]:
+    """Names of the functions include/nvpit.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nv_[a-z_0-9]+)\s*\(", text)))
+
+
+def last_error() -> str:
+    return load_library().nv_last_error().decode()
+
+
+def _check(status: int):
+    if status != NV_OK:
+        raise NvError(status, last_error())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("device buffers must be contiguous float64 CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ------------------------------------------------------------------ descriptors
+
+def rhs(kind: str, dim: int, params=()):
+    arr = (c_double * max(1, len(params)))(*params)
+    r = NvRhs(RHS[kind], dim, arr if params else None, len(params))
+    r._keep = arr
+    return r
+
+
+def samples(map: str, per_dim: int = 0, lo=(0.0, 0.0), hi=(0.0, 0.0), oob: str = "extrapolate"):
+    lo = tuple(lo) + (0.0,) * (2 - len(lo))
+    hi = tuple(hi) + (0.0,) * (2 - len(hi))
+    return NvSamples(MAP[map], per_dim, (c_double * 2)(*lo), (c_double * 2)(*hi), OOB[oob])
+
+
+def steps(scheme: str, dt: float = 0.0, steps_per_slice: int = 0, prec: str = "fp64"):
+    return NvSteps(SCHEME[scheme], dt, steps_per_slice, PREC[prec])
+
+
+class Maps:
+    """Library-owned slice maps (nv_maps); freed by destroy() or garbage collection."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def info(self) -> NvMapsDesc:
+        return maps_info(self)
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(load_library().nv_maps_destroy(h))
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.nv_maps_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ entry points
+
+def build_propagators(rhs_, t0, T, S, samples_, steps_, maps: Maps | None = None, stream=None) -> Maps:
+    """nv_build_propagators: the computation phase (Figure "pseudocode")."""
+    lib = load_library()
+    h = c_void_p(maps.handle if maps is not None else None)
+    _check(lib.nv_build_propagators(byref(rhs_), t0, T, S, byref(samples_), byref(steps_),
+                                    byref(h), _stream(stream)))
+    if maps is not None:
+        return maps
+    return Maps(h.value)
+
+
+def compose(maps: Maps, y0, yT, lambdas=None, stream=None):
+    """nv_compose: the communication phase (Figure "pseudocode")."""
+    _check(load_library().nv_compose(maps.handle, _ptr(y0), _ptr(yT), _ptr(lambdas), _stream(stream)))
+
+
+def solve(rhs_, t0, T, S, samples_, steps_, y0, yT, stream=None):
+    _check(load_library().nv_solve(byref(rhs_), t0, T, S, byref(samples_), byref(steps_), _ptr(y0),
+                                   _ptr(yT), _stream(stream)))
+
+
+def serial_fine(rhs_, t0, T, S, steps_, y0, yT, stream=None):
+    _check(load_library().nv_serial_fine(byref(rhs_), t0, T, S, byref(steps_), _ptr(y0), _ptr(yT),
+                                         _stream(stream)))
+
+
+def maps_info(maps: Maps) -> NvMapsDesc:
+    d = NvMapsDesc()
+    _check(load_library().nv_maps_info(maps.handle, byref(d)))
+    return d
+
+
+def maps_copy_out(maps: Maps, dst, stream=None):
+    """Copy the map data into a torch tensor (host or device) of at least info().bytes bytes."""
+    nbytes = dst.numel() * dst.element_size()
+    _check(load_library().nv_maps_copy_out(maps.handle, dst.data_ptr(), min(nbytes, maps_info(maps).bytes),
+                                           _stream(stream)))
+
+
+def maps_check(maps: Maps, stream=None) -> int:
+    """Synchronise and raise NvError on a recorded device status; returns the out-of-range count."""
+    n = c_int64(0)
+    _check(load_library().nv_maps_check(maps.handle, _stream(stream), byref(n)))
+    return n.value
+
+
+def maps_data(maps: Maps):
+    """The map data as a new CUDA tensor (float64 or float32, flat)."""
+    import torch
+    d = maps_info(maps)
+    dt = torch.float64 if d.elem_bytes == 8 else torch.float32
+    out = torch.empty(d.bytes // d.elem_bytes, dtype=dt, device="cuda")
+    _check(load_library().nv_maps_copy_out(maps.handle, out.data_ptr(), d.bytes, _stream(None)))
+    return out
+
+
+def plan_steps(t0, T, S, dt=0.0, steps_per_slice=0):
+    m, h = c_int64(0), c_double(0.0)
+    _check(load_library().nv_plan_steps(t0, T, S, dt, steps_per_slice, byref(m), byref(h)))
+    return m.value, h.value
+
+
+def tune_set(key: int, value: int):
+    _check(load_library().nv_tune_set(key, value))
+
+
+def version() -> int:
+    return load_library().nv_version()

@@ -1,0 +1,306 @@
+// Exact affine slice maps for linear systems (eqs. lineardiscrete and
+// linearreconstruct): per slice j, one solve from 0 with the forcing on gives
+// b_j and d homogeneous solves from e_c give the columns of A_j.
+//
+// Heat equation kernels: one warp integrates one basis column.  Lane l holds
+// rows l*R .. l*R+R-1 of the d-vector in registers (R = ceil(d/32)); the
+// three-point stencil reaches the neighbouring lanes with two shuffles per
+// stage.  No shared or global memory is touched until the column is written.
+//
+// Time-invariant homogeneous columns use the Horner form of the RK4 step,
+// y <- y + hL(y + hL/2(y + hL/3(y + hL/4 y))): for y' = L y with constant L
+// this is the classical RK4 step exactly (both equal the degree-4 Taylor
+// polynomial of hL applied to y), with 3 instead of 5 float operations per
+// element and stage.  The forcing column and time-dependent operators take
+// the four RK4 stages literally.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nvpit {
+
+struct HeatArgs {
+  void* out;
+  int n, S, rows_valid_full;
+  int64_t m;
+  double t0, H, h;
+  double kappa, amp;     // NV_RHS_HEAT1D parameters
+  int varcoef;           // NV_RHS_HEAT1D_VARCOEF
+};
+
+// Neighbour values of a lane-blocked vector: left of row lane*R, right of row
+// lane*R+R-1 (zero at the Dirichlet boundary and past the last row).
+template <int R, typename T>
+__device__ __forceinline__ void halos(const T* v, int lane, int n, T& left, T& right) {
+  left = __shfl_up_sync(0xffffffffu, v[R - 1], 1);
+  right = __shfl_down_sync(0xffffffffu, v[0], 1);
+  if (lane == 0) left = (T)0;
+  if (lane == 31 || (lane + 1) * R >= n) right = (T)0;
+}
+
+// One Horner-form RK4 step of y' = cdx * lap(y), lap the [1,-2,1] stencil.
+template <int R, typename T>
+__device__ __forceinline__ void heat_horner_step(T* y, T* v, T cdx, T h, int lane, int n) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = y[i];
+#pragma unroll
+  for (int kk = 4; kk >= 1; --kk) {
+    const T ck = (h / (T)kk) * cdx;
+    T prev, right;
+    halos<R>(v, lane, n, prev, right);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const T cur = v[i];
+      const T nxt = (i + 1 < R) ? v[i + 1] : right;
+      T s = prev + nxt;
+      s = fma((T)-2, cur, s);
+      v[i] = fma(ck, s, y[i]);
+      prev = cur;
+    }
+    if ((lane + 1) * R > n) {  // padding rows stay zero
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (lane * R + i >= n) v[i] = (T)0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) y[i] = v[i];
+}
+
+// Right-hand side f(t, z) = a(t) cdx lap(z) + g(t) sx at one stage, folded into
+// the stage updates of the literal RK4 step.
+template <int R, typename T>
+__device__ __forceinline__ void heat_stage(const T* y, T* z, T* acc, T a_cdx, T g, const T* sx,
+                                           bool forced, T zc, T accw, bool first, int lane,
+                                           int n) {
+  T prev, right;
+  halos<R>(z, lane, n, prev, right);
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const T cur = z[i];
+    const T nxt = (i + 1 < R) ? z[i + 1] : right;
+    T s = prev + nxt;
+    s = fma((T)-2, cur, s);
+    T k = a_cdx * s;
+    if (forced) k = fma(g, sx[i], k);
+    acc[i] = first ? k : fma(accw, k, acc[i]);
+    z[i] = fma(zc, k, y[i]);
+    prev = cur;
+  }
+  if ((lane + 1) * R > n) {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (lane * R + i >= n) z[i] = (T)0;
+  }
+}
+
+__device__ __forceinline__ double heat_a(int varcoef, double t) {
+  return varcoef ? 1.0 + 0.25 * sin(t) : 1.0;
+}
+// forcing amplitude g(t) multiplying sin(pi x)
+__device__ __forceinline__ double heat_g(int varcoef, double amp, double t) {
+  if (!varcoef) return amp * cos(t);
+  const double a = 1.0 + 0.25 * sin(t);
+  return -sin(t) + a * (M_PI * M_PI) * cos(t);
+}
+
+// Literal RK4 step (stage times t, t+h/2, t+h) for the heat right-hand side.
+template <int R, typename T>
+__device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double t, double h, T cdx,
+                                              const HeatArgs& a, const T* sx, bool forced,
+                                              int lane, int n) {
+  const T hh = (T)(0.5 * h), hT = (T)h;
+  const double th = __dadd_rn(t, 0.5 * h), t1 = __dadd_rn(t, h);
+  T g0 = 0, gh = 0, g1 = 0;
+  if (forced) {
+    g0 = (T)heat_g(a.varcoef, a.amp, t);
+    gh = (T)heat_g(a.varcoef, a.amp, th);
+    g1 = (T)heat_g(a.varcoef, a.amp, t1);
+  }
+  const T a0 = (T)heat_a(a.varcoef, t) * cdx, ah = (T)heat_a(a.varcoef, th) * cdx;
+  const T a1 = (T)heat_a(a.varcoef, t1) * cdx;
+#pragma unroll
+  for (int i = 0; i < R; ++i) z[i] = y[i];
+  heat_stage<R>(y, z, acc, a0, g0, sx, forced, hh, (T)0, true, lane, n);
+  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hh, (T)2, false, lane, n);
+  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hT, (T)2, false, lane, n);
+  // stage 4: k4 = f(t+h, z); y <- y + h/6 (acc + k4)
+  {
+    T prev, right;
+    halos<R>(z, lane, n, prev, right);
+    const T h6 = (T)(h / 6.0);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const T cur = z[i];
+      const T nxt = (i + 1 < R) ? z[i + 1] : right;
+      T s = prev + nxt;
+      s = fma((T)-2, cur, s);
+      T k = a1 * s;
+      if (forced) k = fma(g1, sx[i], k);
+      y[i] = fma(h6, acc[i] + k, y[i]);
+      prev = cur;
+    }
+    if ((lane + 1) * R > n) {
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (lane * R + i >= n) y[i] = (T)0;
+    }
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) heat_affine_build_kernel(HeatArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n, cols = n + 1;
+  const int64_t total = (int64_t)a.S * cols;
+  const double dx = 1.0 / (double)(n + 1);
+  const T cdx = (T)(a.kappa / (dx * dx));
+  T* out = reinterpret_cast<T*>(a.out);
+
+  for (int64_t w = warp0; w < total; w += nwarps) {
+    const int j = (int)(w / cols);
+    const int c = (int)(w - (int64_t)j * cols);
+    const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
+    T y[R], z[R], acc[R], sx[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = lane * R + i;
+      y[i] = (c >= 1 && r == c - 1) ? (T)1 : (T)0;
+      sx[i] = (c == 0 && r < n) ? (T)sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : (T)0;
+    }
+    const bool forced = (c == 0);
+    if (!forced && !a.varcoef) {
+      for (int64_t i = 0; i < a.m; ++i) heat_horner_step<R>(y, z, cdx, (T)a.h, lane, n);
+    } else {
+      for (int64_t i = 0; i < a.m; ++i) {
+        const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
+        heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, forced, lane, n);
+      }
+    }
+    T* col = out + ((int64_t)j * cols + c) * n;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = lane * R + i;
+      if (r < n) col[r] = y[i];
+    }
+  }
+}
+
+// Serial fine solve of the heat equation: one warp, S*m literal RK4 steps.
+template <int R>
+__global__ void heat_serial_kernel(HeatArgs a, const double* y0, double* yT) {
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int n = a.n;
+  const double dx = 1.0 / (double)(n + 1);
+  const double cdx = a.kappa / (dx * dx);
+  double y[R], z[R], acc[R], sx[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int r = lane * R + i;
+    y[i] = r < n ? y0[r] : 0.0;
+    sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
+  }
+  for (int j = 0; j < a.S; ++j) {
+    const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
+    for (int64_t i = 0; i < a.m; ++i) {
+      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
+      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, true, lane, n);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int r = lane * R + i;
+    if (r < n) yT[r] = y[i];
+  }
+}
+
+}  // namespace nvpit
+
+using namespace nvpit;
+
+static int rows_per_lane(int n) {
+  const int r = (n + 31) / 32;
+  if (r <= 1) return 1;
+  if (r <= 2) return 2;
+  if (r <= 4) return 4;
+  if (r <= 8) return 8;
+  if (r <= 16) return 16;
+  return 0;
+}
+
+static HeatArgs heat_args(const nv_maps* M) {
+  HeatArgs a{};
+  a.out = M->data;
+  a.n = M->dim;
+  a.S = M->S;
+  a.m = M->m;
+  a.t0 = M->t0;
+  a.H = M->H;
+  a.h = M->h;
+  a.varcoef = M->rhs_kind == NV_RHS_HEAT1D_VARCOEF;
+  a.kappa = (!a.varcoef && M->nparams > 0) ? M->params[0] : 1.0;
+  a.amp = (!a.varcoef && M->nparams > 1) ? M->params[1] : 1.0;
+  return a;
+}
+
+template <typename T>
+static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s) {
+  int sms = 152;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
+  const int block = 32 * warps_per_cta;
+  const int64_t total_warps = (int64_t)a.S * (a.n + 1);
+  int per_sm = 0;
+  cudaError_t e = cudaSuccess;
+#define NVPIT_HEAT_CASE(RR)                                                                   \
+  case RR:                                                                                    \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heat_affine_build_kernel<T, RR>, \
+                                                      block, 0);                              \
+    if (e != cudaSuccess) return nv_cuda_check(e, "occupancy query");                         \
+    {                                                                                         \
+      int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);                                \
+      grid = std::min<int64_t>(grid, (total_warps + warps_per_cta - 1) / warps_per_cta);      \
+      heat_affine_build_kernel<T, RR><<<(unsigned)grid, block, 0, s>>>(a);                    \
+    }                                                                                         \
+    break;
+  switch (R) {
+    NVPIT_HEAT_CASE(1)
+    NVPIT_HEAT_CASE(2)
+    NVPIT_HEAT_CASE(4)
+    NVPIT_HEAT_CASE(8)
+    NVPIT_HEAT_CASE(16)
+    default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", a.n);
+  }
+#undef NVPIT_HEAT_CASE
+  return nv_cuda_check(cudaGetLastError(), "heat_affine_build_kernel launch");
+}
+
+nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
+  if (M->rhs_kind == NV_RHS_HEAT1D || M->rhs_kind == NV_RHS_HEAT1D_VARCOEF) {
+    if (M->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "affine heat maps are built with RK4");
+    const int R = rows_per_lane(M->dim);
+    if (R == 0) return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
+    const HeatArgs a = heat_args(M);
+    if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s);
+    return launch_heat_typed<float>(a, R, s);
+  }
+  return nv_fail(NV_ENOTSUP, "affine maps are not built for rhs kind %d", M->rhs_kind);
+}
+
+nv_status launch_serial_heat(const nv_maps* M, const double* y0, double* yT, cudaStream_t s) {
+  const HeatArgs a = heat_args(M);
+  switch (rows_per_lane(M->dim)) {
+    case 1: heat_serial_kernel<1><<<1, 32, 0, s>>>(a, y0, yT); break;
+    case 2: heat_serial_kernel<2><<<1, 32, 0, s>>>(a, y0, yT); break;
+    case 4: heat_serial_kernel<4><<<1, 32, 0, s>>>(a, y0, yT); break;
+    case 8: heat_serial_kernel<8><<<1, 32, 0, s>>>(a, y0, yT); break;
+    case 16: heat_serial_kernel<16><<<1, 32, 0, s>>>(a, y0, yT); break;
+    default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
+  }
+  return nv_cuda_check(cudaGetLastError(), "heat_serial_kernel launch");
+}

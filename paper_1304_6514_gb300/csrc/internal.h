@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of libnvpit.so.
+// Not part of the ABI: include/nvpit.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/nvpit.h"
+
+// Device status word values mirror nv_status.
+#define NVPIT_MAX_PARAMS 8
+
+struct nv_maps {
+  // problem (Figure "pseudocode", Given)
+  int32_t rhs_kind;
+  int32_t dim;
+  double params[NVPIT_MAX_PARAMS];
+  int32_t nparams;
+  double t0, T, H, h;
+  int32_t S;
+  int64_t m;
+  int32_t scheme;
+  // samples / map
+  int32_t map;
+  int32_t prec;
+  int32_t per_dim;
+  double lo[2], hi[2];
+  int32_t oob_policy;
+  // map storage (device)
+  void* data;
+  int64_t bytes;
+  int64_t elems_per_slice;
+  int32_t elem_bytes;
+  // workspace (device), one allocation
+  void* ws;
+  size_t ws_bytes;
+  int* status;                 // device status word (nv_status)
+  unsigned long long* oob;     // evaluations outside Xi
+  unsigned int* bar;           // grid-barrier counter
+  double* xbuf;                // 2 * dim doubles (ping-pong chain state)
+  double* coef;                // per-slice staged coefficients (may be NULL)
+  int64_t coef_per_slice;
+  // reduced-precision composition scratch (NV_TF32_REFINE), allocated lazily
+  void* scan_ws;
+  size_t scan_ws_bytes;
+  int device;
+};
+
+// Error helpers (api.cu).  nv_fail records the message for nv_last_error().
+nv_status nv_fail(nv_status code, const char* fmt, ...);
+nv_status nv_cuda_check(cudaError_t e, const char* what);
+
+// Launchers.  Each validates nothing (the API layer did), launches on `s`
+// and returns NV_OK or NV_ECUDA.
+nv_status launch_coef_tables(nv_maps* M, cudaStream_t s);
+nv_status launch_table_build(nv_maps* M, cudaStream_t s, int block);
+nv_status launch_affine_build(nv_maps* M, cudaStream_t s);
+nv_status launch_table_compose(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                               cudaStream_t s);
+nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                              cudaStream_t s, int rows_per_cta);
+nv_status launch_serial_fine(int32_t rhs_kind, int32_t dim, const double* params, double t0,
+                             double H, double h, int32_t S, int64_t m, int32_t scheme,
+                             const double* y0, double* yT, cudaStream_t s);
+nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
+                             cudaStream_t s);
+
+// Tunables (set by nv_tune_set, read by the launchers).
+struct nv_tunables {
+  int table_block;         // threads per CTA for the table build
+  int chain_rows_per_cta;  // rows of the chain GEMV owned by one CTA
+  int affine_warps;        // warps per CTA in the affine build
+};
+extern nv_tunables g_tune;

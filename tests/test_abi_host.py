@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI: the library loads, exports what the header
+declares, plans steps like the oracle and rejects bad arguments before any
+CUDA call.  CPU only (no GPU is touched)."""
+import ctypes
+
+import pytest
+
+import paper_1304_6514_gb300 as nvp
+from paper_1304_6514_gb300 import _build
+from oracle import nievergelt as nv
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return nvp.load_library()
+
+
+def test_exports_every_declared_function(lib):
+    names = nvp.header_functions()
+    assert "nv_build_propagators" in names and "nv_compose" in names and "nv_solve" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert nvp.version() == 1
+
+
+@pytest.mark.parametrize("t0,T,S,dt,fixed", [
+    (0.0, 0.1, 1024, 1e-5, 0), (0.0, 20.0, 128, 1e-3, 0), (0.0, 1.0, 512, 2e-4, 0),
+    (0.0, 0.5, 4, 0.01, 0), (0.0, 0.5, 4, 0.005, 0), (0.0, 10.0, 16, 0.0, 10000),
+    (1.5, 7.25, 33, 3e-3, 0), (0.0, 17.3, 211, 1e-3, 0)])
+def test_plan_steps_matches_oracle(lib, t0, T, S, dt, fixed):
+    m, h = nvp.plan_steps(t0, T, S, dt, fixed)
+    mo = nv.steps_per_slice(t0, T, S, dt, fixed)
+    assert m == mo
+    assert h == nv.step_size(t0, T, S, mo)
+
+
+def test_plan_steps_rejects(lib):
+    with pytest.raises(nvp.NvError) as e:
+        nvp.plan_steps(1.0, 0.5, 4, 0.1)
+    assert e.value.status == nvp.NV_EINVAL
+    with pytest.raises(nvp.NvError):
+        nvp.plan_steps(0.0, 1.0, 4, 0.0, 0)
+
+
+def _expect(status_wanted, fn):
+    with pytest.raises(nvp.NvError) as e:
+        fn()
+    assert e.value.status == status_wanted, (e.value.status, str(e.value))
+    assert nvp.last_error()
+
+
+@pytest.mark.parametrize("case", [
+    dict(rhs=("cos_cubic", 2, ()), smp=("pl1d", 64, (-2,), (2,)), msg="dim"),
+    dict(rhs=("cos_cubic", 1, ()), smp=("pl1d", 1, (-2,), (2,)), msg="per_dim"),
+    dict(rhs=("cos_cubic", 1, ()), smp=("pl1d", 8, (2,), (-2,)), msg="lo<hi"),
+    dict(rhs=("vdp", 2, ()), smp=("bilinear2d", 8, (-3, -3), (3, 3)), msg="mu missing"),
+    dict(rhs=("vdp", 2, (1.0,)), smp=("pl1d", 8, (-3,), (3,)), msg="map/dim"),
+    dict(rhs=("cos_cubic", 1, ()), smp=("affine", 0, (), ()), msg="affine nonlinear"),
+    dict(rhs=("heat1d", 600, ()), smp=("affine", 0, (), ()), msg="too big"),
+    dict(rhs=("heat1d", 16, (1.0,)), smp=("affine", 0, (), ()), msg="params"),
+])
+def test_build_rejects_before_launch(lib, case):
+    r = nvp.rhs(*case["rhs"])
+    s = nvp.samples(*case["smp"])
+    st = nvp.steps("rk4", 1e-3)
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(r, 0.0, 1.0, 4, s, st, stream=0))
+
+
+def test_build_rejects_bad_grid(lib):
+    r = nvp.rhs("cos_cubic", 1)
+    s = nvp.samples("pl1d", 8, (-2,), (2,))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(r, 1.0, 0.0, 4, s, nvp.steps("euler", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(r, 0.0, 1.0, 0, s, nvp.steps("euler", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(r, 0.0, 1.0, 4, s, nvp.steps("euler", 0.0), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(
+        r, 0.0, 1.0, 4, s, nvp.steps("euler", 1e-3, prec="tf32_refine"), stream=0))
+
+
+def test_null_handles(lib):
+    assert lib.nv_compose(None, None, None, None, None) == nvp.NV_EBADMAP
+    assert lib.nv_maps_info(None, None) == nvp.NV_EINVAL
+    assert lib.nv_maps_destroy(None) == nvp.NV_OK
+    assert lib.nv_tune_set(99, 1) == nvp.NV_EINVAL
+    assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL

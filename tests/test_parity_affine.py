@@ -1,0 +1,132 @@
+"""GPU parity of the affine path (heat equation maps, chain composition)
+against the FP64 oracle.
+
+Tolerances: float64 <= 1e-11 relative L2 (maps: max-norm relative to the
+largest entry), float32 <= 1e-5."""
+import numpy as np
+import pytest
+
+import paper_1304_6514_gb300 as nvp
+import workloads
+from oracle import nievergelt as nv
+
+from gpu_util import need_gpu, rel_l2, rel_max, run_method
+
+pytestmark = pytest.mark.gpu
+
+
+def _heat(torch, w, prec, rhs_name="heat1d"):
+    r = nvp.rhs(rhs_name, w.dim, w.params if rhs_name == "heat1d" else ())
+    smp = nvp.samples("affine")
+    st = nvp.steps("rk4", w.dt, w.steps_per_slice, prec)
+    maps, tab, yT, lam, oob = run_method(torch, r, w.t0, w.T, w.S, smp, st, w.y0)
+    n = w.dim
+    blocks = tab.reshape(w.S, n + 1, n)          # [j, col, row]
+    b = blocks[:, 0, :]
+    A = blocks[:, 1:, :].transpose(0, 2, 1)      # A[j][row, col]
+    return maps, A, b, yT, lam
+
+
+@pytest.mark.parametrize("n,S", [(40, 7), (64, 3), (1, 4), (97, 5)])
+def test_heat_small_elementwise_fp64(n, S):
+    """Every map entry and every boundary state; n = 40 and 97 leave padding
+    rows in the last lanes, n = 1 is the degenerate single-unknown case."""
+    torch = need_gpu()
+    w = workloads.heat1d(n=n, S=S, T=0.003, dt=5e-5)
+    _, A, b, yT, lam = _heat(torch, w, "fp64")
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    assert rel_max(A, oA) <= 1e-11
+    assert rel_max(b, ob) <= 1e-11
+    olam = nv.compose_affine(oA, ob, w.y0)
+    assert rel_l2(lam, olam) <= 1e-11
+    assert rel_l2(yT, olam[-1]) <= 1e-11
+
+
+def test_heat_small_fp32():
+    torch = need_gpu()
+    w = workloads.heat1d(n=40, S=7, T=0.003, dt=1e-4)
+    _, A, b, yT, lam = _heat(torch, w, "fp32")
+    m = nv.workload_steps(w)
+    oA, ob = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                             w.t0, w.T, w.S, m, w.dim)
+    assert rel_max(A, oA) <= 1e-5
+    olam = nv.compose_affine(oA, ob, w.y0)
+    assert rel_l2(yT, olam[-1]) <= 1e-5
+
+
+def test_heat_varcoef_small():
+    """Section 5's variable-coefficient heat equation: time-dependent operator,
+    so every column takes the literal RK4 stages."""
+    torch = need_gpu()
+    n = 19
+    w = workloads.Workload("v", "heat1d_varcoef", n, 0.0, 1.0, 5, "rk4", 1e-3, 0, "affine",
+                           y0=np.sin(np.pi * nv.heat1d_grid(n)))
+    _, A, b, yT, lam = _heat(torch, w, "fp64", "heat1d_varcoef")
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    assert rel_max(A, oA) <= 1e-11 and rel_max(b, ob) <= 1e-11
+    assert rel_l2(yT, nv.compose_affine(oA, ob, w.y0)[-1]) <= 1e-11
+
+
+_FULL = {}
+
+
+def _full_oracle():
+    """Heat equation at full size (n=256, S=1024, m=10): sampled slices of the
+    oracle's maps and its serial fine solve (equal to the composed maps up to
+    rounding, end of Section 4)."""
+    if not _FULL:
+        w = workloads.heat1d()
+        m = nv.workload_steps(w)
+        fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+        _FULL["w"] = w
+        _FULL["slices"] = {j: nv.build_affine_slice(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim, j)
+                           for j in (0, 517, 1023)}
+        _FULL["serial"] = nv.serial_fine(fi, "rk4", w.t0, w.T, w.S, m, w.y0)
+    return _FULL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_heat_full_size(prec, tol):
+    """n=256, S=1024 slices, RK4 with m=10: three whole slice maps element by
+    element, and the composed final state against the serial fine solve."""
+    torch = need_gpu()
+    o = _full_oracle()
+    w = o["w"]
+    _, A, b, yT, lam = _heat(torch, w, prec)
+    for j, (oA, ob) in o["slices"].items():
+        assert rel_max(A[j], oA) <= tol, j
+        assert rel_max(b[j], ob) <= tol, j
+    assert rel_l2(yT, o["serial"]) <= tol
+    assert rel_l2(lam[-1], yT) == 0.0
+
+
+def test_heat_serial_fine_gpu():
+    torch = need_gpu()
+    w = workloads.heat1d(n=40, S=7, T=0.003, dt=1e-4)
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    st = nvp.steps("rk4", w.dt)
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    ys = torch.empty_like(y0)
+    nvp.serial_fine(r, w.t0, w.T, w.S, st, y0, ys)
+    ser = nv.serial_fine(nv.workload_rhs(w, True), "rk4", w.t0, w.T, w.S, nv.workload_steps(w), w.y0)
+    assert rel_l2(ys.cpu().numpy(), ser) <= 1e-11
+
+
+@pytest.mark.parametrize("rpc", [1, 4, 8, 32, 64])
+def test_chain_launch_shapes(rpc):
+    """The chain result does not depend on how rows are split over CTAs."""
+    torch = need_gpu()
+    w = workloads.heat1d(n=97, S=9, T=0.003, dt=5e-5)
+    try:
+        nvp.tune_set(1, rpc)
+        _, A, b, yT, lam = _heat(torch, w, "fp64")
+    finally:
+        nvp.tune_set(1, 0)
+    m = nv.workload_steps(w)
+    oA, ob = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                             w.t0, w.T, w.S, m, w.dim)
+    assert rel_l2(lam, nv.compose_affine(oA, ob, w.y0)) <= 1e-11
