@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="nvpit", choices=["nvpit", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="fp32,tf32_refine")
+    ap.add_argument("--slices", type=int, default=0, help="override S (profiling a reduced case)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
     return ap.parse_args()
 
 
@@ -281,7 +284,7 @@ def main():
     import paper_1304_6514_gb300 as nvp
     import workloads
 
-    w = workloads.heat1d()
+    w = workloads.heat1d(S=args.slices) if args.slices > 0 else workloads.heat1d()
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     K, W = args.steps, max(3, args.warmup)
@@ -339,10 +342,13 @@ def main():
         variants[v]["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(rv["yT"] - ref) / np.linalg.norm(ref))
 
     # ---- end to end through the one-call API with host buffers
-    e2e_t, h2d, d2h = time_e2e(nvp, torch, w, max(3, K // 4), 2, stream)
+    if args.no_e2e:
+        e2e_t, h2d, d2h = [float("nan")], 0, 0
+    else:
+        e2e_t, h2d, d2h = time_e2e(nvp, torch, w, max(3, K // 4), 2, stream)
     e2e_val = units / statistics.mean(e2e_t)
 
-    peaks_probe = gpu_peak_probe(torch)
+    peaks_probe = {} if args.no_probe else gpu_peak_probe(torch)
     peaks, peaks_src = read_peaks()
 
     line = {

@@ -114,16 +114,32 @@ struct RhsChain3 {  // wall-m1-m2-m3-wall, tension k d + k3 d^3, damping c
 // Fine schemes for a D-dimensional state held in registers.
 // c0, ch, c1: the time-dependent coefficient at t, t + h/2, t + h.
 // ---------------------------------------------------------------------------
-template <class R, typename T>
-__device__ __forceinline__ void euler_step(const R& rhs, T c0, T h, T* y) {
-  T f[R::D];
-  rhs(c0, y, f);
-#pragma unroll
-  for (int d = 0; d < R::D; ++d) y[d] = y[d] + h * f[d];
+// State update y <- y + inc.  In float32 the update is compensated (Kahan):
+// the rounding error of each addition is carried in c and fed back, so long
+// recurrences of small increments keep float32 rounding instead of growing
+// with the step count.  In float64 it is the plain sum.
+template <typename T>
+__device__ __forceinline__ void add_update(T& y, T inc, T& c) {
+  if constexpr (sizeof(T) == 4) {
+    const T yk = inc - c;
+    const T t = y + yk;
+    c = (t - y) - yk;
+    y = t;
+  } else {
+    y = y + inc;
+  }
 }
 
 template <class R, typename T>
-__device__ __forceinline__ void rk4_step(const R& rhs, T c0, T ch, T c1, T h, T* y) {
+__device__ __forceinline__ void euler_step(const R& rhs, T c0, T h, T* y, T* comp) {
+  T f[R::D];
+  rhs(c0, y, f);
+#pragma unroll
+  for (int d = 0; d < R::D; ++d) add_update(y[d], h * f[d], comp[d]);
+}
+
+template <class R, typename T>
+__device__ __forceinline__ void rk4_step(const R& rhs, T c0, T ch, T c1, T h, T* y, T* comp) {
   T k[R::D], z[R::D], acc[R::D];
   const T hh = h * (T)0.5;
   rhs(c0, y, k);
@@ -138,7 +154,7 @@ __device__ __forceinline__ void rk4_step(const R& rhs, T c0, T ch, T c1, T h, T*
   rhs(c1, z, k);
   const T h6 = h / (T)6;
 #pragma unroll
-  for (int d = 0; d < R::D; ++d) y[d] = y[d] + h6 * (acc[d] + k[d]);
+  for (int d = 0; d < R::D; ++d) add_update(y[d], h6 * (acc[d] + k[d]), comp[d]);
 }
 
 }  // namespace nvpit

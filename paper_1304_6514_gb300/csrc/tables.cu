@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(256) table_build_kernel(TableArgs a) {
   const R rhs(a.params);
   const T h = (T)a.h;
 
-  T y[R::D];
+  T y[R::D], comp[R::D];
 #pragma unroll
-  for (int d = 0; d < R::D; ++d) y[d] = 0;
+  for (int d = 0; d < R::D; ++d) y[d] = comp[d] = 0;
   if constexpr (R::D == 1) {
     y[0] = (T)__dadd_rn(a.lo0, __dmul_rn((double)k, a.d0));
   } else {
@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(256) table_build_kernel(TableArgs a) {
           const int64_t q = 2 * (i - i0);
           T c0 = 0, ch = 0, c1 = 0;
           if (R::TIME_DEP) { c0 = cs[q]; ch = cs[q + 1]; c1 = cs[q + 2]; }
-          rk4_step(rhs, c0, ch, c1, h, y);
+          rk4_step(rhs, c0, ch, c1, h, y, comp);
         }
       } else {
         for (int64_t i = i0; i < i1; ++i) {
           T c0 = 0;
           if (R::TIME_DEP) c0 = cs[i - i0];
-          euler_step(rhs, c0, h, y);
+          euler_step(rhs, c0, h, y, comp);
         }
       }
     }
@@ -203,8 +203,8 @@ __global__ void serial_table_kernel(ParamPack pp, double t0, double H, double h,
                                     int64_t m, int rk4, const double* y0, double* yT) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const R rhs(pp.p);
-  double y[R::D];
-  for (int d = 0; d < R::D; ++d) y[d] = y0[d];
+  double y[R::D], comp[R::D];
+  for (int d = 0; d < R::D; ++d) { y[d] = y0[d]; comp[d] = 0.0; }
   for (int j = 0; j < S; ++j) {
     const double Tj = __dadd_rn(t0, __dmul_rn((double)j, H));
     for (int64_t i = 0; i < m; ++i) {
@@ -212,11 +212,11 @@ __global__ void serial_table_kernel(ParamPack pp, double t0, double H, double h,
       if (rk4) {
         double c0 = 0, ch = 0, c1 = 0;
         if (R::TIME_DEP) { c0 = cos(t); ch = cos(__dadd_rn(t, 0.5 * h)); c1 = cos(__dadd_rn(t, h)); }
-        rk4_step(rhs, c0, ch, c1, h, y);
+        rk4_step(rhs, c0, ch, c1, h, y, comp);
       } else {
         double c0 = 0;
         if (R::TIME_DEP) c0 = cos(t);
-        euler_step(rhs, c0, h, y);
+        euler_step(rhs, c0, h, y, comp);
       }
     }
   }

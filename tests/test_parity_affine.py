@@ -89,10 +89,16 @@ def _full_oracle():
     return _FULL
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_heat_full_size(prec, tol):
+@pytest.mark.parametrize("prec,tol,final_tol", [("fp64", 1e-11, 1e-11), ("fp32", 1e-5, 2e-4)])
+def test_heat_full_size(prec, tol, final_tol):
     """n=256, S=1024 slices, RK4 with m=10: three whole slice maps element by
-    element, and the composed final state against the serial fine solve."""
+    element, and the composed final state against the serial fine solve.
+
+    float32 final state: the 1024 maps of this constant-coefficient problem
+    are bitwise identical, so their float32 rounding composes coherently:
+    rounding the exact maps to float32 alone gives 1.0e-5, computing them in
+    float32 ~5e-5 to 9e-5 (bound S * m * u32 * O(1) ~ 6e-4).  The bound here is
+    2e-4; the refined tensor-core path is the one held to the method's target."""
     torch = need_gpu()
     o = _full_oracle()
     w = o["w"]
@@ -100,7 +106,7 @@ def test_heat_full_size(prec, tol):
     for j, (oA, ob) in o["slices"].items():
         assert rel_max(A[j], oA) <= tol, j
         assert rel_max(b[j], ob) <= tol, j
-    assert rel_l2(yT, o["serial"]) <= tol
+    assert rel_l2(yT, o["serial"]) <= final_tol
     assert rel_l2(lam[-1], yT) == 0.0
 
 
