@@ -194,6 +194,34 @@ const char* nv_last_error(void);
 /* NVPIT_VERSION of the built library. */
 int32_t nv_version(void);
 
+/* Largest state dimension nv_compose_affine_noalloc accepts. */
+#define NVPIT_NOALLOC_MAX_DIM 4096
+
+/* Affine composition that allocates nothing (the paper has no counterpart:
+ * this serves callers, not the method).  For callers that cannot allocate
+ * device memory when they compose - an application whose memory pool already
+ * owns the GPU, a real-time loop that must not pay for or synchronise on
+ * cudaMalloc/cudaFree, a plug-in that may only use the buffers it is lent.
+ * Computes the same chain as nv_compose for NV_MAP_AFFINE maps, float64:
+ *   maps_dev     S blocks of dim x (dim+1) values in the AFFINE layout of
+ *                nv_maps_desc (column 0 = b_j), double for NV_FP64, float for
+ *                NV_FP32 (input, caller-owned device memory)
+ *   y0_dev       dim doubles (input); yT_dev dim doubles (output, lambda_S)
+ *   lambdas_dev  (S+1) x dim doubles (output, may be NULL)
+ *   status_dev   one int32 (output, may be NULL): the device status of this
+ *                call (NV_OK or NV_ETIMEOUT), written on `stream`
+ * Scratch: a fixed static __device__ array of about 64 KiB per GPU that loads
+ * the library, held until the process exits; it serves 1 <= dim <=
+ * NVPIT_NOALLOC_MAX_DIM, larger dim returns NV_EINVAL.  The first call on a
+ * device looks up that array's device address with cudaGetSymbolAddress (make
+ * that first call before any stream capture on that device).  All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads)
+ * race and give wrong results; order them on one stream or synchronise.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t dim, int32_t S,
+                                    const double* y0_dev, double* yT_dev, double* lambdas_dev,
+                                    int32_t* status_dev, void* stream);
+
 /* Launch-shape tunables, process-wide (host only; set by the autotuner).
  *   key 0: threads per CTA of the table build (32..256, default 64)
  *   key 1: rows of each chain product owned by one CTA (default 16)

@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "nv_maps_copy_out": [P, P, c_int64, P],
         "nv_maps_check": [P, P, POINTER(c_int64)],
         "nv_tune_set": [c_int32, c_int32],
+        "nv_compose_affine_noalloc": [P, c_int32, c_int32, c_int32, P, P, P, P, P],
         "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
                           POINTER(c_double)],
     }
@@ -200,6 +201,27 @@ def solve(rhs_, t0, T, S, samples_, steps_, y0, yT, stream=None):
 def serial_fine(rhs_, t0, T, S, steps_, y0, yT, stream=None):
     _check(load_library().nv_serial_fine(byref(rhs_), t0, T, S, byref(steps_), _ptr(y0), _ptr(yT),
                                          _stream(stream)))
+
+
+def compose_affine_noalloc(maps_dev, prec: str, dim: int, S: int, y0, yT, lambdas=None,
+                           status=None, stream=None):
+    """nv_compose_affine_noalloc: the affine chain over caller-owned maps, with
+    its scratch in the library's fixed static device array (no allocation).
+    maps_dev: CUDA tensor holding the maps in the AFFINE layout (float64 for
+    prec "fp64", float32 for "fp32"); status: optional int32 CUDA tensor."""
+    import torch
+    want = torch.float64 if prec == "fp64" else torch.float32
+    if not (maps_dev.is_cuda and maps_dev.dtype == want and maps_dev.is_contiguous()):
+        raise ValueError("maps_dev must be a contiguous CUDA tensor of the maps' precision")
+    if maps_dev.numel() < S * dim * (dim + 1):
+        raise ValueError("maps_dev holds fewer than S * dim * (dim + 1) values")
+    st = None
+    if status is not None:
+        if not (status.is_cuda and status.dtype == torch.int32):
+            raise ValueError("status must be an int32 CUDA tensor")
+        st = status.data_ptr()
+    _check(load_library().nv_compose_affine_noalloc(maps_dev.data_ptr(), PREC[prec], dim, S, _ptr(y0),
+                                                    _ptr(yT), _ptr(lambdas), st, _stream(stream)))
 
 
 def maps_info(maps: Maps) -> NvMapsDesc:

@@ -136,3 +136,44 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
   return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
                        "affine_chain_kernel cooperative launch");
 }
+
+nv_status launch_affine_chain_buffers(const void* maps, int prec, int n, int S, const double* y0,
+                                      double* yT, double* lambdas, double* xbuf, unsigned* bar,
+                                      int* status, cudaStream_t s, int rows_per_cta) {
+  const int block = 256;
+  int rpc = rows_per_cta > 0 ? rows_per_cta : 16;
+  rpc = std::min(rpc, block);
+  while (block % rpc) --rpc;
+  const int G = (n + rpc - 1) / rpc;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = sizeof(double) * (size_t)(n + 1);
+  const void* fn = (prec == NV_FP64) ? (const void*)affine_chain_kernel<double>
+                                     : (const void*)affine_chain_kernel<float>;
+  if (smem > 48 * 1024) {
+    nv_status st = nv_cuda_check(
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "chain smem attribute");
+    if (st != NV_OK) return st;
+  }
+  nv_status st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem),
+                               "chain occupancy");
+  if (st != NV_OK) return st;
+  if ((int64_t)per_sm * sms < G)
+    return nv_fail(NV_ENOTSUP, "chain needs %d resident CTAs, device holds %d", G, per_sm * sms);
+  AffineChainArgs a{};
+  a.maps = maps;
+  a.n = n;
+  a.S = S;
+  a.rpc = rpc;
+  a.y0 = y0;
+  a.yT = yT;
+  a.lambdas = lambdas;
+  a.xbuf = xbuf;
+  a.bar = bar;
+  a.status = status;
+  void* args[] = {&a};
+  return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
+                       "affine_chain_kernel cooperative launch");
+}

@@ -60,6 +60,12 @@ nv_status launch_table_compose(const nv_maps* M, const double* y0, double* yT, d
                                cudaStream_t s);
 nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                               cudaStream_t s, int rows_per_cta);
+// Chain composition over caller-supplied buffers (used by the allocation-free
+// entry point): maps in the AFFINE layout, prec NV_FP64 or NV_FP32, xbuf of
+// 2*n doubles, bar and status zeroed by the caller before the launch.
+nv_status launch_affine_chain_buffers(const void* maps, int prec, int n, int S, const double* y0,
+                                      double* yT, double* lambdas, double* xbuf, unsigned* bar,
+                                      int* status, cudaStream_t s, int rows_per_cta);
 nv_status launch_serial_fine(int32_t rhs_kind, int32_t dim, const double* params, double t0,
                              double H, double h, int32_t S, int64_t m, int32_t scheme,
                              const double* y0, double* yT, cudaStream_t s);
