@@ -226,7 +226,9 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 0: threads per CTA of the table build (32..256, default 64)
  *   key 1: rows of each chain product owned by one CTA (default 16)
  *   key 2: warps per CTA of the affine build (default 8)
- * A value <= 0 restores the default.  Returns NV_EINVAL for an unknown key. */
+ *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
+ *          fits, up to 16; a negative value selects the grid-wide chain)
+ * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

@@ -15,6 +15,8 @@
 // the four RK4 stages literally.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace nvpit {
@@ -148,36 +150,70 @@ __device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double t, doub
   }
 }
 
+// Homogeneous columns of a time-invariant operator (c = 1..d): Horner-form
+// RK4 only, so a thread holds just y and v (2R values) and many warps fit.
 template <typename T, int R>
-__global__ void __launch_bounds__(256) heat_affine_build_kernel(HeatArgs a) {
+__global__ void __launch_bounds__(256) heat_horner_kernel(HeatArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int n = a.n, cols = n + 1;
-  const int64_t total = (int64_t)a.S * cols;
+  const int64_t total = (int64_t)a.S * n;
+  const double dx = 1.0 / (double)(n + 1);
+  const T cdx = (T)(a.kappa / (dx * dx));
+  const T h = (T)a.h;
+  T* out = reinterpret_cast<T*>(a.out);
+  for (int64_t w = warp0; w < total; w += nwarps) {
+    const int j = (int)(w / n);
+    const int c = 1 + (int)(w - (int64_t)j * n);
+    T y[R], v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = (lane * R + i == c - 1) ? (T)1 : (T)0;
+    for (int64_t i = 0; i < a.m; ++i) heat_horner_step<R>(y, v, cdx, h, lane, n);
+    T* col = out + ((int64_t)j * cols + c) * n;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = lane * R + i;
+      if (r < n) col[r] = y[i];
+    }
+  }
+}
+
+// Columns that take the four RK4 stages literally: the forcing column c = 0
+// of every slice, and for a time-dependent operator every column.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) heat_literal_kernel(HeatArgs a, int all_columns) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n, cols = n + 1;
+  const int per_slice = all_columns ? cols : 1;
+  const int64_t total = (int64_t)a.S * per_slice;
   const double dx = 1.0 / (double)(n + 1);
   const T cdx = (T)(a.kappa / (dx * dx));
   T* out = reinterpret_cast<T*>(a.out);
-
   for (int64_t w = warp0; w < total; w += nwarps) {
-    const int j = (int)(w / cols);
-    const int c = (int)(w - (int64_t)j * cols);
+    const int j = (int)(w / per_slice);
+    const int c = (int)(w - (int64_t)j * per_slice);
     const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
+    const bool forced = (c == 0);
     T y[R], z[R], acc[R], sx[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int r = lane * R + i;
       y[i] = (c >= 1 && r == c - 1) ? (T)1 : (T)0;
-      sx[i] = (c == 0 && r < n) ? (T)sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : (T)0;
+      sx[i] = (T)0;
     }
-    const bool forced = (c == 0);
-    if (!forced && !a.varcoef) {
-      for (int64_t i = 0; i < a.m; ++i) heat_horner_step<R>(y, z, cdx, (T)a.h, lane, n);
-    } else {
-      for (int64_t i = 0; i < a.m; ++i) {
-        const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
-        heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, forced, lane, n);
+    if (forced) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = lane * R + i;
+        if (r < n) sx[i] = (T)sin(M_PI * ((double)(r + 1) / (double)(n + 1)));
       }
+    }
+    for (int64_t i = 0; i < a.m; ++i) {
+      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
+      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, forced, lane, n);
     }
     T* col = out + ((int64_t)j * cols + c) * n;
 #pragma unroll
@@ -246,38 +282,53 @@ static HeatArgs heat_args(const nv_maps* M) {
   return a;
 }
 
-template <typename T>
-static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s) {
-  int sms = 152;
-  int dev = 0;
+template <typename K>
+static nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* grid_out) {
+  int sms = 152, dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  nv_status st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0),
+                               "occupancy query");
+  if (st != NV_OK) return st;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  grid = std::min<int64_t>(grid, (work_warps * 32 + block - 1) / block);
+  *grid_out = (int)std::max<int64_t>(grid, 1);
+  return NV_OK;
+}
+
+template <typename T, int R>
+static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s) {
   const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
   const int block = 32 * warps_per_cta;
-  const int64_t total_warps = (int64_t)a.S * (a.n + 1);
-  int per_sm = 0;
-  cudaError_t e = cudaSuccess;
-#define NVPIT_HEAT_CASE(RR)                                                                   \
-  case RR:                                                                                    \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, heat_affine_build_kernel<T, RR>, \
-                                                      block, 0);                              \
-    if (e != cudaSuccess) return nv_cuda_check(e, "occupancy query");                         \
-    {                                                                                         \
-      int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);                                \
-      grid = std::min<int64_t>(grid, (total_warps + warps_per_cta - 1) / warps_per_cta);      \
-      heat_affine_build_kernel<T, RR><<<(unsigned)grid, block, 0, s>>>(a);                    \
-    }                                                                                         \
-    break;
+  int grid = 0;
+  nv_status st;
+  if (a.varcoef) {
+    st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S * (a.n + 1), &grid);
+    if (st != NV_OK) return st;
+    heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 1);
+    return nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
+  }
+  st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S, &grid);
+  if (st != NV_OK) return st;
+  heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
+  st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
+  if (st != NV_OK) return st;
+  st = persistent_grid(heat_horner_kernel<T, R>, block, (int64_t)a.S * a.n, &grid);
+  if (st != NV_OK) return st;
+  heat_horner_kernel<T, R><<<grid, block, 0, s>>>(a);
+  return nv_cuda_check(cudaGetLastError(), "heat_horner_kernel launch");
+}
+
+template <typename T>
+static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s) {
   switch (R) {
-    NVPIT_HEAT_CASE(1)
-    NVPIT_HEAT_CASE(2)
-    NVPIT_HEAT_CASE(4)
-    NVPIT_HEAT_CASE(8)
-    NVPIT_HEAT_CASE(16)
+    case 1: return launch_heat_R<T, 1>(a, s);
+    case 2: return launch_heat_R<T, 2>(a, s);
+    case 4: return launch_heat_R<T, 4>(a, s);
+    case 8: return launch_heat_R<T, 8>(a, s);
+    case 16: return launch_heat_R<T, 16>(a, s);
     default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", a.n);
   }
-#undef NVPIT_HEAT_CASE
-  return nv_cuda_check(cudaGetLastError(), "heat_affine_build_kernel launch");
 }
 
 nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {

@@ -77,5 +77,6 @@ struct nv_tunables {
   int table_block;         // threads per CTA for the table build
   int chain_rows_per_cta;  // rows of the chain GEMV owned by one CTA
   int affine_warps;        // warps per CTA in the affine build
+  int chain_cluster;       // CTAs per cluster of the d <= 512 chain (0 auto, < 0 grid-wide)
 };
 extern nv_tunables g_tune;

@@ -122,17 +122,22 @@ def test_heat_serial_fine_gpu():
     assert rel_l2(ys.cpu().numpy(), ser) <= 1e-11
 
 
-@pytest.mark.parametrize("rpc", [1, 4, 8, 32, 64])
-def test_chain_launch_shapes(rpc):
-    """The chain result does not depend on how rows are split over CTAs."""
+@pytest.mark.parametrize("cluster,rpc", [(2, 0), (4, 0), (8, 0), (16, 0), (-1, 1), (-1, 4), (-1, 32), (-1, 64)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_chain_launch_shapes(cluster, rpc, prec, tol):
+    """The composition does not depend on how the chain is laid out: one
+    cluster of 2..16 CTAs exchanging lambda through distributed shared memory,
+    or the grid-wide chain with 1..64 rows per CTA."""
     torch = need_gpu()
     w = workloads.heat1d(n=97, S=9, T=0.003, dt=5e-5)
     try:
+        nvp.tune_set(3, cluster)
         nvp.tune_set(1, rpc)
-        _, A, b, yT, lam = _heat(torch, w, "fp64")
+        _, A, b, yT, lam = _heat(torch, w, prec)
     finally:
+        nvp.tune_set(3, 0)
         nvp.tune_set(1, 0)
     m = nv.workload_steps(w)
     oA, ob = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
                              w.t0, w.T, w.S, m, w.dim)
-    assert rel_l2(lam, nv.compose_affine(oA, ob, w.y0)) <= 1e-11
+    assert rel_l2(lam, nv.compose_affine(oA, ob, w.y0)) <= tol
