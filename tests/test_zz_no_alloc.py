@@ -28,8 +28,11 @@ def test_noalloc_rejects_oversized_dim_on_host():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_matches_compose_twice(prec):
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_noalloc_matches_compose_twice(prec, tol):
+    """float32 maps: nv_compose may compose them in float32 arithmetic, this
+    entry point accumulates in float64, so they agree to the float32
+    tolerance of the other tests."""
     torch = need_gpu()
     w = workloads.heat1d(n=97, S=9, T=0.003, dt=5e-5)
     maps = nvp.build_propagators(nvp.rhs("heat1d", w.dim, w.params), w.t0, w.T, w.S,
@@ -50,8 +53,8 @@ def test_noalloc_matches_compose_twice(prec):
         nvp.compose_affine_noalloc(maps_dev, prec, w.dim, w.S, y0, yT, lam, status)
         torch.cuda.synchronize()
         assert int(status.item()) == nvp.NV_OK, call
-        assert rel_l2(yT.cpu().numpy(), yT_ref.cpu().numpy()) <= 1e-11, call
-        assert rel_l2(lam.cpu().numpy(), lam_ref.cpu().numpy()) <= 1e-11, call
+        assert rel_l2(yT.cpu().numpy(), yT_ref.cpu().numpy()) <= tol, call
+        assert rel_l2(lam.cpu().numpy(), lam_ref.cpu().numpy()) <= tol, call
     maps.destroy()
 
 
