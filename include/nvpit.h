@@ -228,6 +228,7 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 2: warps per CTA of the affine build (default 8)
  *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
  *          fits, up to 16; a negative value selects the grid-wide chain)
+ *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 

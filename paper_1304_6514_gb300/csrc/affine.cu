@@ -253,6 +253,39 @@ __global__ void heat_serial_kernel(HeatArgs a, const double* y0, double* yT) {
   }
 }
 
+// Defects of approximate boundary states for the float64 correction pass:
+// d_j = g^j(lt_j) - lt_{j+1}, one warp per slice j integrating the full
+// inhomogeneous right-hand side over slice j from lt_j with literal RK4
+// stages in float64 (lt has S+1 rows of n, d has S rows).
+template <int R>
+__global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const double* lt, double* d) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  const double dx = 1.0 / (double)(n + 1);
+  const double cdx = a.kappa / (dx * dx);
+  for (int64_t j = warp0; j < a.S; j += nwarps) {
+    const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
+    double y[R], z[R], acc[R], sx[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = lane * R + i;
+      y[i] = r < n ? lt[j * n + r] : 0.0;
+      sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
+    }
+    for (int64_t i = 0; i < a.m; ++i) {
+      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
+      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, true, lane, n);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = lane * R + i;
+      if (r < n) d[j * n + r] = y[i] - lt[(j + 1) * n + r];
+    }
+  }
+}
+
 }  // namespace nvpit
 
 using namespace nvpit;
@@ -354,4 +387,29 @@ nv_status launch_serial_heat(const nv_maps* M, const double* y0, double* yT, cud
     default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
   }
   return nv_cuda_check(cudaGetLastError(), "heat_serial_kernel launch");
+}
+
+nv_status launch_heat_defect(const nv_maps* M, const double* lam_tilde, double* d, cudaStream_t s) {
+  if (M->rhs_kind != NV_RHS_HEAT1D && M->rhs_kind != NV_RHS_HEAT1D_VARCOEF)
+    return nv_fail(NV_ENOTSUP, "float64 defects are built for the heat equations");
+  const HeatArgs a = heat_args(M);
+  const int block = 256;
+  int grid = 0;
+  nv_status st;
+#define NVPIT_DEFECT_CASE(RR)                                                                   \
+  case RR:                                                                                     \
+    st = persistent_grid(heat_defect_kernel<RR>, block, (int64_t)a.S, &grid);                  \
+    if (st != NV_OK) return st;                                                                \
+    heat_defect_kernel<RR><<<grid, block, 0, s>>>(a, lam_tilde, d);                            \
+    break;
+  switch (rows_per_lane(M->dim)) {
+    NVPIT_DEFECT_CASE(1)
+    NVPIT_DEFECT_CASE(2)
+    NVPIT_DEFECT_CASE(4)
+    NVPIT_DEFECT_CASE(8)
+    NVPIT_DEFECT_CASE(16)
+    default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
+  }
+#undef NVPIT_DEFECT_CASE
+  return nv_cuda_check(cudaGetLastError(), "heat_defect_kernel launch");
 }

@@ -94,68 +94,82 @@ __global__ void __launch_bounds__(256) affine_chain_kernel(AffineChainArgs a) {
   }
 }
 
-// Chain within one thread-block cluster (d <= 512): the C CTAs of a cluster
-// own ceil(d/C) rows each and exchange lambda through distributed shared
-// memory: after forming its rows, every CTA stores them into the next state
-// buffer of all C CTAs, then the cluster's hardware barrier (release /
-// acquire) orders the step.  No global-memory round trip, no spin loop.
-// AT is the arithmetic type of the products: double for float64 maps, float
-// for float32 maps (the float32 chain keeps its state in float).
+// Batched chains within thread-block clusters (d <= 512).  Cluster q runs
+// chain q: x <- A_j x + v_j for the slices j of that chain, where A_j is a
+// column-major d x d matrix and v_j a d-vector, both addressed by strides so
+// that the same kernel walks the slice maps ([b_j | A_j] blocks), block-total
+// matrices, or separate correction vectors.  The C CTAs of a cluster own
+// ceil(d/C) rows each and exchange x through distributed shared memory:
+// after forming its rows, every CTA stores them into the next state buffer of
+// all C CTAs, then the cluster's hardware barrier (release / acquire) orders
+// the step.  No global-memory round trip, no spin loop.  AT is the arithmetic
+// type: double for float64 maps, float for float32 maps.
+
 template <typename MT, typename AT>
-__global__ void __launch_bounds__(256) affine_chain_cluster_kernel(AffineChainArgs a) {
+__global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+  const int q = (int)(blockIdx.x / csize);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = a.n, rpc = a.rpc, ld = n + 1;
-  AT* xs = reinterpret_cast<AT*>(smem_raw);          // two buffers of n+1, xs[.][0] = 1
-  AT* red = xs + 2 * ld;                              // blockDim partial sums
+  const int n = a.n, rpc = a.rpc;
+  AT* xs = reinterpret_cast<AT*>(smem_raw);           // two state buffers of n
+  AT* red = xs + 2 * n;                                // blockDim partial sums
   const int tid = threadIdx.x;
   const int r = tid % rpc, cgi = tid / rpc, ncg = blockDim.x / rpc;
   const int row = (int)rank * rpc + r;
   const bool active = (cgi < ncg) && (row < n);
-  const MT* maps = reinterpret_cast<const MT*>(a.maps);
-  const int64_t slice_elems = (int64_t)n * (n + 1);
+  const MT* Ab = reinterpret_cast<const MT*>(a.A);
+  const int j0 = q * a.len;
+  const int len = min(a.len, a.S - j0);
 
-  for (int i = tid; i < n; i += blockDim.x) xs[1 + i] = (AT)a.y0[i];
-  if (tid == 0) { xs[0] = (AT)1; xs[ld] = (AT)1; }
-  if (rank == 0 && a.lambdas)
-    for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i];
+  const double* x0 = a.x0 ? a.x0 + (int64_t)q * a.x0_stride : nullptr;
+  for (int i = tid; i < n; i += blockDim.x) xs[i] = x0 ? (AT)x0[i] : (AT)0;
+  if (q == 0 && rank == 0 && a.write_state0 && a.states)
+    for (int i = tid; i < n; i += blockDim.x)
+      a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
 
   MT pre[kPre];
   auto prefetch = [&](int k) {
-    const MT* A = maps + (int64_t)k * slice_elems;
+    const MT* A = Ab + (int64_t)(j0 + k) * a.a_stride;
 #pragma unroll
-    for (int q = 0; q < kPre; ++q) {
-      const int c = cgi + q * ncg;
-      pre[q] = (active && c <= n) ? __ldcs(A + (int64_t)c * n + row) : (MT)0;
+    for (int qq = 0; qq < kPre; ++qq) {
+      const int c = cgi + qq * ncg;
+      pre[qq] = (active && c < n) ? __ldcs(A + (int64_t)c * n + row) : (MT)0;
     }
   };
-  prefetch(0);
-  cl.sync();   // every CTA's buffer 0 is initialised before anyone writes buffer 1
+  if (len > 0) prefetch(0);
+  cl.sync();   // every CTA's first buffer is initialised before anyone writes the second
 
-  for (int k = 0; k < a.S; ++k) {
-    const AT* x = xs + (k & 1) * ld;
+  for (int k = 0; k < len; ++k) {
+    const int j = j0 + k;
+    const AT* x = xs + (k & 1) * n;
     AT acc = 0;
     if (active) {
 #pragma unroll
-      for (int q = 0; q < kPre; ++q) {
-        const int c = cgi + q * ncg;
-        if (c <= n) acc = fma((AT)pre[q], x[c], acc);
+      for (int qq = 0; qq < kPre; ++qq) {
+        const int c = cgi + qq * ncg;
+        if (c < n) acc = fma((AT)pre[qq], x[c], acc);
       }
-      const MT* A = maps + (int64_t)k * slice_elems;
-      for (int c = cgi + kPre * ncg; c <= n; c += ncg)
+      const MT* A = Ab + (int64_t)j * a.a_stride;
+      for (int c = cgi + kPre * ncg; c < n; c += ncg)
         acc = fma((AT)__ldcs(A + (int64_t)c * n + row), x[c], acc);
     }
     red[tid] = acc;
-    if (k + 1 < a.S) prefetch(k + 1);
+    if (k + 1 < len) prefetch(k + 1);
     __syncthreads();
     if (tid < rpc && row < n) {
-      AT v = 0;
-      for (int g = 0; g < ncg; ++g) v += red[g * rpc + tid];
-      const int nb = ((k + 1) & 1) * ld + 1 + row;
-      for (unsigned p = 0; p < csize; ++p) cl.map_shared_rank(xs, p)[nb] = v;
-      if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row] = (double)v;
-      if (k == a.S - 1) a.yT[row] = (double)v;
+      AT s = 0;
+      for (int g = 0; g < ncg; ++g) s += red[g * rpc + tid];
+      AT vj = a.v_double ? (AT)(reinterpret_cast<const double*>(a.v)[(int64_t)j * a.v_stride + row])
+                         : (AT)(reinterpret_cast<const MT*>(a.v)[(int64_t)j * a.v_stride + row]);
+      s += vj;
+      const int nb = ((k + 1) & 1) * n + row;
+      for (unsigned p = 0; p < csize; ++p) cl.map_shared_rank(xs, p)[nb] = s;
+      const int64_t o = (int64_t)(j + 1) * n + row;
+      const double out = (double)s + (a.add ? a.add[o] : 0.0);
+      if (a.states) a.states[o] = out;
+      if (a.yT && j == a.S - 1) a.yT[row] = out;
+      if (a.finals && k == len - 1) a.finals[(int64_t)q * n + row] = (double)s;
     }
     cl.sync();
   }
@@ -165,25 +179,24 @@ __global__ void __launch_bounds__(256) affine_chain_cluster_kernel(AffineChainAr
 
 using namespace nvpit;
 
-// One cluster of up to 16 CTAs for d <= 512; returns NV_ENOTSUP if the device
-// cannot hold such a cluster (the caller then takes the grid-wide chain).
-static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0, double* yT,
-                                             double* lambdas, cudaStream_t s, int want_csize) {
-  const int n = M->dim;
+// Launch nchains clusters of up to `want_csize` CTAs (0 = as large as fits,
+// up to 16); NV_ENOTSUP if no cluster shape fits the device.
+nv_status launch_chains(const ChainsArgs& args_in, bool f64, cudaStream_t s, int want_csize) {
+  const int n = args_in.n;
   const int block = 256;
-  const bool f64 = M->prec == NV_FP64;
-  const void* fn = f64 ? (const void*)affine_chain_cluster_kernel<double, double>
-                       : (const void*)affine_chain_cluster_kernel<float, float>;
+  if (n > 512) return nv_fail(NV_ENOTSUP, "cluster chains need d <= 512");
+  const void* fn = f64 ? (const void*)affine_chains_kernel<double, double>
+                       : (const void*)affine_chains_kernel<float, float>;
   const size_t esz = f64 ? sizeof(double) : sizeof(float);
-  const size_t smem = esz * (2 * (size_t)(n + 1) + block);
+  const size_t smem = esz * (2 * (size_t)n + block);
   nv_status st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                                "cluster size attribute");
   if (st != NV_OK) return st;
-  for (int csize = want_csize > 0 ? want_csize : 16; csize >= 2; csize /= 2) {
+  for (int csize = want_csize > 0 ? want_csize : 16; csize >= 1; csize /= 2) {
     const int rpc = (n + csize - 1) / csize;
     if (rpc > block) break;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(csize);
+    cfg.gridDim = dim3((unsigned)(csize * args_in.nchains));
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -199,19 +212,33 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
       cudaGetLastError();
       continue;
     }
-    AffineChainArgs a{};
-    a.maps = M->data;
-    a.n = n;
-    a.S = M->S;
+    ChainsArgs a = args_in;
     a.rpc = rpc;
-    a.y0 = y0;
-    a.yT = yT;
-    a.lambdas = lambdas;
-    a.status = M->status;
     void* args[] = {&a};
-    return nv_cuda_check(cudaLaunchKernelExC(&cfg, fn, args), "affine_chain_cluster_kernel launch");
+    return nv_cuda_check(cudaLaunchKernelExC(&cfg, fn, args), "affine_chains_kernel launch");
   }
   return nv_fail(NV_ENOTSUP, "no cluster configuration fits the chain");
+}
+
+static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0, double* yT,
+                                             double* lambdas, cudaStream_t s, int want_csize) {
+  const int n = M->dim;
+  const bool f64 = M->prec == NV_FP64;
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  ChainsArgs a{};
+  a.n = n;
+  a.nchains = 1;
+  a.len = M->S;
+  a.S = M->S;
+  a.A = static_cast<const char*>(M->data) + esz * n;   // column 1 of slice 0's block
+  a.a_stride = (int64_t)n * (n + 1);
+  a.v = M->data;                                       // column 0 = b_j
+  a.v_stride = (int64_t)n * (n + 1);
+  a.x0 = y0;
+  a.states = lambdas;
+  a.yT = yT;
+  a.write_state0 = 1;
+  return launch_chains(a, f64, s, want_csize);
 }
 
 nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,

@@ -72,11 +72,33 @@ nv_status launch_serial_fine(int32_t rhs_kind, int32_t dim, const double* params
 nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
                              cudaStream_t s);
 
+// Batched cluster chains (compose.cu, affine_chains_kernel): chain q runs
+// x <- A_j x + v_j over slices j = q*len .. min(S, (q+1)*len) - 1.
+struct ChainsArgs {
+  int n, nchains, len, S, rpc;
+  const void* A;          // A_j = A + j * a_stride (elements of MT), column-major, ld n
+  int64_t a_stride;
+  const void* v;          // v_j = v + j * v_stride (elements of MT, or double if v_double)
+  int64_t v_stride;
+  int v_double;
+  const double* x0;       // start of chain q: x0 + q * x0_stride; NULL = zero
+  int64_t x0_stride;
+  double* states;         // optional: states[(j+1)*n + i] = x after slice j (+ add)
+  double* finals;         // optional: finals[q*n + i] = x at the end of chain q
+  const double* add;      // optional: added to x when writing states / yT
+  double* yT;             // optional: x after the last slice S-1 (+ add)
+  int write_state0;       // chain 0 also writes states[0..n) = x0 (+ add)
+};
+
+nv_status launch_chains(const ChainsArgs& args, bool f64, cudaStream_t s, int want_csize);
+nv_status launch_heat_defect(const nv_maps* M, const double* lam_tilde, double* d, cudaStream_t s);
+
 // Tunables (set by nv_tune_set, read by the launchers).
 struct nv_tunables {
   int table_block;         // threads per CTA for the table build
   int chain_rows_per_cta;  // rows of the chain GEMV owned by one CTA
   int affine_warps;        // warps per CTA in the affine build
   int chain_cluster;       // CTAs per cluster of the d <= 512 chain (0 auto, < 0 grid-wide)
+  int scan_block;          // slices per block of the tensor-core scan (0 auto)
 };
 extern nv_tunables g_tune;

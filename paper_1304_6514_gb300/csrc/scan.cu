@@ -1,7 +1,514 @@
-// Reduced-precision composition (NV_TF32_REFINE): placeholder until the
-// tensor-core scan lands.
-#include "internal.h"
+// Reduced-precision composition with float64 refinement (NV_TF32_REFINE).
+//
+// The communication phase of Figure "pseudocode" is a chain of S dependent
+// affine steps.  Affine maps compose associatively, (A2,b2)o(A1,b1) =
+// (A2 A1, A2 b1 + b2), so the chain can be cut into B blocks of L slices:
+//   A  block totals   R_b = A_{bL+L-1} ... A_{bL}      tcgen05 TF32 GEMMs
+//   B  block vectors  c_b = chain of block b from 0    batched cluster chains
+//   C  block chain    Lam_b = R_b Lam_{b-1} + c_b      one cluster chain, B steps
+//   D  block states   lt_j: chain of block b from Lam_{b-1}   batched chains
+// and the sequential depth drops from S to 2L + B.  The float32 maps and the
+// TF32 products carry ~1e-3 relative error, which one float64 residual
+// correction removes (the parareal-style combination the Conclusion
+// proposes, with the reduced-precision maps as the coarse propagator):
+//   E  d_j = g^j(lt_j) - lt_{j+1}       float64 fine solve from lt_j per slice
+//   F, G, H  the same block scheme on e_{j+1} = A_j e_j + d_j, e_0 = 0
+//   lambda_j = lt_j + e_j.
+//
+// Block-total kernel (phase A): CTA (h, b) owns rows [128h, 128h+128) of the
+// running suffix product R <- R A_j (j from the block's last slice down), so
+// the row halves never exchange data.  R's rows stay in shared memory as the
+// K-major A operand (128B-swizzled, 1024-byte atoms).  Each A_j is stored
+// column-major in HBM, which is exactly the K-major layout of the B operand;
+// TMA streams it in K-slabs of 32 (256 x 128 B boxes, SWIZZLE_128B) through a
+// two-stage mbarrier ring.  One thread issues tcgen05.mma (kind::tf32,
+// M=128, N=256, K=8) into a 128 x 256 float32 accumulator in tensor memory;
+// four warps read it back with tcgen05.ld and write the next A operand (or,
+// after the last slice, the block total to global memory).  Every mbarrier
+// wait is bounded (1 s of globaltimer), after which the kernel records
+// NV_ETIMEOUT, waits (bounded) for its copies in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
 
-nv_status launch_scan_refine(nv_maps*, const double*, double*, double*, cudaStream_t) {
-  return nv_fail(NV_ENOTSUP, "TF32 scan composition is not built yet");
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace nvpit {
+namespace tc {
+
+constexpr int kRows = 128;              // rows of R per CTA (UMMA M)
+constexpr int kN = 256;                 // UMMA N (padded d)
+constexpr int kSlab = 32;               // K per TMA box / swizzle atom (128 B of tf32)
+constexpr int kSlabBytesA = kRows * 128;
+constexpr int kSlabBytesB = kN * 128;
+constexpr int kStages = 2;
+constexpr int kMaxSlabs = 8;            // d <= 256
+constexpr int kSmemA = kMaxSlabs * kSlabBytesA;          // 128 KB
+constexpr int kSmemB = kStages * kSlabBytesB;            // 64 KB
+constexpr int kSmemBytes = kSmemA + kSmemB + 128 + 1024; // + barriers + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Wait for the phase with the given parity; gives up after 1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.b32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D float32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0;"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive float32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct ScanArgs {
+  int n, S, L, nblocks, nslabs;
+  float* R;        // nblocks x n x n, column-major block totals
+  int* status;
+};
+
+// Row m of the K-major A operand, 32 floats of slab s, 128B-swizzled.
+__device__ __forceinline__ float4* arow_chunk(uint8_t* aop, int s, int m, int chunk) {
+  return reinterpret_cast<float4*>(aop + s * kSlabBytesA + m * 128 + ((chunk ^ (m & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(128, 1)
+    scan_block_totals_kernel(const __grid_constant__ CUtensorMap tmB, ScanArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* aop = base;
+  uint8_t* bst = base + kSmemA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + kSmemA + kSmemB);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int h = blockIdx.x, blk = blockIdx.y;
+  const int n = a.n;
+  const int j0 = blk * a.L;
+  const int len = min(a.L, a.S - j0);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // A operand = rows [128h, 128h+128) of the identity (zero beyond d)
+  {
+    const int m = tid;                      // 128 threads, one row each
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < kMaxSlabs; ++s)
+      for (int c = 0; c < 8; ++c) *arow_chunk(aop, s, m, c) = z;
+    const int gm = kRows * h + m;
+    if (gm < n) {
+      const int s = gm / kSlab, kk = gm % kSlab;
+      float* p = reinterpret_cast<float*>(arow_chunk(aop, s, m, kk >> 2));
+      p[kk & 3] = 1.0f;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_tf32(kRows, kN);
+  const uint32_t aop_addr = smem_u32(aop), bst_addr = smem_u32(bst);
+
+  uint32_t fph[kStages] = {0, 0}, eph[kStages] = {0, 0}, dph = 0;
+  bool pending[kStages] = {false, false};
+  bool ok = true;
+  for (int step = 0; step < len && !abort_flag; ++step) {
+    const int j = j0 + len - 1 - step;      // suffix product: last slice of the block first
+    if (tid == 0) {
+      const int ns = a.nslabs;
+      for (int s = 0; s < min(kStages, ns); ++s) {
+        mbar_expect_tx(&full[s], kSlabBytesB);
+        tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j);
+        pending[s] = true;
+      }
+      for (int s = 0; s < ns && ok; ++s) {
+        const int st = s % kStages;
+        ok = mbar_wait(&full[st], fph[st]);
+        fph[st] ^= 1;
+        pending[st] = false;
+        if (!ok) break;
+        fence_after();
+#pragma unroll
+        for (int kk = 0; kk < kSlab / 8; ++kk) {
+          const uint64_t ad = sdesc_k_sw128(aop_addr + s * kSlabBytesA + kk * 32);
+          const uint64_t bd = sdesc_k_sw128(bst_addr + st * kSlabBytesB + kk * 32);
+          mma_tf32(tmem, ad, bd, idesc, (s | kk) != 0);
+        }
+        mma_commit(&empty[st]);
+        if (s + kStages < ns) {
+          ok = mbar_wait(&empty[st], eph[st]);
+          eph[st] ^= 1;
+          if (!ok) break;
+          mbar_expect_tx(&full[st], kSlabBytesB);
+          tma_load_3d(bst + st * kSlabBytesB, &tmB, &full[st], (s + kStages) * kSlab, 1, j);
+          pending[st] = true;
+        }
+      }
+      if (ok) {
+        mma_commit(done);
+        // the last stages' release arrivals complete with the MMAs
+        for (int s = max(0, ns - kStages); s < ns && ok; ++s) {
+          const int st = s % kStages;
+          ok = mbar_wait(&empty[st], eph[st]);
+          eph[st] ^= 1;
+        }
+      }
+      if (!ok) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    if (!mbar_wait(done, dph)) {
+      abort_flag = 1;
+    }
+    dph ^= 1;
+    __syncthreads();
+    if (abort_flag) break;
+    fence_after();
+    // epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w+31
+    const int m = warp * 32 + lane;
+    const int gm = kRows * h + m;
+    const bool last = (step == len - 1);
+    for (int s = 0; s < a.nslabs; ++s) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kSlab), v);
+      if (!last) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *arow_chunk(aop, s, m, c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+      } else if (gm < n) {
+        float* Rb = a.R + (int64_t)blk * n * n;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = s * kSlab + i;
+          if (col < n) Rb[(int64_t)col * n + gm] = v[i];
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      record_status(a.status, NV_ETIMEOUT);
+      for (int st = 0; st < kStages; ++st)   // let copies in flight land (bounded)
+        if (pending[st]) mbar_wait(&full[st], fph[st]);
+    }
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN) : "memory");
+}
+
+}  // namespace tc
+}  // namespace nvpit
+
+using namespace nvpit;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static nv_status encode_fn(EncodeTiledFn* out) {
+  static std::mutex mu;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    nv_status st = nv_cuda_check(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                                  cudaEnableDefault, &q),
+                                 "driver entry point cuTensorMapEncodeTiled");
+    if (st != NV_OK) return st;
+    if (q != cudaDriverEntryPointSuccess || !p)
+      return nv_fail(NV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *out = fn;
+  return NV_OK;
+}
+
+// Scratch of the refined composition, carved from one allocation.
+struct ScanScratch {
+  float* R;
+  double *cvec, *lam, *lt, *d, *cpr, *E;
+};
+
+static size_t scan_scratch_bytes(int n, int S, int B) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t b = al(sizeof(float) * (size_t)B * n * n);
+  b += al(sizeof(double) * (size_t)B * n) * 2;         // cvec, cpr
+  b += al(sizeof(double) * (size_t)(B + 1) * n) * 2;   // lam, E
+  b += al(sizeof(double) * (size_t)(S + 1) * n);        // lt
+  b += al(sizeof(double) * (size_t)S * n);              // d
+  return b;
+}
+
+static ScanScratch carve(void* p, int n, int S, int B) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* c = static_cast<char*>(p);
+  ScanScratch s;
+  s.R = reinterpret_cast<float*>(c);
+  c += al(sizeof(float) * (size_t)B * n * n);
+  s.cvec = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)B * n);
+  s.cpr = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)B * n);
+  s.lam = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)(B + 1) * n);
+  s.E = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)(B + 1) * n);
+  s.lt = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)(S + 1) * n);
+  s.d = reinterpret_cast<double*>(c);
+  return s;
+}
+
+static int pow2_floor(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
+  const int n = M->dim, S = M->S;
+  if (M->rhs_kind != NV_RHS_HEAT1D && M->rhs_kind != NV_RHS_HEAT1D_VARCOEF)
+    return nv_fail(NV_ENOTSUP, "refined tensor-core composition is built for the heat equations");
+  if (n > tc::kN || n % 4 != 0)
+    return nv_fail(NV_ENOTSUP, "tensor-core scan needs d <= 256 and d a multiple of 4 (d = %d)", n);
+  int L = g_tune.scan_block > 0 ? g_tune.scan_block : (int)lround(sqrt((double)S));
+  L = std::max(1, std::min(L, S));
+  const int B = (S + L - 1) / L;
+
+  const size_t need = scan_scratch_bytes(n, S, B);
+  if (M->scan_ws_bytes < need) {
+    if (M->scan_ws) {
+      cudaStreamSynchronize(s);
+      cudaFree(M->scan_ws);
+      M->scan_ws = nullptr;
+      M->scan_ws_bytes = 0;
+    }
+    nv_status st = nv_cuda_check(cudaMalloc(&M->scan_ws, need), "scan scratch allocation");
+    if (st != NV_OK) return st;
+    M->scan_ws_bytes = need;
+  }
+  const ScanScratch sc = carve(M->scan_ws, n, S, B);
+
+  // TMA view of the float32 maps: (row i: d, column c: d+1, slice j: S); a box
+  // of 32 rows x 256 columns of one slice is one K-slab of A_j (columns 1..d).
+  EncodeTiledFn enc = nullptr;
+  nv_status st = encode_fn(&enc);
+  if (st != NV_OK) return st;
+  CUtensorMap tmap;
+  const cuuint64_t gdim[3] = {(cuuint64_t)n, (cuuint64_t)(n + 1), (cuuint64_t)S};
+  const cuuint64_t gstride[2] = {(cuuint64_t)n * 4, (cuuint64_t)n * (n + 1) * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)tc::kSlab, (cuuint32_t)tc::kN, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, M->data, gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return nv_fail(NV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+
+  // A: block totals on the tensor cores
+  tc::ScanArgs sa{};
+  sa.n = n;
+  sa.S = S;
+  sa.L = L;
+  sa.nblocks = B;
+  sa.nslabs = (n + tc::kSlab - 1) / tc::kSlab;
+  sa.R = sc.R;
+  sa.status = M->status;
+  st = nv_cuda_check(cudaFuncSetAttribute(tc::scan_block_totals_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes),
+                     "scan smem attribute");
+  if (st != NV_OK) return st;
+  const int halves = (n + tc::kRows - 1) / tc::kRows;
+  tc::scan_block_totals_kernel<<<dim3(halves, B), 128, tc::kSmemBytes, s>>>(tmap, sa);
+  st = nv_cuda_check(cudaGetLastError(), "scan_block_totals_kernel launch");
+  if (st != NV_OK) return st;
+
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int cs_many = std::max(1, std::min(16, pow2_floor(std::max(1, sms / B))));
+  const float* mapsf = static_cast<const float*>(M->data);
+  const int64_t bs = (int64_t)n * (n + 1);
+
+  ChainsArgs blockc{};            // chains over the slices of each block
+  blockc.n = n;
+  blockc.nchains = B;
+  blockc.len = L;
+  blockc.S = S;
+  blockc.A = mapsf + n;
+  blockc.a_stride = bs;
+
+  ChainsArgs topc{};              // one chain over the block totals
+  topc.n = n;
+  topc.nchains = 1;
+  topc.len = B;
+  topc.S = B;
+  topc.A = sc.R;
+  topc.a_stride = (int64_t)n * n;
+  topc.v_double = 1;
+  topc.v_stride = n;
+  topc.write_state0 = 1;
+
+  // B: block vectors from zero
+  ChainsArgs cb = blockc;
+  cb.v = mapsf;
+  cb.v_stride = bs;
+  cb.finals = sc.cvec;
+  if ((st = launch_chains(cb, false, s, cs_many)) != NV_OK) return st;
+  // C: Lam_b
+  ChainsArgs cc = topc;
+  cc.v = sc.cvec;
+  cc.x0 = y0;
+  cc.states = sc.lam;
+  if ((st = launch_chains(cc, false, s, 16)) != NV_OK) return st;
+  // D: approximate boundary states lt
+  ChainsArgs cd = blockc;
+  cd.v = mapsf;
+  cd.v_stride = bs;
+  cd.x0 = sc.lam;
+  cd.x0_stride = n;
+  cd.states = sc.lt;
+  cd.write_state0 = 1;
+  if ((st = launch_chains(cd, false, s, cs_many)) != NV_OK) return st;
+  // E: float64 defects
+  if ((st = launch_heat_defect(M, sc.lt, sc.d, s)) != NV_OK) return st;
+  // F: correction block vectors from zero
+  ChainsArgs cf = blockc;
+  cf.v = sc.d;
+  cf.v_double = 1;
+  cf.v_stride = n;
+  cf.finals = sc.cpr;
+  if ((st = launch_chains(cf, false, s, cs_many)) != NV_OK) return st;
+  // G: correction at block ends
+  ChainsArgs cgc = topc;
+  cgc.v = sc.cpr;
+  cgc.states = sc.E;
+  if ((st = launch_chains(cgc, false, s, 16)) != NV_OK) return st;
+  // H: e_j inside the blocks; lambda_j = lt_j + e_j
+  ChainsArgs ch = blockc;
+  ch.v = sc.d;
+  ch.v_double = 1;
+  ch.v_stride = n;
+  ch.x0 = sc.E;
+  ch.x0_stride = n;
+  ch.states = lambdas;
+  ch.add = sc.lt;
+  ch.yT = yT;
+  ch.write_state0 = 1;
+  return launch_chains(ch, false, s, cs_many);
 }
