@@ -85,9 +85,11 @@ typedef enum {
 typedef enum {
   NV_FP64 = 0,             /* integrate and store in float64                           */
   NV_FP32 = 1,             /* integrate and store in float32                           */
-  NV_TF32_REFINE = 2       /* affine only: float32 maps, composition on tcgen05 tensor
-                              cores in TF32 with float32 accumulation, then one float64
-                              residual-correction pass                                  */
+  NV_TF32_REFINE = 2       /* affine only: maps integrated in float32 and stored rounded
+                              to TF32 (float32 containers, 11 significant bits; the
+                              forcing column b_j keeps float32), composition on tcgen05
+                              tensor cores in TF32 with float32 accumulation, then one
+                              float64 residual-correction pass                          */
 } nv_precision;
 
 typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;

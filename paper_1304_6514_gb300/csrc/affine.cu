@@ -152,7 +152,7 @@ __device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double t, doub
 
 // Homogeneous columns of a time-invariant operator (c = 1..d): Horner-form
 // RK4 only, so a thread holds just y and v (2R values) and many warps fit.
-template <typename T, int R>
+template <typename T, int R, bool TF32OUT>
 __global__ void __launch_bounds__(256) heat_horner_kernel(HeatArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(256) heat_horner_kernel(HeatArgs a) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int r = lane * R + i;
-      if (r < n) col[r] = y[i];
+      if constexpr (TF32OUT) {
+        if (r < n) col[r] = round_tf32(y[i]);
+      } else {
+        if (r < n) col[r] = y[i];
+      }
     }
   }
 }
@@ -330,7 +334,7 @@ static nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* g
 }
 
 template <typename T, int R>
-static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s) {
+static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) {
   const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
   const int block = 32 * warps_per_cta;
   int grid = 0;
@@ -346,20 +350,28 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s) {
   heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
   st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   if (st != NV_OK) return st;
-  st = persistent_grid(heat_horner_kernel<T, R>, block, (int64_t)a.S * a.n, &grid);
+  if constexpr (sizeof(T) == 4) {
+    if (tf32out) {
+      st = persistent_grid(heat_horner_kernel<T, R, true>, block, (int64_t)a.S * a.n, &grid);
+      if (st != NV_OK) return st;
+      heat_horner_kernel<T, R, true><<<grid, block, 0, s>>>(a);
+      return nv_cuda_check(cudaGetLastError(), "heat_horner_kernel launch");
+    }
+  }
+  st = persistent_grid(heat_horner_kernel<T, R, false>, block, (int64_t)a.S * a.n, &grid);
   if (st != NV_OK) return st;
-  heat_horner_kernel<T, R><<<grid, block, 0, s>>>(a);
+  heat_horner_kernel<T, R, false><<<grid, block, 0, s>>>(a);
   return nv_cuda_check(cudaGetLastError(), "heat_horner_kernel launch");
 }
 
 template <typename T>
-static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s) {
+static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s, bool tf32out) {
   switch (R) {
-    case 1: return launch_heat_R<T, 1>(a, s);
-    case 2: return launch_heat_R<T, 2>(a, s);
-    case 4: return launch_heat_R<T, 4>(a, s);
-    case 8: return launch_heat_R<T, 8>(a, s);
-    case 16: return launch_heat_R<T, 16>(a, s);
+    case 1: return launch_heat_R<T, 1>(a, s, tf32out);
+    case 2: return launch_heat_R<T, 2>(a, s, tf32out);
+    case 4: return launch_heat_R<T, 4>(a, s, tf32out);
+    case 8: return launch_heat_R<T, 8>(a, s, tf32out);
+    case 16: return launch_heat_R<T, 16>(a, s, tf32out);
     default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", a.n);
   }
 }
@@ -370,8 +382,8 @@ nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
     const int R = rows_per_lane(M->dim);
     if (R == 0) return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
     const HeatArgs a = heat_args(M);
-    if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s);
-    return launch_heat_typed<float>(a, R, s);
+    if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s, false);
+    return launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE);
   }
   return nv_fail(NV_ENOTSUP, "affine maps are not built for rhs kind %d", M->rhs_kind);
 }

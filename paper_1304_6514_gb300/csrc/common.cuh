@@ -48,6 +48,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
   return *smem_flag != 0;
 }
 
+// Round a float32 to the nearest TF32 value (10 explicit mantissa bits, ties
+// away from zero).  Tensor cores read TF32 operands by dropping the low 13
+// bits; feeding them values that are already rounded keeps the operand error
+// unbiased instead of always toward zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------------------
 // Right-hand sides of the table workloads, f(c, y) with c a staged
 // time-dependent coefficient (cos t for the cos-cubic problem).

@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(128, 1)
       if (!last) {
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-          *arow_chunk(aop, s, m, c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+          *arow_chunk(aop, s, m, c) = make_float4(round_tf32(v[4 * c]), round_tf32(v[4 * c + 1]),
+                                                  round_tf32(v[4 * c + 2]), round_tf32(v[4 * c + 3]));
       } else if (gm < n) {
         float* Rb = a.R + (int64_t)blk * n * n;
 #pragma unroll
