@@ -231,6 +231,8 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
  *          fits, up to 16; a negative value selects the grid-wide chain)
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
+ *   key 5: float64 correction passes of NV_TF32_REFINE (default 0 = one pass;
+ *          a negative value returns the unrefined tensor-core states)
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 

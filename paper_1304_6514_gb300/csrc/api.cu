@@ -15,7 +15,7 @@ nv_status launch_serial_table(int32_t rhs_kind, const double* params, double t0,
                               double* yT, cudaStream_t s);
 nv_status launch_serial_heat(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 
-nv_tunables g_tune = {0, 0, 0, 0, 0};
+nv_tunables g_tune = {0, 0, 0, 0, 0, 0};
 
 static thread_local char g_err[512] = "";
 
@@ -353,6 +353,7 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 2: g_tune.affine_warps = value; break;
     case 3: g_tune.chain_cluster = value; break;
     case 4: g_tune.scan_block = value; break;
+    case 5: g_tune.refine_passes = value; break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }
   return NV_OK;

@@ -343,7 +343,7 @@ static nv_status encode_fn(EncodeTiledFn* out) {
 // Scratch of the refined composition, carved from one allocation.
 struct ScanScratch {
   float* R;
-  double *cvec, *lam, *lt, *d, *cpr, *E;
+  double *cvec, *lam, *lt, *lt2, *d, *cpr, *E;
 };
 
 static size_t scan_scratch_bytes(int n, int S, int B) {
@@ -351,7 +351,7 @@ static size_t scan_scratch_bytes(int n, int S, int B) {
   size_t b = al(sizeof(float) * (size_t)B * n * n);
   b += al(sizeof(double) * (size_t)B * n) * 2;         // cvec, cpr
   b += al(sizeof(double) * (size_t)(B + 1) * n) * 2;   // lam, E
-  b += al(sizeof(double) * (size_t)(S + 1) * n);        // lt
+  b += al(sizeof(double) * (size_t)(S + 1) * n) * 2;    // lt, lt2
   b += al(sizeof(double) * (size_t)S * n);              // d
   return b;
 }
@@ -371,6 +371,8 @@ static ScanScratch carve(void* p, int n, int S, int B) {
   s.E = reinterpret_cast<double*>(c);
   c += al(sizeof(double) * (size_t)(B + 1) * n);
   s.lt = reinterpret_cast<double*>(c);
+  c += al(sizeof(double) * (size_t)(S + 1) * n);
+  s.lt2 = reinterpret_cast<double*>(c);
   c += al(sizeof(double) * (size_t)(S + 1) * n);
   s.d = reinterpret_cast<double*>(c);
   return s;
@@ -486,30 +488,48 @@ nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* l
   cd.states = sc.lt;
   cd.write_state0 = 1;
   if ((st = launch_chains(cd, false, s, cs_many)) != NV_OK) return st;
-  // E: float64 defects
-  if ((st = launch_heat_defect(M, sc.lt, sc.d, s)) != NV_OK) return st;
-  // F: correction block vectors from zero
-  ChainsArgs cf = blockc;
-  cf.v = sc.d;
-  cf.v_double = 1;
-  cf.v_stride = n;
-  cf.finals = sc.cpr;
-  if ((st = launch_chains(cf, false, s, cs_many)) != NV_OK) return st;
-  // G: correction at block ends
-  ChainsArgs cgc = topc;
-  cgc.v = sc.cpr;
-  cgc.states = sc.E;
-  if ((st = launch_chains(cgc, false, s, 16)) != NV_OK) return st;
-  // H: e_j inside the blocks; lambda_j = lt_j + e_j
-  ChainsArgs ch = blockc;
-  ch.v = sc.d;
-  ch.v_double = 1;
-  ch.v_stride = n;
-  ch.x0 = sc.E;
-  ch.x0_stride = n;
-  ch.states = lambdas;
-  ch.add = sc.lt;
-  ch.yT = yT;
-  ch.write_state0 = 1;
-  return launch_chains(ch, false, s, cs_many);
+  // E-H: float64 correction passes (tunable; 0 returns the unrefined states)
+  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes
+                     : (g_tune.refine_passes < 0 ? 0 : 1);
+  const double* cur = sc.lt;
+  if (passes == 0) {
+    if (lambdas &&
+        (st = nv_cuda_check(cudaMemcpyAsync(lambdas, sc.lt, sizeof(double) * (size_t)(S + 1) * n,
+                                            cudaMemcpyDeviceToDevice, s), "states copy")) != NV_OK)
+      return st;
+    return nv_cuda_check(cudaMemcpyAsync(yT, sc.lt + (size_t)S * n, sizeof(double) * n,
+                                         cudaMemcpyDeviceToDevice, s), "final state copy");
+  }
+  for (int p = 0; p < passes; ++p) {
+    const bool lastp = (p == passes - 1);
+    double* out = lastp ? lambdas : (cur == sc.lt ? sc.lt2 : sc.lt);
+    // E: float64 defects d_j = g^j(cur_j) - cur_{j+1}
+    if ((st = launch_heat_defect(M, cur, sc.d, s)) != NV_OK) return st;
+    // F: correction block vectors from zero
+    ChainsArgs cf = blockc;
+    cf.v = sc.d;
+    cf.v_double = 1;
+    cf.v_stride = n;
+    cf.finals = sc.cpr;
+    if ((st = launch_chains(cf, false, s, cs_many)) != NV_OK) return st;
+    // G: correction at block ends
+    ChainsArgs cgc = topc;
+    cgc.v = sc.cpr;
+    cgc.states = sc.E;
+    if ((st = launch_chains(cgc, false, s, 16)) != NV_OK) return st;
+    // H: e_j inside the blocks; lambda_j = cur_j + e_j
+    ChainsArgs ch = blockc;
+    ch.v = sc.d;
+    ch.v_double = 1;
+    ch.v_stride = n;
+    ch.x0 = sc.E;
+    ch.x0_stride = n;
+    ch.states = out;
+    ch.add = cur;
+    ch.yT = lastp ? yT : nullptr;
+    ch.write_state0 = 1;
+    if ((st = launch_chains(ch, false, s, cs_many)) != NV_OK) return st;
+    cur = out;
+  }
+  return NV_OK;
 }
