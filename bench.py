@@ -366,7 +366,7 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": None,
                      "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)",
                      "flop_per_launch": flop},
-        "gpu_launches": 2 * K,
+        "gpu_launches": 3 * K,
         "clocks": clocks,
         "variants": variants,
         "gpu_library_rates": peaks_probe,

@@ -88,8 +88,8 @@ typedef enum {
   NV_TF32_REFINE = 2       /* affine only: maps integrated in float32 and stored rounded
                               to TF32 (float32 containers, 11 significant bits; the
                               forcing column b_j keeps float32), composition on tcgen05
-                              tensor cores in TF32 with float32 accumulation, then one
-                              float64 residual-correction pass                          */
+                              tensor cores in TF32 with float32 accumulation, then
+                              float64 residual-correction passes (three by default)      */
 } nv_precision;
 
 typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;
@@ -231,8 +231,8 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
  *          fits, up to 16; a negative value selects the grid-wide chain)
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
- *   key 5: float64 correction passes of NV_TF32_REFINE (default 0 = one pass;
- *          a negative value returns the unrefined tensor-core states)
+ *   key 5: float64 correction passes of NV_TF32_REFINE (default 0 = three
+ *          passes; a negative value returns the unrefined tensor-core states)
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
