@@ -405,7 +405,7 @@ nv_status launch_heat_defect(const nv_maps* M, const double* lam_tilde, double* 
   if (M->rhs_kind != NV_RHS_HEAT1D && M->rhs_kind != NV_RHS_HEAT1D_VARCOEF)
     return nv_fail(NV_ENOTSUP, "float64 defects are built for the heat equations");
   const HeatArgs a = heat_args(M);
-  const int block = 256;
+  const int block = 64;     // two warps per CTA: one slice per warp spread over all SMs
   int grid = 0;
   nv_status st;
 #define NVPIT_DEFECT_CASE(RR)                                                                   \

@@ -128,8 +128,10 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
     for (int i = tid; i < n; i += blockDim.x)
       a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
 
-  MT pre[kPre];
-  auto prefetch = [&](int k) {
+  // Loads of A_j are independent of x: they are issued two steps ahead into
+  // two register sets, so HBM latency overlaps two cluster barriers.
+  MT pa[kPre], pb[kPre];
+  auto prefetch = [&](MT* pre, int k) {
     const MT* A = Ab + (int64_t)(j0 + k) * a.a_stride;
 #pragma unroll
     for (int qq = 0; qq < kPre; ++qq) {
@@ -137,10 +139,7 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
       pre[qq] = (active && c < n) ? __ldcs(A + (int64_t)c * n + row) : (MT)0;
     }
   };
-  if (len > 0) prefetch(0);
-  cl.sync();   // every CTA's first buffer is initialised before anyone writes the second
-
-  for (int k = 0; k < len; ++k) {
+  auto step = [&](MT* pre, int k) {
     const int j = j0 + k;
     const AT* x = xs + (k & 1) * n;
     AT acc = 0;
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
         acc = fma((AT)__ldcs(A + (int64_t)c * n + row), x[c], acc);
     }
     red[tid] = acc;
-    if (k + 1 < len) prefetch(k + 1);
+    if (k + 2 < len) prefetch(pre, k + 2);
     __syncthreads();
     if (tid < rpc && row < n) {
       AT s = 0;
@@ -172,6 +171,13 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
       if (a.finals && k == len - 1) a.finals[(int64_t)q * n + row] = (double)s;
     }
     cl.sync();
+  };
+  if (len > 0) prefetch(pa, 0);
+  if (len > 1) prefetch(pb, 1);
+  cl.sync();   // every CTA's first buffer is initialised before anyone writes the second
+  for (int k = 0; k < len; k += 2) {
+    step(pa, k);
+    if (k + 1 < len) step(pb, k + 1);
   }
 }
 

@@ -378,11 +378,6 @@ static ScanScratch carve(void* p, int n, int S, int B) {
   return s;
 }
 
-static int pow2_floor(int x) {
-  int p = 1;
-  while (p * 2 <= x) p *= 2;
-  return p;
-}
 
 nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
   const int n = M->dim, S = M->S;
@@ -441,10 +436,9 @@ nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* l
   st = nv_cuda_check(cudaGetLastError(), "scan_block_totals_kernel launch");
   if (st != NV_OK) return st;
 
-  int sms = 152, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int cs_many = std::max(1, std::min(16, pow2_floor(std::max(1, sms / B))));
+  // 16-CTA clusters keep every thread's columns inside the prefetched set
+  // (16 rows per CTA); clusters of different chains share SMs.
+  const int cs_many = 16;
   const float* mapsf = static_cast<const float*>(M->data);
   const int64_t bs = (int64_t)n * (n + 1);
 
