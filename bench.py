@@ -279,8 +279,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    import __graft_entry__
-    __graft_entry__.build()
+    from paper_1304_6514_gb300 import _build
+    _build.build()                       # quiet: stdout carries only the JSON line
     import paper_1304_6514_gb300 as nvp
     import workloads
 

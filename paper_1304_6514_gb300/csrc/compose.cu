@@ -11,8 +11,10 @@
 // warp's loads for one column are contiguous rows.  Each barrier wait is
 // bounded and records NV_ETIMEOUT instead of hanging.
 #include <cooperative_groups.h>
+#include <cuda.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -181,16 +183,218 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
   }
 }
 
+// TMA-fed variant (d <= 256, rows per CTA rpc <= 16): each CTA's rows of A_j
+// (rpc x d, one 3-D box) are copied by the tensor memory accelerator into a
+// ring of kRing shared-memory stages, kRing - 1 slices ahead, completing on an
+// mbarrier.  The copies run in the async proxy, so the release half of the
+// cluster barrier does not wait for them and HBM latency leaves the
+// dependency chain.  Stage layout: element (row r, column c) at c*rpc + r.
+constexpr int kRing = 4;
+
+__device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.b32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(cta_smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+template <typename MT, typename AT>
+__global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                ChainsArgs a, int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+  const int q = (int)(blockIdx.x / csize);
+  extern __shared__ __align__(128) unsigned char ring_smem[];
+  const int n = a.n, rpc = a.rpc;
+  const int stage_elems = rpc * n;
+  MT* ring = reinterpret_cast<MT*>(ring_smem);                          // kRing stages
+  AT* xs = reinterpret_cast<AT*>(ring + kRing * stage_elems);          // two state buffers
+  AT* red = xs + 2 * n;                                                // blockDim partials
+  uint64_t* full = reinterpret_cast<uint64_t*>(
+      ((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const int r = tid % rpc, cgi = tid / rpc, ncg = blockDim.x / rpc;
+  const int row = (int)rank * rpc + r;
+  const bool active = (cgi < ncg) && (row < n);
+  const int j0 = q * a.len;
+  const int len = min(a.len, a.S - j0);
+  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT));
+
+  if (tid == 0) {
+    for (int i = 0; i < kRing; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cta_smem_u32(&full[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int k) {   // thread 0: copy this CTA's rows of A_{j0+k}
+    const int st = k % kRing;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cta_smem_u32(&full[st])),
+                 "r"(stage_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(cta_smem_u32(ring + st * stage_elems)),
+        "l"(&tmA), "r"((int)rank * rpc), "r"(0), "r"(j0 + k), "r"(cta_smem_u32(&full[st]))
+        : "memory");
+  };
+  int issued = 0;   // copies issued so far (thread 0)
+  if (tid == 0)
+    for (; issued < min(kRing - 1, len); ++issued) issue(issued);
+
+  const double* x0 = a.x0 ? a.x0 + (int64_t)q * a.x0_stride : nullptr;
+  for (int i = tid; i < n; i += blockDim.x) xs[i] = x0 ? (AT)x0[i] : (AT)0;
+  if (q == 0 && rank == 0 && a.write_state0 && a.states)
+    for (int i = tid; i < n; i += blockDim.x)
+      a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
+  cl.sync();
+
+  int consumed = len;
+  for (int k = 0; k < len; ++k) {
+    const int j = j0 + k;
+    const int st = k % kRing;
+    if (!ring_wait(&full[st], (uint32_t)((k / kRing) & 1))) {
+      abort_flag = 1;
+      if (consumed == len) consumed = k;
+    }
+    const AT* x = xs + (k & 1) * n;
+    const MT* Aj = ring + st * stage_elems;
+    AT acc = 0;
+    if (active)
+      for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
+    red[tid] = acc;
+    __syncthreads();   // stage st fully read: it may be refilled
+    if (tid == 0 && issued < len && !abort_flag) issue(issued++);
+    if (tid < rpc && row < n) {
+      AT s = 0;
+      for (int g = 0; g < ncg; ++g) s += red[g * rpc + tid];
+      AT vj = a.v_double ? (AT)(reinterpret_cast<const double*>(a.v)[(int64_t)j * a.v_stride + row])
+                         : (AT)(reinterpret_cast<const MT*>(a.v)[(int64_t)j * a.v_stride + row]);
+      s += vj;
+      const int nb = ((k + 1) & 1) * n + row;
+      for (unsigned p = 0; p < csize; ++p) cl.map_shared_rank(xs, p)[nb] = s;
+      const int64_t o = (int64_t)(j + 1) * n + row;
+      const double out = (double)s + (a.add ? a.add[o] : 0.0);
+      if (a.states) a.states[o] = out;
+      if (a.yT && j == a.S - 1) a.yT[row] = out;
+      if (a.finals && k == len - 1) a.finals[(int64_t)q * n + row] = (double)s;
+    }
+    cl.sync();
+  }
+  if (abort_flag && tid == 0) {
+    record_status(status, NV_ETIMEOUT);
+    for (int kk = min(consumed, issued); kk < issued; ++kk)   // copies in flight (bounded waits)
+      ring_wait(&full[kk % kRing], (uint32_t)((kk / kRing) & 1));
+  }
+}
+
 }  // namespace nvpit
 
 using namespace nvpit;
 
+typedef CUresult (*EncodeTiledFnC)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+static nv_status chain_encode_fn(EncodeTiledFnC* out) {
+  static std::mutex mu;
+  static EncodeTiledFnC fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    nv_status st = nv_cuda_check(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                                  cudaEnableDefault, &qr),
+                                 "driver entry point cuTensorMapEncodeTiled");
+    if (st != NV_OK) return st;
+    if (qr != cudaDriverEntryPointSuccess || !p)
+      return nv_fail(NV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<EncodeTiledFnC>(p);
+  }
+  *out = fn;
+  return NV_OK;
+}
+
 // Launch nchains clusters of up to `want_csize` CTAs (0 = as large as fits,
 // up to 16); NV_ENOTSUP if no cluster shape fits the device.
+// TMA-fed chains: 16-CTA clusters, 16 rows per CTA (d <= 256, d % 4 == 0,
+// 16-byte aligned matrices and strides).  NV_ENOTSUP if the shape or device
+// does not allow it (the caller then takes the register-prefetch kernel).
+static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStream_t s, int* status) {
+  const int n = args_in.n;
+  const int block = 256, csize = 16, rpc = 16;
+  const size_t esz = f64 ? 8 : 4;
+  if (n > 256 || n < 64 || n % 16 != 0) return NV_ENOTSUP;
+  if (((uintptr_t)args_in.A % 16) || ((args_in.a_stride * esz) % 16)) return NV_ENOTSUP;
+  EncodeTiledFnC enc = nullptr;
+  nv_status st = chain_encode_fn(&enc);
+  if (st != NV_OK) return st;
+  CUtensorMap tmap;
+  const cuuint64_t gdim[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)args_in.S};
+  const cuuint64_t gstride[2] = {(cuuint64_t)n * esz, (cuuint64_t)args_in.a_stride * esz};
+  const cuuint32_t box[3] = {(cuuint32_t)rpc, (cuuint32_t)n, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(&tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                    const_cast<void*>(args_in.A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return NV_ENOTSUP;
+  const void* fn = f64 ? (const void*)affine_chains_tma_kernel<double, double>
+                       : (const void*)affine_chains_tma_kernel<float, float>;
+  const size_t smem = esz * ((size_t)kRing * rpc * n + 2 * (size_t)n + block) + 8 * kRing + 16;
+  if ((st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                          "cluster size attribute")) != NV_OK)
+    return st;
+  if ((st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "chain smem attribute")) != NV_OK)
+    return st;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(csize * args_in.nchains));
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return NV_ENOTSUP;
+  }
+  ChainsArgs a = args_in;
+  a.rpc = rpc;
+  void* args[] = {&tmap, &a, &status};
+  return nv_cuda_check(cudaLaunchKernelExC(&cfg, fn, args), "affine_chains_tma_kernel launch");
+}
+
 nv_status launch_chains(const ChainsArgs& args_in, bool f64, cudaStream_t s, int want_csize) {
   const int n = args_in.n;
   const int block = 256;
   if (n > 512) return nv_fail(NV_ENOTSUP, "cluster chains need d <= 512");
+  if (want_csize <= 0 || want_csize == 16) {
+    nv_status st = launch_chains_tma(args_in, f64, s, args_in.status);
+    if (st != NV_ENOTSUP) return st;
+  }
   const void* fn = f64 ? (const void*)affine_chains_kernel<double, double>
                        : (const void*)affine_chains_kernel<float, float>;
   const size_t esz = f64 ? sizeof(double) : sizeof(float);
@@ -244,6 +448,7 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   a.states = lambdas;
   a.yT = yT;
   a.write_state0 = 1;
+  a.status = M->status;
   return launch_chains(a, f64, s, want_csize);
 }
 

@@ -88,6 +88,7 @@ struct ChainsArgs {
   const double* add;      // optional: added to x when writing states / yT
   double* yT;             // optional: x after the last slice S-1 (+ add)
   int write_state0;       // chain 0 also writes states[0..n) = x0 (+ add)
+  int* status;            // device status word (bounded waits record NV_ETIMEOUT)
 };
 
 nv_status launch_chains(const ChainsArgs& args, bool f64, cudaStream_t s, int want_csize);

@@ -444,6 +444,7 @@ nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* l
 
   ChainsArgs blockc{};            // chains over the slices of each block
   blockc.n = n;
+  blockc.status = M->status;
   blockc.nchains = B;
   blockc.len = L;
   blockc.S = S;
@@ -452,6 +453,7 @@ nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* l
 
   ChainsArgs topc{};              // one chain over the block totals
   topc.n = n;
+  topc.status = M->status;
   topc.nchains = 1;
   topc.len = B;
   topc.S = B;
