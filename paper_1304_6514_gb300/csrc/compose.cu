@@ -222,7 +222,10 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   const int n = a.n, rpc = a.rpc;
   const int stage_elems = rpc * n;
   MT* ring = reinterpret_cast<MT*>(ring_smem);                          // kRing stages
-  AT* xs = reinterpret_cast<AT*>(ring + kRing * stage_elems);          // two state buffers
+  // per stage also rpc values of v_j and of add_{j+1}, as doubles (16-byte slots)
+  double* vring = reinterpret_cast<double*>(ring + kRing * stage_elems);
+  double* aring = vring + kRing * rpc;
+  AT* xs = reinterpret_cast<AT*>(aring + kRing * rpc);                 // two state buffers
   AT* red = xs + 2 * n;                                                // blockDim partials
   uint64_t* full = reinterpret_cast<uint64_t*>(
       ((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);
@@ -233,7 +236,9 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   const bool active = (cgi < ncg) && (row < n);
   const int j0 = q * a.len;
   const int len = min(a.len, a.S - j0);
-  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT));
+  const int vsz = a.v_double ? 8 : (int)sizeof(MT);
+  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT)) + (uint32_t)(rpc * vsz) +
+                               (a.add ? (uint32_t)(rpc * 8) : 0u);
 
   if (tid == 0) {
     for (int i = 0; i < kRing; ++i)
@@ -252,6 +257,21 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(cta_smem_u32(ring + st * stage_elems)),
         "l"(&tmA), "r"((int)rank * rpc), "r"(0), "r"(j0 + k), "r"(cta_smem_u32(&full[st]))
         : "memory");
+    const char* vsrc = reinterpret_cast<const char*>(a.v) +
+                       ((int64_t)(j0 + k) * a.v_stride + (int64_t)rank * rpc) * vsz;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            cta_smem_u32(vring + st * rpc)),
+        "l"(vsrc), "r"(rpc * vsz), "r"(cta_smem_u32(&full[st]))
+        : "memory");
+    if (a.add) {
+      const double* asrc = a.add + (int64_t)(j0 + k + 1) * n + (int64_t)rank * rpc;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              cta_smem_u32(aring + st * rpc)),
+          "l"(asrc), "r"(rpc * 8), "r"(cta_smem_u32(&full[st]))
+          : "memory");
+    }
   };
   int issued = 0;   // copies issued so far (thread 0)
   if (tid == 0)
@@ -278,23 +298,23 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
     if (active)
       for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
     red[tid] = acc;
-    __syncthreads();   // stage st fully read: it may be refilled
-    if (tid == 0 && issued < len && !abort_flag) issue(issued++);
+    __syncthreads();
     if (tid < rpc && row < n) {
       AT s = 0;
       for (int g = 0; g < ncg; ++g) s += red[g * rpc + tid];
-      AT vj = a.v_double ? (AT)(reinterpret_cast<const double*>(a.v)[(int64_t)j * a.v_stride + row])
-                         : (AT)(reinterpret_cast<const MT*>(a.v)[(int64_t)j * a.v_stride + row]);
+      const AT vj = a.v_double ? (AT)vring[st * rpc + r]
+                               : (AT)reinterpret_cast<const MT*>(vring + st * rpc)[r];
       s += vj;
       const int nb = ((k + 1) & 1) * n + row;
       for (unsigned p = 0; p < csize; ++p) cl.map_shared_rank(xs, p)[nb] = s;
       const int64_t o = (int64_t)(j + 1) * n + row;
-      const double out = (double)s + (a.add ? a.add[o] : 0.0);
+      const double out = (double)s + (a.add ? aring[st * rpc + r] : 0.0);
       if (a.states) a.states[o] = out;
       if (a.yT && j == a.S - 1) a.yT[row] = out;
       if (a.finals && k == len - 1) a.finals[(int64_t)q * n + row] = (double)s;
     }
-    cl.sync();
+    cl.sync();   // also: stage st (matrix, v and add slots) fully read, it may be refilled
+    if (tid == 0 && issued < len && !abort_flag) issue(issued++);
   }
   if (abort_flag && tid == 0) {
     record_status(status, NV_ETIMEOUT);
@@ -342,6 +362,9 @@ static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStre
   const size_t esz = f64 ? 8 : 4;
   if (n > 256 || n < 64 || n % 16 != 0) return NV_ENOTSUP;
   if (((uintptr_t)args_in.A % 16) || ((args_in.a_stride * esz) % 16)) return NV_ENOTSUP;
+  const size_t vsz = args_in.v_double ? 8 : esz;
+  if (((uintptr_t)args_in.v % 16) || ((args_in.v_stride * vsz) % 16)) return NV_ENOTSUP;
+  if (args_in.add && ((uintptr_t)args_in.add % 16)) return NV_ENOTSUP;
   EncodeTiledFnC enc = nullptr;
   nv_status st = chain_encode_fn(&enc);
   if (st != NV_OK) return st;
@@ -357,7 +380,8 @@ static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStre
   if (cr != CUDA_SUCCESS) return NV_ENOTSUP;
   const void* fn = f64 ? (const void*)affine_chains_tma_kernel<double, double>
                        : (const void*)affine_chains_tma_kernel<float, float>;
-  const size_t smem = esz * ((size_t)kRing * rpc * n + 2 * (size_t)n + block) + 8 * kRing + 16;
+  const size_t smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc +
+                      esz * (2 * (size_t)n + block) + 8 * kRing + 16;
   if ((st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                           "cluster size attribute")) != NV_OK)
     return st;
