@@ -106,21 +106,54 @@ __device__ __forceinline__ double heat_g(int varcoef, double amp, double t) {
   return -sin(t) + a * (M_PI * M_PI) * cos(t);
 }
 
+// Time-dependent coefficients of one literal RK4 step, at t, t+h/2, t+h:
+// forcing amplitudes g and diffusion coefficients a(t) cdx.
+template <typename T>
+struct StageCoefs {
+  T g0, gh, g1, a0, ah, a1;
+};
+
+// Coefficients of the steps i0 .. i0+15 of a slice starting at Tj: lane l
+// evaluates the half-step time q = 2 i0 + l (l <= 30; l = 31 idles) once, and
+// the steps read them by shuffle, so the trigonometric calls run once per
+// warp instead of once per lane.
+struct HalfStepCoefs {
+  double g, a;
+};
+
+__device__ __forceinline__ HalfStepCoefs half_step_coefs(const HeatArgs& a, double Tj, int64_t i0,
+                                                         int lane) {
+  const int64_t q = 2 * i0 + lane;
+  const int64_t i = q >> 1;
+  double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
+  if (q & 1) t = __dadd_rn(t, 0.5 * a.h);
+  HalfStepCoefs c;
+  c.g = heat_g(a.varcoef, a.amp, t);
+  c.a = heat_a(a.varcoef, t);
+  return c;
+}
+
+template <typename T>
+__device__ __forceinline__ StageCoefs<T> step_coefs(const HalfStepCoefs& hc, int64_t i, int64_t i0,
+                                                    T cdx) {
+  const int l = (int)(2 * (i - i0));
+  StageCoefs<T> c;
+  c.g0 = (T)__shfl_sync(0xffffffffu, hc.g, l);
+  c.gh = (T)__shfl_sync(0xffffffffu, hc.g, l + 1);
+  c.g1 = (T)__shfl_sync(0xffffffffu, hc.g, l + 2);
+  c.a0 = (T)__shfl_sync(0xffffffffu, hc.a, l) * cdx;
+  c.ah = (T)__shfl_sync(0xffffffffu, hc.a, l + 1) * cdx;
+  c.a1 = (T)__shfl_sync(0xffffffffu, hc.a, l + 2) * cdx;
+  return c;
+}
+
 // Literal RK4 step (stage times t, t+h/2, t+h) for the heat right-hand side.
 template <int R, typename T>
-__device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double t, double h, T cdx,
-                                              const HeatArgs& a, const T* sx, bool forced,
-                                              int lane, int n) {
+__device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double h, const StageCoefs<T>& c,
+                                              const T* sx, bool forced, int lane, int n) {
   const T hh = (T)(0.5 * h), hT = (T)h;
-  const double th = __dadd_rn(t, 0.5 * h), t1 = __dadd_rn(t, h);
-  T g0 = 0, gh = 0, g1 = 0;
-  if (forced) {
-    g0 = (T)heat_g(a.varcoef, a.amp, t);
-    gh = (T)heat_g(a.varcoef, a.amp, th);
-    g1 = (T)heat_g(a.varcoef, a.amp, t1);
-  }
-  const T a0 = (T)heat_a(a.varcoef, t) * cdx, ah = (T)heat_a(a.varcoef, th) * cdx;
-  const T a1 = (T)heat_a(a.varcoef, t1) * cdx;
+  const T g0 = forced ? c.g0 : (T)0, gh = forced ? c.gh : (T)0, g1 = forced ? c.g1 : (T)0;
+  const T a0 = c.a0, ah = c.ah, a1 = c.a1;
 #pragma unroll
   for (int i = 0; i < R; ++i) z[i] = y[i];
   heat_stage<R>(y, z, acc, a0, g0, sx, forced, hh, (T)0, true, lane, n);
@@ -215,9 +248,11 @@ __global__ void __launch_bounds__(256) heat_literal_kernel(HeatArgs a, int all_c
         if (r < n) sx[i] = (T)sin(M_PI * ((double)(r + 1) / (double)(n + 1)));
       }
     }
+    HalfStepCoefs hc{};
     for (int64_t i = 0; i < a.m; ++i) {
-      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
-      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, forced, lane, n);
+      const int64_t i0 = i - (i % 15);
+      if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
+      heat_rk4_step<R>(y, z, acc, a.h, step_coefs<T>(hc, i, i0, cdx), sx, forced, lane, n);
     }
     T* col = out + ((int64_t)j * cols + c) * n;
 #pragma unroll
@@ -245,9 +280,11 @@ __global__ void heat_serial_kernel(HeatArgs a, const double* y0, double* yT) {
   }
   for (int j = 0; j < a.S; ++j) {
     const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
+    HalfStepCoefs hc{};
     for (int64_t i = 0; i < a.m; ++i) {
-      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
-      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, true, lane, n);
+      const int64_t i0 = i - (i % 15);
+      if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
+      heat_rk4_step<R>(y, z, acc, a.h, step_coefs<double>(hc, i, i0, cdx), sx, true, lane, n);
     }
   }
 #pragma unroll
@@ -278,9 +315,11 @@ __global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const doub
       y[i] = r < n ? lt[j * n + r] : 0.0;
       sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
     }
+    HalfStepCoefs hc{};
     for (int64_t i = 0; i < a.m; ++i) {
-      const double t = __dadd_rn(Tj, __dmul_rn((double)i, a.h));
-      heat_rk4_step<R>(y, z, acc, t, a.h, cdx, a, sx, true, lane, n);
+      const int64_t i0 = i - (i % 15);
+      if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
+      heat_rk4_step<R>(y, z, acc, a.h, step_coefs<double>(hc, i, i0, cdx), sx, true, lane, n);
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {

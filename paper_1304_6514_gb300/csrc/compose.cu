@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
 // mbarrier.  The copies run in the async proxy, so the release half of the
 // cluster barrier does not wait for them and HBM latency leaves the
 // dependency chain.  Stage layout: element (row r, column c) at c*rpc + r.
-constexpr int kRing = 4;
+constexpr int kRing = 3;
 
 __device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
