@@ -196,6 +196,61 @@ const char* nv_last_error(void);
 /* NVPIT_VERSION of the built library. */
 int32_t nv_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Batched independent instances (the "great deal more parallelism" of the
+ * Conclusion: every (instance, slice, sample) trajectory is independent).
+ * B instances of one right-hand side family, each with its own parameters,
+ * interval [t0_i, T_i] and slice count S_i, share the sample grid and the
+ * step rule.  The computation phase of all instances runs in ONE persistent
+ * launch: CTAs pull (instance, slice) work items from a device queue ordered
+ * by decreasing cost (longest-processing-time first).  Table maps only
+ * (NV_MAP_PL1D for d = 1, NV_MAP_BILINEAR2D for d = 2); composition in float64.
+ * Tables of instance i start at element offset sum_{i'<i} S_i' * E, E the
+ * elements per slice (M or 2 P^2), and follow the nv_maps_desc layout.
+ * ------------------------------------------------------------------------- */
+typedef struct nv_batch nv_batch;   /* opaque, library-owned */
+
+/* Builds the tables of every instance.  params: B x nparams host array (row
+ * i = parameters of instance i); t0, T, S: host arrays of B values.  Allocates
+ * the batch object (tables, instance descriptors, work queue) and launches
+ * the persistent build on `stream`.  NV_EINVAL for inconsistent arguments. */
+nv_status nv_build_batch(int32_t rhs_kind, int32_t dim, int32_t B, const double* params,
+                         int32_t nparams, const double* t0, const double* T, const int32_t* S,
+                         const nv_samples* samples, const nv_steps* steps, nv_batch** out,
+                         void* stream);
+
+/* Rebuilds the tables of an existing batch (same instances) on `stream`. */
+nv_status nv_batch_rebuild(nv_batch* batch, void* stream);
+
+/* Composes every instance: yT[i] = phi^{S_i}_i( ... phi^1_i(y0[i])), float64.
+ * y0_dev, yT_dev: B x dim doubles (device). */
+nv_status nv_batch_compose(const nv_batch* batch, const double* y0_dev, double* yT_dev,
+                           void* stream);
+
+/* Build + compose replayed from a CUDA graph captured on the first call with
+ * these buffers (re-captured when the buffers change).  Launches on `stream`. */
+nv_status nv_batch_run(nv_batch* batch, const double* y0_dev, double* yT_dev, void* stream);
+
+/* Times the persistent build for each candidate CTA shape (threads per CTA
+ * 128/256/512/1024 at full occupancy) on this batch with CUDA events, keeps
+ * the fastest for this batch and as the default for the device, and returns
+ * it in best_threads (may be NULL).  Synchronises `stream`. */
+nv_status nv_batch_autotune(nv_batch* batch, void* stream, int32_t* best_threads);
+
+/* Sizes: total slices (work items), trajectory-steps of one build, bytes of
+ * tables, and the CTA size in use. */
+nv_status nv_batch_info(const nv_batch* batch, int64_t* total_slices, int64_t* traj_steps,
+                        int64_t* table_bytes, int32_t* threads);
+
+/* Copies the tables (table_bytes bytes) to a host or device pointer. */
+nv_status nv_batch_copy_out(const nv_batch* batch, void* dst, int64_t bytes, void* stream);
+
+/* Synchronises, returns the recorded device status and the out-of-range count. */
+nv_status nv_batch_check(const nv_batch* batch, void* stream, int64_t* oob_count);
+
+/* Releases the batch (NULL accepted); synchronises the device first. */
+nv_status nv_batch_destroy(nv_batch* batch);
+
 /* Largest state dimension nv_compose_affine_noalloc accepts. */
 #define NVPIT_NOALLOC_MAX_DIM 4096
 

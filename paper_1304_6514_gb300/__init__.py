@@ -84,6 +84,16 @@ def load_library(path: str = LIB_PATH):
         "nv_maps_check": [P, P, POINTER(c_int64)],
         "nv_tune_set": [c_int32, c_int32],
         "nv_compose_affine_noalloc": [P, c_int32, c_int32, c_int32, P, P, P, P, P],
+        "nv_build_batch": [c_int32, c_int32, c_int32, P, c_int32, P, P, P, POINTER(NvSamples),
+                           POINTER(NvSteps), POINTER(c_void_p), P],
+        "nv_batch_rebuild": [P, P],
+        "nv_batch_compose": [P, P, P, P],
+        "nv_batch_run": [P, P, P, P],
+        "nv_batch_autotune": [P, P, POINTER(c_int32)],
+        "nv_batch_info": [P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64), POINTER(c_int32)],
+        "nv_batch_copy_out": [P, P, c_int64, P],
+        "nv_batch_check": [P, P, POINTER(c_int64)],
+        "nv_batch_destroy": [P],
         "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
                           POINTER(c_double)],
     }
@@ -266,3 +276,81 @@ def tune_set(key: int, value: int):
 
 def version() -> int:
     return load_library().nv_version()
+
+
+# ------------------------------------------------------------------ batched instances
+
+class Batch:
+    """Library-owned batch of independent instances (nv_batch)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(load_library().nv_batch_destroy(h))
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.nv_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def build_batch(kind: str, dim: int, params, t0, T, S, samples_, steps_, stream=None) -> Batch:
+    """nv_build_batch: params (B, nparams), t0/T (B,), S (B,) host arrays."""
+    import numpy as np
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    if params.ndim == 1:
+        params = params[:, None]
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    B = len(T)
+    h = c_void_p()
+    _check(load_library().nv_build_batch(RHS[kind], dim, B, params.ctypes.data, params.shape[1],
+                                         t0.ctypes.data, T.ctypes.data, S.ctypes.data, byref(samples_),
+                                         byref(steps_), byref(h), _stream(stream)))
+    return Batch(h.value)
+
+
+def batch_rebuild(batch: Batch, stream=None):
+    _check(load_library().nv_batch_rebuild(batch.handle, _stream(stream)))
+
+
+def batch_compose(batch: Batch, y0, yT, stream=None):
+    _check(load_library().nv_batch_compose(batch.handle, _ptr(y0), _ptr(yT), _stream(stream)))
+
+
+def batch_run(batch: Batch, y0, yT, stream=None):
+    _check(load_library().nv_batch_run(batch.handle, _ptr(y0), _ptr(yT), _stream(stream)))
+
+
+def batch_autotune(batch: Batch, stream=None) -> int:
+    best = c_int32(0)
+    _check(load_library().nv_batch_autotune(batch.handle, _stream(stream), byref(best)))
+    return best.value
+
+
+def batch_info(batch: Batch) -> dict:
+    a, b, c, d = c_int64(0), c_int64(0), c_int64(0), c_int32(0)
+    _check(load_library().nv_batch_info(batch.handle, byref(a), byref(b), byref(c), byref(d)))
+    return {"total_slices": a.value, "traj_steps": b.value, "table_bytes": c.value, "threads": d.value}
+
+
+def batch_tables(batch: Batch, dtype):
+    """The tables of every instance as a new flat CUDA tensor of `dtype`."""
+    import torch
+    nbytes = batch_info(batch)["table_bytes"]
+    out = torch.empty(nbytes // torch.empty((), dtype=dtype).element_size(), dtype=dtype, device="cuda")
+    _check(load_library().nv_batch_copy_out(batch.handle, out.data_ptr(), nbytes, _stream(None)))
+    return out
+
+
+def batch_check(batch: Batch, stream=None) -> int:
+    n = c_int64(0)
+    _check(load_library().nv_batch_check(batch.handle, _stream(stream), byref(n)))
+    return n.value
