@@ -184,6 +184,12 @@ nv_status nv_maps_info(const nv_maps* maps, nv_maps_desc* out);
  * or device pointer, asynchronously on `stream`. */
 nv_status nv_maps_copy_out(const nv_maps* maps, void* dst, int64_t bytes, void* stream);
 
+/* Copies `bytes` bytes of map data starting `offset` bytes into the maps to
+ * dst (host or device), asynchronously on `stream`; NV_EINVAL if the range
+ * leaves the maps. */
+nv_status nv_maps_copy_range(const nv_maps* maps, void* dst, int64_t offset, int64_t bytes,
+                             void* stream);
+
 /* Synchronises `stream`, then returns the device status recorded by this
  * maps object's kernels (NV_OK, NV_EDOMAIN, NV_ETIMEOUT) and, if oob_count is
  * non-NULL, the number of evaluations outside Xi since the last compose. */

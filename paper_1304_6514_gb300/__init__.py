@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "nv_maps_destroy": [P],
         "nv_maps_info": [P, POINTER(NvMapsDesc)],
         "nv_maps_copy_out": [P, P, c_int64, P],
+        "nv_maps_copy_range": [P, P, c_int64, c_int64, P],
         "nv_maps_check": [P, P, POINTER(c_int64)],
         "nv_tune_set": [c_int32, c_int32],
         "nv_compose_affine_noalloc": [P, c_int32, c_int32, c_int32, P, P, P, P, P],
@@ -261,6 +262,17 @@ def maps_data(maps: Maps):
     dt = torch.float64 if d.elem_bytes == 8 else torch.float32
     out = torch.empty(d.bytes // d.elem_bytes, dtype=dt, device="cuda")
     _check(load_library().nv_maps_copy_out(maps.handle, out.data_ptr(), d.bytes, _stream(None)))
+    return out
+
+
+def maps_slice(maps: Maps, j: int, count: int = 1):
+    """Map data of slices j .. j+count-1 as a new flat CUDA tensor."""
+    import torch
+    d = maps_info(maps)
+    dt = torch.float64 if d.elem_bytes == 8 else torch.float32
+    out = torch.empty(d.elems_per_slice * count, dtype=dt, device="cuda")
+    _check(load_library().nv_maps_copy_range(maps.handle, out.data_ptr(), j * d.elems_per_slice * d.elem_bytes,
+                                             count * d.elems_per_slice * d.elem_bytes, _stream(None)))
     return out
 
 

@@ -329,6 +329,148 @@ __global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const doub
   }
 }
 
+// ---------------------------------------------------------------------------
+// Periodic 2-D advection-diffusion on an nx x nx grid (nx = 64, d = 4096):
+// L u = nu lap5(u) - ax D-x u - ay D-y u.  One CTA of 256 threads integrates
+// one basis column.  Thread t holds the strip iy = 16*(t/64) .. +15 at
+// ix = t % 64 in registers: its y-neighbours are in the same thread except at
+// the strip ends, its x-neighbours in lanes +-1 (warp shuffles) except at the
+// warp's edge lanes; strip-end rows and edge-lane strips cross through
+// double-buffered shared memory, one __syncthreads per stage.  RK4 runs in
+// Horner form (time-invariant operator), the stage factor h/k folded into the
+// five stencil weights.
+constexpr int kAdvNx = 64;
+constexpr int kAdvRows = 16;     // rows per thread strip
+
+struct AdvArgs {
+  void* out;
+  int S;
+  int64_t m;
+  double h;
+  double w_xm, w_xp, w_ym, w_yp, w_0;   // L u = sum of weights times neighbours
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
+  constexpr int n = kAdvNx * kAdvNx;
+  __shared__ T top[2][4][kAdvNx];     // first row of each strip block, per buffer
+  __shared__ T bot[2][4][kAdvNx];     // last row
+  __shared__ T edge[2][8][2][kAdvRows];  // per warp: strips of lanes 0 and 31
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;
+  const int pw = warp ^ 1;            // the other warp of the same 64-wide row band
+  T* out = reinterpret_cast<T*>(a.out);
+  const int64_t total = (int64_t)a.S * (n + 1);
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int j = (int)(w / (n + 1));
+    const int c = (int)(w - (int64_t)j * (n + 1));     // 0: solve from 0 (no forcing), else e_{c-1}
+    T y[kAdvRows], v[kAdvRows];
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) y[r] = ((c >= 1) && ((iy0 + r) * kAdvNx + ix == c - 1)) ? (T)1 : (T)0;
+    int buf = 0;
+    for (int64_t i = 0; i < a.m; ++i) {
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
+#pragma unroll 1
+      for (int kk = 4; kk >= 1; --kk) {
+        const T f = (T)(a.h / kk);
+        const T cxm = f * (T)a.w_xm, cxp = f * (T)a.w_xp, cym = f * (T)a.w_ym, cyp = f * (T)a.w_yp;
+        const T c0 = f * (T)a.w_0;
+        top[buf][blk][ix] = v[0];
+        bot[buf][blk][ix] = v[kAdvRows - 1];
+        if (lane == 0 || lane == 31) {
+#pragma unroll
+          for (int r = 0; r < kAdvRows; ++r) edge[buf][warp][lane == 31][r] = v[r];
+        }
+        __syncthreads();
+        const T above = bot[buf][(blk + 3) & 3][ix];     // row iy0 - 1 (periodic)
+        const T below = top[buf][(blk + 1) & 3][ix];     // row iy0 + 16
+        T nv[kAdvRows];
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) {
+          T xm = __shfl_up_sync(0xffffffffu, v[r], 1);
+          T xp = __shfl_down_sync(0xffffffffu, v[r], 1);
+          if (lane == 0) xm = edge[buf][pw][1][r];        // ix - 1 lives in the other warp's lane 31
+          if (lane == 31) xp = edge[buf][pw][0][r];       // ix + 1 in its lane 0
+          const T ym = r == 0 ? above : v[r - 1];
+          const T yp = r == kAdvRows - 1 ? below : v[r + 1];
+          T acc = fma(c0, v[r], y[r]);
+          acc = fma(cxm, xm, acc);
+          acc = fma(cxp, xp, acc);
+          acc = fma(cym, ym, acc);
+          nv[r] = fma(cyp, yp, acc);
+        }
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
+        buf ^= 1;
+      }
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
+    }
+    T* col = out + ((int64_t)j * (n + 1) + c) * n;
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
+    __syncthreads();   // shared halos are reused by the next column
+  }
+}
+
+// Serial fine solve of the advection-diffusion system (one CTA, S*m steps).
+template <typename T>
+__global__ void __launch_bounds__(256) advdiff_serial_kernel(AdvArgs a, const double* y0, double* yT) {
+  __shared__ T top[2][4][kAdvNx];
+  __shared__ T bot[2][4][kAdvNx];
+  __shared__ T edge[2][8][2][kAdvRows];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;
+  const int pw = warp ^ 1;
+  T y[kAdvRows], v[kAdvRows];
+#pragma unroll
+  for (int r = 0; r < kAdvRows; ++r) y[r] = (T)y0[(iy0 + r) * kAdvNx + ix];
+  int buf = 0;
+  const int64_t steps = (int64_t)a.S * a.m;
+  for (int64_t i = 0; i < steps; ++i) {
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
+#pragma unroll 1
+    for (int kk = 4; kk >= 1; --kk) {
+      const T f = (T)(a.h / kk);
+      const T cxm = f * (T)a.w_xm, cxp = f * (T)a.w_xp, cym = f * (T)a.w_ym, cyp = f * (T)a.w_yp;
+      const T c0 = f * (T)a.w_0;
+      top[buf][blk][ix] = v[0];
+      bot[buf][blk][ix] = v[kAdvRows - 1];
+      if (lane == 0 || lane == 31) {
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) edge[buf][warp][lane == 31][r] = v[r];
+      }
+      __syncthreads();
+      const T above = bot[buf][(blk + 3) & 3][ix];
+      const T below = top[buf][(blk + 1) & 3][ix];
+      T nv[kAdvRows];
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) {
+        T xm = __shfl_up_sync(0xffffffffu, v[r], 1);
+        T xp = __shfl_down_sync(0xffffffffu, v[r], 1);
+        if (lane == 0) xm = edge[buf][pw][1][r];
+        if (lane == 31) xp = edge[buf][pw][0][r];
+        const T ym = r == 0 ? above : v[r - 1];
+        const T yp = r == kAdvRows - 1 ? below : v[r + 1];
+        T acc = fma(c0, v[r], y[r]);
+        acc = fma(cxm, xm, acc);
+        acc = fma(cxp, xp, acc);
+        acc = fma(cym, ym, acc);
+        nv[r] = fma(cyp, yp, acc);
+      }
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
+  }
+#pragma unroll
+  for (int r = 0; r < kAdvRows; ++r) yT[(iy0 + r) * kAdvNx + ix] = (double)y[r];
+}
+
 }  // namespace nvpit
 
 using namespace nvpit;
@@ -415,6 +557,8 @@ static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s, boo
   }
 }
 
+nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s);
+
 nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
   if (M->rhs_kind == NV_RHS_HEAT1D || M->rhs_kind == NV_RHS_HEAT1D_VARCOEF) {
     if (M->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "affine heat maps are built with RK4");
@@ -424,6 +568,7 @@ nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
     if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s, false);
     return launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE);
   }
+  if (M->rhs_kind == NV_RHS_ADVDIFF2D) return launch_advdiff_build(M, s);
   return nv_fail(NV_ENOTSUP, "affine maps are not built for rhs kind %d", M->rhs_kind);
 }
 
@@ -463,4 +608,46 @@ nv_status launch_heat_defect(const nv_maps* M, const double* lam_tilde, double* 
   }
 #undef NVPIT_DEFECT_CASE
   return nv_cuda_check(cudaGetLastError(), "heat_defect_kernel launch");
+}
+
+static AdvArgs adv_args(const nv_maps* M) {
+  AdvArgs a{};
+  a.out = M->data;
+  a.S = M->S;
+  a.m = M->m;
+  a.h = M->h;
+  const double nu = M->params[0], ax = M->params[1], ay = M->params[2];
+  const double dx = 1.0 / kAdvNx;
+  a.w_xm = nu / (dx * dx) + ax / dx;
+  a.w_xp = nu / (dx * dx);
+  a.w_ym = nu / (dx * dx) + ay / dx;
+  a.w_yp = nu / (dx * dx);
+  a.w_0 = -4.0 * nu / (dx * dx) - ax / dx - ay / dx;
+  return a;
+}
+
+nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
+  if (M->dim != kAdvNx * kAdvNx) return nv_fail(NV_ENOTSUP, "advection-diffusion is built for a 64 x 64 grid");
+  if (M->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "affine maps are built with RK4");
+  const AdvArgs a = adv_args(M);
+  int grid = 0;
+  nv_status st;
+  const int64_t cols = (int64_t)M->S * (M->dim + 1);
+  if (M->prec == NV_FP64) {
+    st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);
+    if (st != NV_OK) return st;
+    advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
+  } else {
+    st = persistent_grid(advdiff_affine_kernel<float>, 256, cols * 8, &grid);
+    if (st != NV_OK) return st;
+    advdiff_affine_kernel<float><<<grid, 256, 0, s>>>(a);
+  }
+  return nv_cuda_check(cudaGetLastError(), "advdiff_affine_kernel launch");
+}
+
+nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, cudaStream_t s) {
+  if (M->dim != kAdvNx * kAdvNx) return nv_fail(NV_ENOTSUP, "advection-diffusion is built for a 64 x 64 grid");
+  const AdvArgs a = adv_args(M);
+  advdiff_serial_kernel<double><<<1, 256, 0, s>>>(a, y0, yT);
+  return nv_cuda_check(cudaGetLastError(), "advdiff_serial_kernel launch");
 }

@@ -14,6 +14,7 @@ nv_status launch_serial_table(int32_t rhs_kind, const double* params, double t0,
                               double h, int32_t S, int64_t m, int32_t scheme, const double* y0,
                               double* yT, cudaStream_t s);
 nv_status launch_serial_heat(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
+nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 
 nv_tunables g_tune = {0, 0, 0, 0, 0, 0};
 
@@ -299,7 +300,10 @@ extern "C" nv_status nv_serial_fine(const nv_rhs* rhs, double t0, double T, int3
     if (steps->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "heat serial solve uses RK4");
     return launch_serial_heat(&P, y0_dev, yT_dev, s);
   }
-  if (rhs->kind == NV_RHS_ADVDIFF2D) return nv_fail(NV_ENOTSUP, "advection-diffusion serial solve");
+  if (rhs->kind == NV_RHS_ADVDIFF2D) {
+    if (steps->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "advection-diffusion serial solve uses RK4");
+    return launch_serial_advdiff(&P, y0_dev, yT_dev, s);
+  }
   return launch_serial_table(rhs->kind, P.params, t0, P.H, P.h, S, P.m, steps->scheme, y0_dev,
                              yT_dev, s);
 }
@@ -326,6 +330,16 @@ extern "C" nv_status nv_maps_copy_out(const nv_maps* maps, void* dst, int64_t by
   return nv_cuda_check(cudaMemcpyAsync(dst, maps->data, (size_t)bytes, cudaMemcpyDefault,
                                        static_cast<cudaStream_t>(stream)),
                        "maps copy-out");
+}
+
+extern "C" nv_status nv_maps_copy_range(const nv_maps* maps, void* dst, int64_t offset, int64_t bytes,
+                                        void* stream) {
+  if (!maps || !dst) return nv_fail(NV_EINVAL, "NULL argument");
+  if (offset < 0 || bytes < 0 || offset > maps->bytes || bytes > maps->bytes - offset)
+    return nv_fail(NV_EINVAL, "range leaves the maps");
+  return nv_cuda_check(cudaMemcpyAsync(dst, static_cast<const char*>(maps->data) + offset, (size_t)bytes,
+                                       cudaMemcpyDefault, static_cast<cudaStream_t>(stream)),
+                       "maps range copy");
 }
 
 extern "C" nv_status nv_maps_check(const nv_maps* maps, void* stream, int64_t* oob_count) {

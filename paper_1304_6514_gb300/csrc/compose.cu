@@ -36,11 +36,12 @@ struct AffineChainArgs {
 // Loads issued ahead of the barrier: up to kPre columns per thread.
 constexpr int kPre = 16;
 
-template <typename MT>
+template <typename MT, typename AT>
 __global__ void __launch_bounds__(256) affine_chain_kernel(AffineChainArgs a) {
-  extern __shared__ double sx[];  // n + 1 (sx[0] = 1 multiplies b_j)
+  extern __shared__ __align__(16) unsigned char sx_raw[];
+  AT* sx = reinterpret_cast<AT*>(sx_raw);  // n + 1 (sx[0] = 1 multiplies b_j)
   __shared__ int flag;
-  __shared__ double red[256];
+  __shared__ AT red[256];
   const int n = a.n, rpc = a.rpc;
   const int tid = threadIdx.x;
   const int r = tid % rpc, cg = tid / rpc, ncg = blockDim.x / rpc;
@@ -66,25 +67,26 @@ __global__ void __launch_bounds__(256) affine_chain_kernel(AffineChainArgs a) {
 
   for (int k = 0; k < a.S; ++k) {
     const double* xin = (k == 0) ? a.y0 : a.xbuf + ((k - 1) & 1) * n;
-    for (int i = tid; i < n; i += blockDim.x) sx[i + 1] = __ldcg(xin + i);
-    if (tid == 0) sx[0] = 1.0;
+    for (int i = tid; i < n; i += blockDim.x) sx[i + 1] = (AT)__ldcg(xin + i);
+    if (tid == 0) sx[0] = (AT)1;
     __syncthreads();
-    double acc = 0.0;
+    AT acc = 0;
     if (active) {
 #pragma unroll
       for (int q = 0; q < kPre; ++q) {
         const int c = cg + q * ncg;
-        if (c <= n) acc = fma((double)pre[q], sx[c], acc);
+        if (c <= n) acc = fma((AT)pre[q], sx[c], acc);
       }
       const MT* A = maps + (int64_t)k * slice_elems;
+#pragma unroll 8
       for (int c = cg + kPre * ncg; c <= n; c += ncg)
-        acc = fma((double)__ldcs(A + (int64_t)c * n + row), sx[c], acc);
+        acc = fma((AT)__ldcs(A + (int64_t)c * n + row), sx[c], acc);
     }
     red[tid] = acc;
     __syncthreads();
     if (tid < rpc && row < n) {
       double v = 0.0;
-      for (int g = 0; g < ncg; ++g) v += red[g * rpc + tid];
+      for (int g = 0; g < ncg; ++g) v += (double)red[g * rpc + tid];
       a.xbuf[(k & 1) * n + row] = v;
       if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row] = v;
       if (k == a.S - 1) a.yT[row] = v;
@@ -491,9 +493,9 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = sizeof(double) * (size_t)(n + 1);
-  const void* fn = (M->prec == NV_FP64) ? (const void*)affine_chain_kernel<double>
-                                        : (const void*)affine_chain_kernel<float>;
+  const size_t smem = (M->prec == NV_FP64 ? sizeof(double) : sizeof(float)) * (size_t)(n + 1);
+  const void* fn = (M->prec == NV_FP64) ? (const void*)affine_chain_kernel<double, double>
+                                        : (const void*)affine_chain_kernel<float, float>;
   if (smem > 48 * 1024) {
     nv_status st = nv_cuda_check(
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -535,8 +537,8 @@ nv_status launch_affine_chain_buffers(const void* maps, int prec, int n, int S, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = sizeof(double) * (size_t)(n + 1);
-  const void* fn = (prec == NV_FP64) ? (const void*)affine_chain_kernel<double>
-                                     : (const void*)affine_chain_kernel<float>;
+  const void* fn = (prec == NV_FP64) ? (const void*)affine_chain_kernel<double, double>
+                                     : (const void*)affine_chain_kernel<float, double>;
   if (smem > 48 * 1024) {
     nv_status st = nv_cuda_check(
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
