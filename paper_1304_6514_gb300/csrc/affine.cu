@@ -348,7 +348,22 @@ struct AdvArgs {
   int64_t m;
   double h;
   double w_xm, w_xp, w_ym, w_yp, w_0;   // L u = sum of weights times neighbours
+  // stage weights (h/k) w_* for Horner stage k = 4..1 (index 4 - k), in both
+  // precisions so the float32 kernel does no float64 arithmetic
+  double cw64[4][5];
+  float cw32[4][5];
 };
+
+template <typename T>
+__device__ __forceinline__ const T* adv_weights(const AdvArgs& a, int stage);
+template <>
+__device__ __forceinline__ const double* adv_weights<double>(const AdvArgs& a, int stage) {
+  return a.cw64[stage];
+}
+template <>
+__device__ __forceinline__ const float* adv_weights<float>(const AdvArgs& a, int stage) {
+  return a.cw32[stage];
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
@@ -373,9 +388,8 @@ __global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
       for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
 #pragma unroll 1
       for (int kk = 4; kk >= 1; --kk) {
-        const T f = (T)(a.h / kk);
-        const T cxm = f * (T)a.w_xm, cxp = f * (T)a.w_xp, cym = f * (T)a.w_ym, cyp = f * (T)a.w_yp;
-        const T c0 = f * (T)a.w_0;
+        const T* cw = adv_weights<T>(a, 4 - kk);
+        const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
         top[buf][blk][ix] = v[0];
         bot[buf][blk][ix] = v[kAdvRows - 1];
         if (lane == 0 || lane == 31) {
@@ -433,9 +447,8 @@ __global__ void __launch_bounds__(256) advdiff_serial_kernel(AdvArgs a, const do
     for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
 #pragma unroll 1
     for (int kk = 4; kk >= 1; --kk) {
-      const T f = (T)(a.h / kk);
-      const T cxm = f * (T)a.w_xm, cxp = f * (T)a.w_xp, cym = f * (T)a.w_ym, cyp = f * (T)a.w_yp;
-      const T c0 = f * (T)a.w_0;
+      const T* cw = adv_weights<T>(a, 4 - kk);
+      const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
       top[buf][blk][ix] = v[0];
       bot[buf][blk][ix] = v[kAdvRows - 1];
       if (lane == 0 || lane == 31) {
@@ -623,6 +636,12 @@ static AdvArgs adv_args(const nv_maps* M) {
   a.w_ym = nu / (dx * dx) + ay / dx;
   a.w_yp = nu / (dx * dx);
   a.w_0 = -4.0 * nu / (dx * dx) - ax / dx - ay / dx;
+  const double w[5] = {a.w_xm, a.w_xp, a.w_ym, a.w_yp, a.w_0};
+  for (int st = 0; st < 4; ++st)
+    for (int q = 0; q < 5; ++q) {
+      a.cw64[st][q] = (a.h / (4 - st)) * w[q];
+      a.cw32[st][q] = (float)a.cw64[st][q];
+    }
   return a;
 }
 

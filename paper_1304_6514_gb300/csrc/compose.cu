@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -325,6 +326,64 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   }
 }
 
+// Grid-wide chain for large d (d > 512, d a multiple of 4): like
+// affine_chain_kernel, but every thread owns VEC = 16 / sizeof(MT) consecutive
+// rows and reads them with one 16-byte load per column, so each SM keeps
+// enough bytes in flight for the chain to stream the maps at HBM speed.
+template <typename MT, typename AT>
+__global__ void __launch_bounds__(256) affine_chain_vec_kernel(AffineChainArgs a) {
+  constexpr int VEC = 16 / (int)sizeof(MT);
+  using V = typename std::conditional<sizeof(MT) == 4, float4, double2>::type;
+  extern __shared__ __align__(16) unsigned char sxv_raw[];
+  AT* sx = reinterpret_cast<AT*>(sxv_raw);   // n + 1
+  AT* red = sx + (a.n + 1);                  // ncg x rpc partial sums
+  __shared__ int flag;
+  const int n = a.n, rpc = a.rpc;
+  const int nq = rpc / VEC;                  // row groups per CTA
+  const int tid = threadIdx.x;
+  const int rq = tid % nq, cg = tid / nq, ncg = blockDim.x / nq;
+  const int row0 = blockIdx.x * rpc + rq * VEC;
+  const bool active = (cg < ncg) && (row0 < n);
+  const unsigned G = gridDim.x;
+  const MT* maps = reinterpret_cast<const MT*>(a.maps);
+  const int64_t slice_elems = (int64_t)n * (n + 1);
+  if (blockIdx.x == 0 && a.lambdas)
+    for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i];
+  for (int k = 0; k < a.S; ++k) {
+    const double* xin = (k == 0) ? a.y0 : a.xbuf + ((k - 1) & 1) * n;
+    for (int i = tid; i < n; i += blockDim.x) sx[i + 1] = (AT)__ldcg(xin + i);
+    if (tid == 0) sx[0] = (AT)1;
+    __syncthreads();
+    AT acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = 0;
+    if (active) {
+      const MT* A = maps + (int64_t)k * slice_elems + row0;
+#pragma unroll 8
+      for (int c = cg; c <= n; c += ncg) {
+        const V t = __ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n));
+        const AT xc = sx[c];
+        const MT* tv = reinterpret_cast<const MT*>(&t);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = fma((AT)tv[v], xc, acc[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) red[cg * rpc + rq * VEC + v] = acc[v];
+    __syncthreads();
+    const int row = blockIdx.x * rpc + tid;
+    if (tid < rpc && row < n) {
+      double s = 0.0;
+      for (int g = 0; g < ncg; ++g) s += (double)red[g * rpc + tid];
+      a.xbuf[(k & 1) * n + row] = s;
+      if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row] = s;
+      if (k == a.S - 1) a.yT[row] = s;
+    }
+    if (k + 1 < a.S)
+      if (!grid_barrier(a.bar, (unsigned)(k + 1) * G, a.status, &flag)) return;
+  }
+}
+
 }  // namespace nvpit
 
 using namespace nvpit;
@@ -478,6 +537,53 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   return launch_chains(a, f64, s, want_csize);
 }
 
+// Grid-wide chain with 16-byte loads (d > 512, d % 4 == 0).
+static nv_status launch_affine_chain_vec(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                                         cudaStream_t s, int rows_per_cta) {
+  const int n = M->dim;
+  const int block = 256;
+  const bool f64 = M->prec == NV_FP64;
+  const int vec = f64 ? 2 : 4;
+  int rpc = rows_per_cta > 0 ? rows_per_cta : 32;
+  rpc = std::max(vec, std::min(rpc, 256) / vec * vec);
+  while ((block % (rpc / vec)) != 0) rpc -= vec;
+  const int G = (n + rpc - 1) / rpc;
+  const int ncg = block / (rpc / vec);
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  const size_t smem = esz * ((size_t)(n + 1) + (size_t)ncg * rpc);
+  const void* fn = f64 ? (const void*)affine_chain_vec_kernel<double, double>
+                       : (const void*)affine_chain_vec_kernel<float, float>;
+  nv_status st;
+  if (smem > 48 * 1024 &&
+      (st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "chain smem attribute")) != NV_OK)
+    return st;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem),
+                          "chain occupancy")) != NV_OK)
+    return st;
+  if ((int64_t)per_sm * sms < G)
+    return nv_fail(NV_ENOTSUP, "chain needs %d resident CTAs, device holds %d", G, per_sm * sms);
+  if ((st = nv_cuda_check(cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s), "barrier reset")) != NV_OK)
+    return st;
+  AffineChainArgs a{};
+  a.maps = M->data;
+  a.n = n;
+  a.S = M->S;
+  a.rpc = rpc;
+  a.y0 = y0;
+  a.yT = yT;
+  a.lambdas = lambdas;
+  a.xbuf = M->xbuf;
+  a.bar = M->bar;
+  a.status = M->status;
+  void* args[] = {&a};
+  return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
+                       "affine_chain_vec_kernel cooperative launch");
+}
+
 nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                               cudaStream_t s, int rows_per_cta) {
   const int n = M->dim;
@@ -485,6 +591,7 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
     nv_status st = launch_affine_chain_cluster(M, y0, yT, lambdas, s, g_tune.chain_cluster);
     if (st != NV_ENOTSUP) return st;
   }
+  if (n > 512 && n % 4 == 0) return launch_affine_chain_vec(M, y0, yT, lambdas, s, rows_per_cta);
   const int block = 256;
   int rpc = rows_per_cta > 0 ? rows_per_cta : 16;
   rpc = std::min(rpc, block);
