@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) affine_chain_vec_kernel(AffineChainArgs a
     for (int v = 0; v < VEC; ++v) acc[v] = 0;
     if (active) {
       const MT* A = maps + (int64_t)k * slice_elems + row0;
-#pragma unroll 8
+#pragma unroll 16
       for (int c = cg; c <= n; c += ncg) {
         const V t = __ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n));
         const AT xc = sx[c];
@@ -544,7 +544,7 @@ static nv_status launch_affine_chain_vec(const nv_maps* M, const double* y0, dou
   const int block = 256;
   const bool f64 = M->prec == NV_FP64;
   const int vec = f64 ? 2 : 4;
-  int rpc = rows_per_cta > 0 ? rows_per_cta : 32;
+  int rpc = rows_per_cta > 0 ? rows_per_cta : (f64 ? 8 : 16);
   rpc = std::max(vec, std::min(rpc, 256) / vec * vec);
   while ((block % (rpc / vec)) != 0) rpc -= vec;
   const int G = (n + rpc - 1) / rpc;
