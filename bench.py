@@ -58,6 +58,23 @@ def dist_info():
     return world, rank, local
 
 
+def aggregate_over_ranks(units_local: float, seconds_local: float):
+    """Whole-job throughput of replicas: units summed over ranks divided by the
+    slowest rank's time (max over ranks).  Uses torch.distributed when it is
+    initialised (NCCL on GPUs, gloo in the CPU tests); returns
+    (value, max_seconds, total_units)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([seconds_local], dtype=torch.float64, device=dev)
+        u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+    return units_local / seconds_local, seconds_local, units_local
+
+
 def traj_steps(w, m):
     """Trajectory-steps of one build: every basis column of every slice, m steps."""
     return w.S * (w.dim + 1) * m
@@ -542,12 +559,7 @@ def main():
     clocks = sampler.stop()
     m = res["m"]
     units = traj_steps(w, m)
-    dev_s = sum(res["step_ms"]) * 1e-3
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = units * K * world / dev_s
+    value, dev_s, _ = aggregate_over_ranks(units * K, sum(res["step_ms"]) * 1e-3)
     build_s = statistics.mean(res["build_ms"]) * 1e-3
     flop = FLOP_PER_COMPONENT_STEP * units * w.dim
     achieved = flop / build_s
