@@ -257,6 +257,70 @@ nv_status nv_batch_check(const nv_batch* batch, void* stream, int64_t* oob_count
 /* Releases the batch (NULL accepted); synchronises the device first. */
 nv_status nv_batch_destroy(nv_batch* batch);
 
+/* ---------------------------------------------------------------------------
+ * Learned propagator for high-dimensional nonlinear problems (Section 4: a
+ * uniform table with l points per axis costs l^r solves).  The method's own
+ * computation phase produces training pairs; a slice-conditioned MLP
+ * (x = (y0/sx, T_{j-1}/T) -> 256 -> 256 -> 256 -> (y_end - y0)/sd, GELU)
+ * trained on the GPU with bf16 tensor-core forward/backward stands in for the
+ * table; float64 fine integration judges it and replaces it on slices whose
+ * validation error is too large.  Built for the 3-mass chain (NV_RHS_CHAIN3).
+ * ------------------------------------------------------------------------- */
+typedef struct nv_mlp nv_mlp;   /* opaque, library-owned */
+
+/* Training pairs: for slice j and sample k, xi = lo + (hi-lo) u with u the
+ * SplitMix64 outputs (j*M + k)*6 + c (c = 0..5) of `seed` (top 53 bits), and
+ * g^j(xi) from the fine scheme.  y0_dev, yend_dev: S x M x 6 values, float for
+ * NV_FP32 (Kahan-compensated updates), double for NV_FP64. */
+nv_status nv_build_pairs(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
+                         int64_t M, uint64_t seed, double lo, double hi, void* y0_dev, void* yend_dev,
+                         void* stream);
+
+/* Fine integration in float64 of `count` states (y_dev, count x 6 doubles, in
+ * place) over slices j0 .. j0+nslices-1: the judge and the fallback. */
+nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
+                       int32_t j0, int32_t nslices, int64_t count, double* y_dev, void* stream);
+
+/* Creates the network with weights drawn from SplitMix64(seed), uniform in
+ * +-1/sqrt(fan_in).  Synchronous. */
+nv_status nv_mlp_create(uint64_t seed, nv_mlp** out);
+nv_status nv_mlp_destroy(nv_mlp* mlp);
+
+/* Input scale sx and output scale sd (6 positive doubles each, host). */
+nv_status nv_mlp_set_scales(nv_mlp* mlp, const double* sx, const double* sd);
+
+/* Parameter vector (float32, layout in mlp.cu): count in *count; copied to
+ * host if host != NULL.  nv_mlp_set_params writes it back.  Synchronous. */
+nv_status nv_mlp_params(nv_mlp* mlp, float* host, int64_t* count);
+nv_status nv_mlp_set_params(nv_mlp* mlp, const float* host);
+
+/* Gradients of the half mean-squared loss on one batch: X_dev B x 8 floats
+ * (features, column 7 zero), Y_dev B x 8 floats (targets, columns 6, 7 zero),
+ * grads_dev receives the parameter-vector gradient.  B multiple of 128.
+ * Synchronous. */
+nv_status nv_mlp_grads(nv_mlp* mlp, const float* X_dev, const float* Y_dev, int32_t B, float* grads_dev,
+                       double* loss, void* stream);
+
+/* `steps` Adam steps (lr) on batches of B pairs drawn from the S x M float32
+ * pairs (S*M a power of two), replayed from a captured CUDA graph.  Returns
+ * the last batch's loss.  Synchronous. */
+nv_status nv_mlp_train(nv_mlp* mlp, const float* y0_dev, const float* yend_dev, int32_t S, int64_t M,
+                       int64_t steps, int32_t B, double lr, void* stream, double* last_loss);
+
+/* Per-slice relative error ||y0 + sd*MLP - y_end|| / ||y_end|| over Mv float64
+ * validation pairs per slice (S x Mv x 6 doubles each); err_host: S doubles.
+ * Mv multiple of 128.  Synchronous. */
+nv_status nv_mlp_validate(nv_mlp* mlp, const double* y0_dev, const double* yend_dev, int32_t S,
+                          int64_t Mv, double* err_host, void* stream);
+
+/* Composition with the learned map for `count` initial states (multiple of
+ * 128; y0_dev, yT_dev: count x 6 doubles): slice j advances
+ * lambda += sd*MLP(lambda/sx, j/S), or, where fallback[j] != 0 (host array of
+ * S flags, may be NULL), integrates the slice in float64. */
+nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, int32_t S,
+                         const nv_steps* steps, const int32_t* fallback, int64_t count,
+                         const double* y0_dev, double* yT_dev, void* stream);
+
 /* Largest state dimension nv_compose_affine_noalloc accepts. */
 #define NVPIT_NOALLOC_MAX_DIM 4096
 

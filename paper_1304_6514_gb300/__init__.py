@@ -95,6 +95,19 @@ def load_library(path: str = LIB_PATH):
         "nv_batch_copy_out": [P, P, c_int64, P],
         "nv_batch_check": [P, P, POINTER(c_int64)],
         "nv_batch_destroy": [P],
+        "nv_build_pairs": [POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), c_int64,
+                           ctypes.c_uint64, c_double, c_double, P, P, P],
+        "nv_propagate": [POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), c_int32, c_int32,
+                         c_int64, P, P],
+        "nv_mlp_create": [ctypes.c_uint64, POINTER(c_void_p)],
+        "nv_mlp_destroy": [P],
+        "nv_mlp_set_scales": [P, P, P],
+        "nv_mlp_params": [P, P, POINTER(c_int64)],
+        "nv_mlp_set_params": [P, P],
+        "nv_mlp_grads": [P, P, P, c_int32, P, POINTER(c_double), P],
+        "nv_mlp_train": [P, P, P, c_int32, c_int64, c_int64, c_int32, c_double, P, POINTER(c_double)],
+        "nv_mlp_validate": [P, P, P, c_int32, c_int64, P, P],
+        "nv_mlp_compose": [P, POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), P, c_int64, P, P, P],
         "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
                           POINTER(c_double)],
     }
@@ -366,3 +379,96 @@ def batch_check(batch: Batch, stream=None) -> int:
     n = c_int64(0)
     _check(load_library().nv_batch_check(batch.handle, _stream(stream), byref(n)))
     return n.value
+
+
+# ------------------------------------------------------------------ learned propagator
+
+def _dptr(t):
+    """Device pointer of any contiguous CUDA tensor (float32 / float64)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def build_pairs(rhs_, t0, T, S, steps_, M, seed, lo, hi, y0, yend, stream=None):
+    """nv_build_pairs into y0 / yend (S*M*6 float32 or float64 CUDA tensors)."""
+    _check(load_library().nv_build_pairs(byref(rhs_), t0, T, S, byref(steps_), M, seed, lo, hi, _dptr(y0),
+                                         _dptr(yend), _stream(stream)))
+
+
+def propagate(rhs_, t0, T, S, steps_, j0, nslices, y, stream=None):
+    """nv_propagate: float64 fine integration of the states y (count x 6, in place)."""
+    _check(load_library().nv_propagate(byref(rhs_), t0, T, S, byref(steps_), j0, nslices, y.shape[0], _ptr(y),
+                                       _stream(stream)))
+
+
+class MLP:
+    """The slice-conditioned MLP propagator (nv_mlp)."""
+
+    def __init__(self, seed: int = 0):
+        h = c_void_p()
+        _check(load_library().nv_mlp_create(seed, byref(h)))
+        self.handle = h.value
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(load_library().nv_mlp_destroy(h))
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.nv_mlp_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def set_scales(self, sx, sd):
+        a = (c_double * 6)(*sx)
+        b = (c_double * 6)(*sd)
+        _check(load_library().nv_mlp_set_scales(self.handle, a, b))
+
+    def params(self):
+        import numpy as np
+        n = c_int64(0)
+        _check(load_library().nv_mlp_params(self.handle, None, byref(n)))
+        out = np.empty(n.value, dtype=np.float32)
+        _check(load_library().nv_mlp_params(self.handle, out.ctypes.data, byref(n)))
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load_library().nv_mlp_set_params(self.handle, p.ctypes.data))
+
+    def grads(self, X, Y, stream=None):
+        import torch
+        n = c_int64(0)
+        _check(load_library().nv_mlp_params(self.handle, None, byref(n)))
+        g = torch.empty(n.value, dtype=torch.float32, device="cuda")
+        loss = c_double(0.0)
+        _check(load_library().nv_mlp_grads(self.handle, _dptr(X), _dptr(Y), X.shape[0], _dptr(g), byref(loss),
+                                           _stream(stream)))
+        return g, loss.value
+
+    def train(self, y0, yend, S, M, steps, batch, lr, stream=None):
+        loss = c_double(0.0)
+        _check(load_library().nv_mlp_train(self.handle, _dptr(y0), _dptr(yend), S, M, steps, batch, lr,
+                                           _stream(stream), byref(loss)))
+        return loss.value
+
+    def validate(self, y0, yend, S, Mv, stream=None):
+        import numpy as np
+        err = np.zeros(S, dtype=np.float64)
+        _check(load_library().nv_mlp_validate(self.handle, _dptr(y0), _dptr(yend), S, Mv, err.ctypes.data,
+                                              _stream(stream)))
+        return err
+
+    def compose(self, rhs_, t0, T, S, steps_, y0, yT, fallback=None, stream=None):
+        import numpy as np
+        fb = None
+        if fallback is not None:
+            fb = np.ascontiguousarray(fallback, dtype=np.int32)
+        _check(load_library().nv_mlp_compose(self.handle, byref(rhs_), t0, T, S, byref(steps_),
+                                             fb.ctypes.data if fb is not None else None, y0.shape[0], _ptr(y0),
+                                             _ptr(yT), _stream(stream)))

@@ -58,6 +58,11 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Right-hand-side parameters passed by value to kernels.
+struct RhsParams {
+  double p[NVPIT_MAX_PARAMS];
+};
+
 // ---------------------------------------------------------------------------
 // Right-hand sides of the table workloads, f(c, y) with c a staged
 // time-dependent coefficient (cos t for the cos-cubic problem).

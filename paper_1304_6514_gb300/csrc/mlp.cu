@@ -1,0 +1,697 @@
+// Learned slice propagator: a slice-conditioned MLP stands in for the table
+// map when the initial-value space has many dimensions (a uniform table with
+// l points per axis costs l^r solves, Section 4).  The method itself produces
+// the training data: pairs (xi, g^j(xi)) from the same per-(slice, sample)
+// integrator as the tables.
+//
+// Network: x = (y0 / sx, T_{j-1}/T) in R^7 -> 256 -> 256 -> 256 -> R^6 with
+// GELU, output the increment (y_end - y0) / sd.  Layers 2 and 3 (97 % of the
+// work) run as bf16 tensor-core GEMMs with float32 accumulation (gemm.cu) in
+// the forward and the backward pass; layers 1 and 4 (K = 7, N = 6) run on the
+// CUDA cores.  Adam keeps float32 master weights and refreshes the bf16 copies
+// (row-major for the forward GEMM, transposed for the backward one).
+//
+// Parameter vector (float32, [out][in] weights):
+//   W1 256x8 (column 7 zero) | b1 256 | W2 256x256 | b2 256 | W3 256x256 | b3 256
+//   | W4 8x256 (rows 6, 7 zero) | b4 8
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int splits, int mode, float* out32,
+                           const float* bias, float* zsave, const float* zin, void* out_bf, void* out_bfT,
+                           float* dbias, int* status, cudaStream_t s);
+nv_status gemm_bf16_prepare();
+
+namespace nvpit {
+namespace mlp {
+
+constexpr int H = 256, IN = 8, OUT = 8, D = 6;
+constexpr int64_t oW1 = 0, ob1 = oW1 + H * IN, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
+                  ob3 = oW3 + H * H, oW4 = ob3 + H, ob4 = oW4 + OUT * H, NP = ob4 + OUT;
+constexpr int kModeAtomic = 0, kModeFwdTrain = 1, kModeBwd = 2, kModeFwdInfer = 3;
+
+__device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double u01(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// ---- training pairs: sample k of slice j, component c is SplitMix64 output
+// (j*M + k)*D + c of the seed, mapped to [lo, hi]; integrated over slice j.
+template <typename T>
+__global__ void pairs_kernel(RhsParams pp, double h, int S, int64_t M, int64_t m, int rk4, uint64_t seed,
+                             double lo, double hi, T* y0o, T* yeo) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)S * M) return;
+  const RhsChain3<T> rhs(pp.p);
+  T y[D], comp[D];
+  for (int c = 0; c < D; ++c) {
+    y[c] = (T)(lo + (hi - lo) * u01(splitmix(seed, (uint64_t)(idx * D + c))));
+    comp[c] = 0;
+    y0o[idx * D + c] = y[c];
+  }
+  const T hT = (T)h;
+  for (int64_t i = 0; i < m; ++i) {
+    if (rk4) rk4_step(rhs, (T)0, (T)0, (T)0, hT, y, comp);
+    else euler_step(rhs, (T)0, hT, y, comp);
+  }
+  for (int c = 0; c < D; ++c) yeo[idx * D + c] = y[c];
+}
+
+// ---- float64 propagation of `count` states over slices [j0, j0 + ns)
+template <class R>
+__global__ void propagate_kernel(RhsParams pp, double h, int64_t m, int ns, int rk4, int64_t count,
+                                 double* y) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const R rhs(pp.p);
+  double s[R::D], comp[R::D];
+  for (int c = 0; c < R::D; ++c) { s[c] = y[idx * R::D + c]; comp[c] = 0.0; }
+  for (int64_t i = 0; i < (int64_t)ns * m; ++i) {
+    if (rk4) rk4_step(rhs, 0.0, 0.0, 0.0, h, s, comp);
+    else euler_step(rhs, 0.0, h, s, comp);
+  }
+  for (int c = 0; c < R::D; ++c) y[idx * R::D + c] = s[c];
+}
+
+// ---- parameters
+__global__ void init_params_kernel(float* P, uint64_t seed) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= NP) return;
+  double bound;
+  bool zero = false;
+  if (i < ob1) { bound = 1.0 / sqrt(7.0); zero = (i % IN) >= 7; }
+  else if (i < oW2) bound = 1.0 / sqrt(7.0);
+  else if (i < oW4) bound = 1.0 / 16.0;
+  else if (i < ob4) { bound = 1.0 / 16.0; zero = (i - oW4) / H >= D; }
+  else { bound = 1.0 / 16.0; zero = (i - ob4) >= D; }
+  P[i] = zero ? 0.f : (float)(bound * (2.0 * u01(splitmix(seed, (uint64_t)i)) - 1.0));
+}
+
+__global__ void pack_kernel(const float* P, __nv_bfloat16* W2b, __nv_bfloat16* W3b, __nv_bfloat16* W2t,
+                            __nv_bfloat16* W3t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H * H) return;
+  const int r = i / H, c = i % H;
+  const __nv_bfloat16 a = __float2bfloat16(P[oW2 + i]), b = __float2bfloat16(P[oW3 + i]);
+  W2b[i] = a;
+  W3b[i] = b;
+  W2t[c * H + r] = a;
+  W3t[c * H + r] = b;
+}
+
+// ---- training batch: sample (a * (step*B + b) + 1) mod N of the pairs
+__global__ void gather_kernel(const float* y0, const float* ye, int64_t N, int64_t M, int S, const int* step,
+                              int B, const float* sx_inv, const float* sd_inv, float* X, float* Y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const uint64_t g = (uint64_t)(*step) * (uint64_t)B + (uint64_t)b;
+  const int64_t idx = (int64_t)((g * 2654435761ull + 1ull) & (uint64_t)(N - 1));   // N is a power of two
+  const int j = (int)(idx / M);
+  for (int c = 0; c < D; ++c) {
+    const float a0 = y0[idx * D + c];
+    X[b * IN + c] = a0 * sx_inv[c];
+    Y[b * OUT + c] = (ye[idx * D + c] - a0) * sd_inv[c];
+  }
+  X[b * IN + 6] = (float)j / (float)S;
+  X[b * IN + 7] = 0.f;
+  Y[b * OUT + 6] = Y[b * OUT + 7] = 0.f;
+}
+
+// layer 1: Z1 = X W1^T + b1 (K = 8), H1 = GELU(Z1)
+__global__ void l1_fwd_kernel(const float* P, const float* X, int B, float* Z1, __nv_bfloat16* H1,
+                              __nv_bfloat16* H1t, int train) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * H) return;
+  const int b = (int)(i / H), n = (int)(i % H);
+  float z = P[ob1 + n];
+#pragma unroll
+  for (int k = 0; k < IN; ++k) z = fmaf(P[oW1 + n * IN + k], X[b * IN + k], z);
+  const __nv_bfloat16 hb = __float2bfloat16(gelu_f(z));
+  H1[i] = hb;
+  if (train) {
+    Z1[i] = z;
+    H1t[(int64_t)n * B + b] = hb;
+  }
+}
+
+// layer 4 forward (+ loss and backward to dZ3 when training): one warp per
+// sample, lane l holds hidden units 8l .. 8l+7.
+__global__ void l4_kernel(const float* P, const __nv_bfloat16* H3, const float* Z3, const float* Y, int B,
+                          float* out, float* dOut, __nv_bfloat16* dZ3, __nv_bfloat16* dZ3t, float* loss,
+                          int train) {
+  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int b = warp;
+  float h[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) h[q] = __bfloat162float(H3[(int64_t)b * H + lane * 8 + q]);
+  float o[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(P[oW4 + c * H + lane * 8 + q], h[q], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    o[c] = s + P[ob4 + c];
+  }
+  if (!train) {
+    if (lane < D) out[b * OUT + lane] = o[lane];
+    return;
+  }
+  float r[D], l = 0.f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    r[c] = o[c] - Y[b * OUT + c];
+    l += 0.5f * r[c] * r[c];
+    r[c] /= (float)B;
+  }
+  if (lane == 0) atomicAdd(loss, l / (float)B);
+  if (lane < D) dOut[b * OUT + lane] = r[lane];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int k = lane * 8 + q;
+    float dh = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) dh = fmaf(r[c], P[oW4 + c * H + k], dh);
+    const float dz = dh * gelu_grad_f(Z3[(int64_t)b * H + k]);
+    const __nv_bfloat16 db = __float2bfloat16(dz);
+    dZ3[(int64_t)b * H + k] = db;
+    dZ3t[(int64_t)k * B + b] = db;
+  }
+}
+
+// dW4 = dOut^T H3, db4 = column sums of dOut (thread per (output, unit))
+__global__ void l4_wgrad_kernel(const float* dOut, const __nv_bfloat16* H3t, int B, float* G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D * H + D) return;
+  if (i < D * H) {
+    const int c = i / H, k = i % H;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s = fmaf(dOut[b * OUT + c], __bfloat162float(H3t[(int64_t)k * B + b]), s);
+    G[oW4 + c * H + k] += s;
+  } else {
+    const int c = i - D * H;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dOut[b * OUT + c];
+    G[ob4 + c] += s;
+  }
+}
+
+// column sums of a transposed bf16 matrix (rows n, B columns) into G[off + n]
+__global__ void colsum_kernel(const __nv_bfloat16* Mt, int B, float* G, int64_t off) {
+  __shared__ float red[256];
+  const int n = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += __bfloat162float(Mt[(int64_t)n * B + b]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) G[off + n] += red[0];
+}
+
+// dW1 = dZ1^T X (thread per (unit, input))
+__global__ void l1_wgrad_kernel(const __nv_bfloat16* dZ1t, const float* X, int B, float* G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H * 7) return;
+  const int n = i / 7, k = i % 7;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s = fmaf(__bfloat162float(dZ1t[(int64_t)n * B + b]), X[b * IN + k], s);
+  G[oW1 + n * IN + k] += s;
+}
+
+__global__ void adam_kernel(float* P, float* G, float* Mm, float* Vv, int* step, float lr) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int t = *step + 1;
+  if (i < NP) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float g = G[i];
+    const float m = b1 * Mm[i] + (1.f - b1) * g;
+    const float v = b2 * Vv[i] + (1.f - b2) * g * g;
+    Mm[i] = m;
+    Vv[i] = v;
+    const float mh = m / (1.f - powf(b1, (float)t)), vh = v / (1.f - powf(b2, (float)t));
+    P[i] -= lr * mh / (sqrtf(vh) + eps);
+    G[i] = 0.f;
+  }
+}
+
+__global__ void step_kernel(int* step) { *step += 1; }
+
+// composition: lambda <- lambda + sd * MLP(lambda / sx, j / S) on `count` states
+__global__ void features_kernel(const double* lam, int64_t count, int j, int S, const float* sx_inv, float* X) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  for (int c = 0; c < D; ++c) X[b * IN + c] = (float)lam[b * D + c] * sx_inv[c];
+  X[b * IN + 6] = (float)j / (float)S;
+  X[b * IN + 7] = 0.f;
+}
+
+__global__ void advance_kernel(double* lam, int64_t count, const float* out, const double* sd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count * D) return;
+  const int64_t b = i / D;
+  const int c = (int)(i % D);
+  lam[i] += sd[c] * (double)out[b * OUT + c];
+}
+
+// per-slice relative error of the learned map against float64 end states
+__global__ void val_err_kernel(const double* y0, const double* ye, const float* out, const double* sd,
+                               int64_t n, double* num, double* den) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e = 0.0, r = 0.0;
+  if (b < n) {
+    for (int c = 0; c < D; ++c) {
+      const double pred = y0[b * D + c] + sd[c] * (double)out[b * OUT + c];
+      const double d = pred - ye[b * D + c];
+      e += d * d;
+      r += ye[b * D + c] * ye[b * D + c];
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, off);
+    r += __shfl_xor_sync(0xffffffffu, r, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(num, e);
+    atomicAdd(den, r);
+  }
+}
+
+}  // namespace mlp
+}  // namespace nvpit
+
+using namespace nvpit;
+using namespace nvpit::mlp;
+
+struct nv_mlp {
+  float *P, *G, *Mm, *Vv;
+  __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
+  float *sx_inv, *sd_inv;     // device, 6 floats each
+  double* sd;                 // device, 6 doubles
+  double sx_h[D], sd_h[D];
+  int* step;
+  int* status;
+  float* loss;
+  // batch buffers
+  int B;
+  float *X, *Y, *Z1, *Z2, *Z3, *out, *dOut;
+  __nv_bfloat16 *H1, *H2, *H3, *H1t, *H2t, *H3t, *dZ1, *dZ2, *dZ3, *dZ1t, *dZ2t, *dZ3t;
+  cudaGraphExec_t train_graph;
+  const float *graph_y0, *graph_ye;
+  int64_t graph_N, graph_M;
+  int graph_S;
+  float graph_lr;
+};
+
+static void mlp_free_batch(nv_mlp* m) {
+  void* bufs[] = {m->X, m->Y, m->Z1, m->Z2, m->Z3, m->out, m->dOut, m->H1, m->H2, m->H3, m->H1t, m->H2t,
+                  m->H3t, m->dZ1, m->dZ2, m->dZ3, m->dZ1t, m->dZ2t, m->dZ3t};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  m->X = m->Y = m->Z1 = m->Z2 = m->Z3 = m->out = m->dOut = nullptr;
+  m->H1 = m->H2 = m->H3 = m->H1t = m->H2t = m->H3t = nullptr;
+  m->dZ1 = m->dZ2 = m->dZ3 = m->dZ1t = m->dZ2t = m->dZ3t = nullptr;
+  m->B = 0;
+  if (m->train_graph) {
+    cudaGraphExecDestroy(m->train_graph);
+    m->train_graph = nullptr;
+  }
+}
+
+static nv_status mlp_batch(nv_mlp* m, int B) {
+  if (B == m->B) return NV_OK;
+  mlp_free_batch(m);
+  const size_t bf = sizeof(__nv_bfloat16), f = sizeof(float);
+  struct { void** p; size_t bytes; } req[] = {
+      {(void**)&m->X, f * B * IN}, {(void**)&m->Y, f * B * OUT}, {(void**)&m->Z1, f * B * H},
+      {(void**)&m->Z2, f * B * H}, {(void**)&m->Z3, f * B * H}, {(void**)&m->out, f * B * OUT},
+      {(void**)&m->dOut, f * B * OUT}, {(void**)&m->H1, bf * B * H}, {(void**)&m->H2, bf * B * H},
+      {(void**)&m->H3, bf * B * H}, {(void**)&m->H1t, bf * B * H}, {(void**)&m->H2t, bf * B * H},
+      {(void**)&m->H3t, bf * B * H}, {(void**)&m->dZ1, bf * B * H}, {(void**)&m->dZ2, bf * B * H},
+      {(void**)&m->dZ3, bf * B * H}, {(void**)&m->dZ1t, bf * B * H}, {(void**)&m->dZ2t, bf * B * H},
+      {(void**)&m->dZ3t, bf * B * H}};
+  for (auto& r : req) {
+    nv_status st = nv_cuda_check(cudaMalloc(r.p, r.bytes), "mlp batch buffers");
+    if (st != NV_OK) {
+      mlp_free_batch(m);
+      return st;
+    }
+  }
+  m->B = B;
+  return NV_OK;
+}
+
+static nv_status mlp_pack(nv_mlp* m, cudaStream_t s) {
+  pack_kernel<<<(H * H + 255) / 256, 256, 0, s>>>(m->P, m->W2b, m->W3b, m->W2t, m->W3t);
+  return nv_cuda_check(cudaGetLastError(), "mlp pack");
+}
+
+// forward (+ backward when train) of the batch already in m->X (and m->Y)
+static nv_status mlp_fwd_bwd(nv_mlp* m, int train, cudaStream_t s) {
+  const int B = m->B;
+  nv_status st;
+  const int64_t nBH = (int64_t)B * H;
+  l1_fwd_kernel<<<(unsigned)((nBH + 255) / 256), 256, 0, s>>>(m->P, m->X, B, m->Z1, m->H1, m->H1t, train);
+  if ((st = nv_cuda_check(cudaGetLastError(), "l1 forward")) != NV_OK) return st;
+  const int fm = train ? kModeFwdTrain : kModeFwdInfer;
+  if ((st = launch_gemm_bf16(m->H1, m->W2b, B, H, 1, fm, nullptr, m->P + ob2, m->Z2, nullptr, m->H2, m->H2t,
+                             nullptr, m->status, s)) != NV_OK)
+    return st;
+  if ((st = launch_gemm_bf16(m->H2, m->W3b, B, H, 1, fm, nullptr, m->P + ob3, m->Z3, nullptr, m->H3, m->H3t,
+                             nullptr, m->status, s)) != NV_OK)
+    return st;
+  l4_kernel<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(m->P, m->H3, m->Z3, m->Y, B, m->out, m->dOut, m->dZ3,
+                                                             m->dZ3t, m->loss, train);
+  if ((st = nv_cuda_check(cudaGetLastError(), "l4")) != NV_OK) return st;
+  if (!train) return NV_OK;
+  l4_wgrad_kernel<<<(D * H + D + 255) / 256, 256, 0, s>>>(m->dOut, m->H3t, B, m->G);
+  colsum_kernel<<<H, 256, 0, s>>>(m->dZ3t, B, m->G, ob3);
+  if ((st = nv_cuda_check(cudaGetLastError(), "l4 weight gradients")) != NV_OK) return st;
+  const int splits = std::max(1, std::min(16, B / 256));
+  // dW3 = dZ3^T H2, dH2 = dZ3 W3 -> dZ2 (db2 in the epilogue)
+  if ((st = launch_gemm_bf16(m->dZ3t, m->H2t, H, B, splits, kModeAtomic, m->G + oW3, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, m->status, s)) != NV_OK)
+    return st;
+  if ((st = launch_gemm_bf16(m->dZ3, m->W3t, B, H, 1, kModeBwd, nullptr, nullptr, nullptr, m->Z2, m->dZ2, m->dZ2t,
+                             m->G + ob2, m->status, s)) != NV_OK)
+    return st;
+  // dW2 = dZ2^T H1, dH1 = dZ2 W2 -> dZ1 (db1 in the epilogue)
+  if ((st = launch_gemm_bf16(m->dZ2t, m->H1t, H, B, splits, kModeAtomic, m->G + oW2, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, m->status, s)) != NV_OK)
+    return st;
+  if ((st = launch_gemm_bf16(m->dZ2, m->W2t, B, H, 1, kModeBwd, nullptr, nullptr, nullptr, m->Z1, m->dZ1, m->dZ1t,
+                             m->G + ob1, m->status, s)) != NV_OK)
+    return st;
+  l1_wgrad_kernel<<<(H * 7 + 255) / 256, 256, 0, s>>>(m->dZ1t, m->X, B, m->G);
+  return nv_cuda_check(cudaGetLastError(), "l1 weight gradients");
+}
+
+extern "C" nv_status nv_mlp_create(uint64_t seed, nv_mlp** out) {
+  if (!out) return nv_fail(NV_EINVAL, "out is NULL");
+  nv_mlp* m = new (std::nothrow) nv_mlp();
+  if (!m) return nv_fail(NV_ENOMEM, "host allocation of the MLP");
+  const size_t f = sizeof(float), bf = sizeof(__nv_bfloat16);
+  struct { void** p; size_t bytes; } req[] = {
+      {(void**)&m->P, f * NP}, {(void**)&m->G, f * NP}, {(void**)&m->Mm, f * NP}, {(void**)&m->Vv, f * NP},
+      {(void**)&m->W2b, bf * H * H}, {(void**)&m->W3b, bf * H * H}, {(void**)&m->W2t, bf * H * H},
+      {(void**)&m->W3t, bf * H * H}, {(void**)&m->sx_inv, f * 8}, {(void**)&m->sd_inv, f * 8},
+      {(void**)&m->sd, sizeof(double) * 8}, {(void**)&m->step, 256}, {(void**)&m->status, 256},
+      {(void**)&m->loss, 256}};
+  for (auto& r : req) {
+    nv_status st = nv_cuda_check(cudaMalloc(r.p, r.bytes), "mlp allocation");
+    if (st != NV_OK) {
+      nv_mlp_destroy(m);
+      return st;
+    }
+  }
+  init_params_kernel<<<(unsigned)((NP + 255) / 256), 256>>>(m->P, seed);
+  cudaMemset(m->G, 0, f * NP);
+  cudaMemset(m->Mm, 0, f * NP);
+  cudaMemset(m->Vv, 0, f * NP);
+  cudaMemset(m->step, 0, 256);
+  cudaMemset(m->status, 0, 256);
+  cudaMemset(m->loss, 0, 256);
+  for (int c = 0; c < D; ++c) m->sx_h[c] = m->sd_h[c] = 1.0;
+  nv_status st = nv_mlp_set_scales(m, m->sx_h, m->sd_h);
+  if (st == NV_OK) st = gemm_bf16_prepare();
+  if (st == NV_OK) st = mlp_pack(m, 0);
+  if (st == NV_OK) st = nv_cuda_check(cudaDeviceSynchronize(), "mlp init");
+  if (st != NV_OK) {
+    nv_mlp_destroy(m);
+    return st;
+  }
+  *out = m;
+  return NV_OK;
+}
+
+extern "C" nv_status nv_mlp_destroy(nv_mlp* m) {
+  if (!m) return NV_OK;
+  cudaDeviceSynchronize();
+  mlp_free_batch(m);
+  void* bufs[] = {m->P, m->G, m->Mm, m->Vv, m->W2b, m->W3b, m->W2t, m->W3t, m->sx_inv, m->sd_inv, m->sd,
+                  m->step, m->status, m->loss};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete m;
+  return NV_OK;
+}
+
+extern "C" nv_status nv_mlp_set_scales(nv_mlp* m, const double* sx, const double* sd) {
+  if (!m || !sx || !sd) return nv_fail(NV_EINVAL, "NULL argument");
+  float fx[8] = {0}, fd[8] = {0};
+  double dd[8] = {0};
+  for (int c = 0; c < D; ++c) {
+    if (!(sx[c] > 0) || !(sd[c] > 0)) return nv_fail(NV_EINVAL, "scales must be positive");
+    m->sx_h[c] = sx[c];
+    m->sd_h[c] = sd[c];
+    fx[c] = (float)(1.0 / sx[c]);
+    fd[c] = (float)(1.0 / sd[c]);
+    dd[c] = sd[c];
+  }
+  nv_status st = nv_cuda_check(cudaMemcpy(m->sx_inv, fx, sizeof(fx), cudaMemcpyHostToDevice), "scales");
+  if (st == NV_OK) st = nv_cuda_check(cudaMemcpy(m->sd_inv, fd, sizeof(fd), cudaMemcpyHostToDevice), "scales");
+  if (st == NV_OK) st = nv_cuda_check(cudaMemcpy(m->sd, dd, sizeof(dd), cudaMemcpyHostToDevice), "scales");
+  return st;
+}
+
+extern "C" nv_status nv_mlp_params(nv_mlp* m, float* host, int64_t* count) {
+  if (!m) return nv_fail(NV_EINVAL, "mlp is NULL");
+  if (count) *count = NP;
+  if (!host) return NV_OK;
+  return nv_cuda_check(cudaMemcpy(host, m->P, sizeof(float) * NP, cudaMemcpyDeviceToHost), "params read");
+}
+
+extern "C" nv_status nv_mlp_set_params(nv_mlp* m, const float* host) {
+  if (!m || !host) return nv_fail(NV_EINVAL, "NULL argument");
+  nv_status st = nv_cuda_check(cudaMemcpy(m->P, host, sizeof(float) * NP, cudaMemcpyHostToDevice), "params write");
+  if (st == NV_OK) st = mlp_pack(m, 0);
+  if (st == NV_OK) st = nv_cuda_check(cudaDeviceSynchronize(), "params write");
+  return st;
+}
+
+extern "C" nv_status nv_mlp_grads(nv_mlp* m, const float* X_dev, const float* Y_dev, int32_t B, float* grads_dev,
+                                  double* loss, void* stream) {
+  if (!m || !X_dev || !Y_dev || !grads_dev) return nv_fail(NV_EINVAL, "NULL argument");
+  if (B < 128 || B % 128) return nv_fail(NV_EINVAL, "batch must be a positive multiple of 128");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  nv_status st = mlp_batch(m, B);
+  if (st != NV_OK) return st;
+  cudaMemcpyAsync(m->X, X_dev, sizeof(float) * B * IN, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(m->Y, Y_dev, sizeof(float) * B * OUT, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s);
+  cudaMemsetAsync(m->loss, 0, sizeof(float), s);
+  if ((st = mlp_fwd_bwd(m, 1, s)) != NV_OK) return st;
+  cudaMemcpyAsync(grads_dev, m->G, sizeof(float) * NP, cudaMemcpyDeviceToDevice, s);
+  float l = 0.f;
+  cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+  if ((st = nv_cuda_check(cudaStreamSynchronize(s), "mlp grads")) != NV_OK) return st;
+  cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s);
+  if (loss) *loss = l;
+  int dst = 0;
+  cudaMemcpy(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (dst != NV_OK) return nv_fail((nv_status)dst, "device status %d in the MLP kernels", dst);
+  return NV_OK;
+}
+
+// One training step: gather, forward, backward, Adam, repack, step += 1.
+static nv_status mlp_train_step(nv_mlp* m, const float* y0, const float* ye, int64_t N, int64_t M, int S, float lr,
+                                cudaStream_t s) {
+  const int B = m->B;
+  gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(y0, ye, N, M, S, m->step, B, m->sx_inv, m->sd_inv, m->X, m->Y);
+  nv_status st = nv_cuda_check(cudaGetLastError(), "gather");
+  if (st != NV_OK) return st;
+  if ((st = mlp_fwd_bwd(m, 1, s)) != NV_OK) return st;
+  adam_kernel<<<(unsigned)((NP + 255) / 256), 256, 0, s>>>(m->P, m->G, m->Mm, m->Vv, m->step, lr);
+  if ((st = mlp_pack(m, s)) != NV_OK) return st;
+  step_kernel<<<1, 1, 0, s>>>(m->step);
+  return nv_cuda_check(cudaGetLastError(), "adam");
+}
+
+extern "C" nv_status nv_mlp_train(nv_mlp* m, const float* y0_dev, const float* yend_dev, int32_t S, int64_t M,
+                                  int64_t steps, int32_t B, double lr, void* stream, double* last_loss) {
+  if (!m || !y0_dev || !yend_dev) return nv_fail(NV_EINVAL, "NULL argument");
+  const int64_t N = (int64_t)S * M;
+  if (S < 1 || M < 1 || (N & (N - 1)) != 0) return nv_fail(NV_EINVAL, "S * M must be a power of two");
+  if (B < 128 || B % 128 || B > (1 << 20)) return nv_fail(NV_EINVAL, "batch must be a multiple of 128");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  nv_status st = mlp_batch(m, B);
+  if (st != NV_OK) return st;
+  // one training step is captured once into a CUDA graph and replayed
+  if (!m->train_graph || m->graph_y0 != y0_dev || m->graph_ye != yend_dev || m->graph_N != N ||
+      m->graph_M != M || m->graph_S != S || m->graph_lr != (float)lr) {
+    if (m->train_graph) {
+      cudaGraphExecDestroy(m->train_graph);
+      m->train_graph = nullptr;
+    }
+    cudaStream_t cap;
+    if ((st = nv_cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream")) != NV_OK)
+      return st;
+    cudaGraph_t g = nullptr;
+    st = nv_cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st == NV_OK) {
+      nv_status e1 = mlp_train_step(m, y0_dev, yend_dev, N, M, S, (float)lr, cap);
+      nv_status e2 = nv_cuda_check(cudaStreamEndCapture(cap, &g), "end capture");
+      st = e1 != NV_OK ? e1 : e2;
+    }
+    if (st == NV_OK) st = nv_cuda_check(cudaGraphInstantiate(&m->train_graph, g, 0), "graph instantiate");
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (st != NV_OK) {
+      m->train_graph = nullptr;
+      return st;
+    }
+    m->graph_y0 = y0_dev;
+    m->graph_ye = yend_dev;
+    m->graph_N = N;
+    m->graph_M = M;
+    m->graph_S = S;
+    m->graph_lr = (float)lr;
+  }
+  for (int64_t k = 0; k < steps; ++k) {
+    if (k == steps - 1) cudaMemsetAsync(m->loss, 0, sizeof(float), s);
+    if ((st = nv_cuda_check(cudaGraphLaunch(m->train_graph, s), "training step")) != NV_OK) return st;
+  }
+  float l = 0.f;
+  cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+  if ((st = nv_cuda_check(cudaStreamSynchronize(s), "training")) != NV_OK) return st;
+  if (last_loss) *last_loss = l;
+  int dst = 0;
+  cudaMemcpy(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (dst != NV_OK) return nv_fail((nv_status)dst, "device status %d in the MLP kernels", dst);
+  return NV_OK;
+}
+
+// Forward of the learned map on `count` states (count a multiple of 128) at
+// slice j: out = MLP(lam / sx, j / S) into m->out.
+static nv_status mlp_infer(nv_mlp* m, const double* lam, int64_t count, int j, int S, cudaStream_t s) {
+  features_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(lam, count, j, S, m->sx_inv, m->X);
+  nv_status st = nv_cuda_check(cudaGetLastError(), "features");
+  if (st != NV_OK) return st;
+  return mlp_fwd_bwd(m, 0, s);
+}
+
+extern "C" nv_status nv_mlp_validate(nv_mlp* m, const double* y0_dev, const double* yend_dev, int32_t S,
+                                     int64_t Mv, double* err_host, void* stream) {
+  if (!m || !y0_dev || !yend_dev || !err_host) return nv_fail(NV_EINVAL, "NULL argument");
+  if (Mv < 128 || Mv % 128) return nv_fail(NV_EINVAL, "validation samples per slice: multiple of 128");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  nv_status st = mlp_batch(m, (int)Mv);
+  if (st != NV_OK) return st;
+  double* acc = nullptr;
+  if ((st = nv_cuda_check(cudaMalloc(&acc, sizeof(double) * 2 * S), "validation accumulators")) != NV_OK) return st;
+  cudaMemsetAsync(acc, 0, sizeof(double) * 2 * S, s);
+  for (int j = 0; j < S && st == NV_OK; ++j) {
+    const double* y0j = y0_dev + (int64_t)j * Mv * D;
+    st = mlp_infer(m, y0j, Mv, j, S, s);
+    if (st != NV_OK) break;
+    val_err_kernel<<<(unsigned)((Mv + 255) / 256), 256, 0, s>>>(y0j, yend_dev + (int64_t)j * Mv * D, m->out, m->sd,
+                                                               Mv, acc + 2 * j, acc + 2 * j + 1);
+    st = nv_cuda_check(cudaGetLastError(), "validation");
+  }
+  std::vector<double> h(2 * S);
+  if (st == NV_OK)
+    st = nv_cuda_check(cudaMemcpyAsync(h.data(), acc, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, s), "read");
+  if (st == NV_OK) st = nv_cuda_check(cudaStreamSynchronize(s), "validation");
+  cudaFree(acc);
+  if (st != NV_OK) return st;
+  for (int j = 0; j < S; ++j) err_host[j] = sqrt(h[2 * j] / std::max(h[2 * j + 1], 1e-300));
+  return NV_OK;
+}
+
+static nv_status plan_rhs(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps, RhsParams* pp,
+                          int64_t* m, double* h) {
+  if (!rhs || !steps) return nv_fail(NV_EINVAL, "NULL argument");
+  if (rhs->kind != NV_RHS_CHAIN3 || rhs->dim != 6)
+    return nv_fail(NV_ENOTSUP, "pairs and the learned map are built for the 3-mass chain (dim 6)");
+  for (int i = 0; i < NVPIT_MAX_PARAMS; ++i) pp->p[i] = 0.0;
+  if (rhs->nparams == 0) {
+    pp->p[0] = 1.0;
+    pp->p[1] = 0.5;
+    pp->p[2] = 0.05;
+  } else {
+    if (rhs->nparams < 3 || !rhs->params) return nv_fail(NV_EINVAL, "chain rhs needs params {k, k3, c}");
+    for (int i = 0; i < 3; ++i) pp->p[i] = rhs->params[i];
+  }
+  if (steps->scheme != NV_EULER && steps->scheme != NV_RK4) return nv_fail(NV_EINVAL, "unknown scheme");
+  return nv_plan_steps(t0, T, S, steps->dt, steps->steps_per_slice, m, h);
+}
+
+extern "C" nv_status nv_build_pairs(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
+                                    int64_t M, uint64_t seed, double lo, double hi, void* y0_dev, void* yend_dev,
+                                    void* stream) {
+  RhsParams pp;
+  int64_t m = 0;
+  double h = 0;
+  nv_status st = plan_rhs(rhs, t0, T, S, steps, &pp, &m, &h);
+  if (st != NV_OK) return st;
+  if (M < 1 || !y0_dev || !yend_dev || !(hi > lo)) return nv_fail(NV_EINVAL, "bad sample arguments");
+  const int64_t n = (int64_t)S * M;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int rk4 = steps->scheme == NV_RK4;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (steps->prec == NV_FP64)
+    pairs_kernel<double><<<grid, 256, 0, s>>>(pp, h, S, M, m, rk4, seed, lo, hi, static_cast<double*>(y0_dev),
+                                              static_cast<double*>(yend_dev));
+  else if (steps->prec == NV_FP32)
+    pairs_kernel<float><<<grid, 256, 0, s>>>(pp, h, S, M, m, rk4, seed, lo, hi, static_cast<float*>(y0_dev),
+                                             static_cast<float*>(yend_dev));
+  else
+    return nv_fail(NV_EINVAL, "pairs are float64 or float32");
+  return nv_cuda_check(cudaGetLastError(), "pairs_kernel launch");
+}
+
+extern "C" nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
+                                  int32_t j0, int32_t nslices, int64_t count, double* y_dev, void* stream) {
+  RhsParams pp;
+  int64_t m = 0;
+  double h = 0;
+  nv_status st = plan_rhs(rhs, t0, T, S, steps, &pp, &m, &h);
+  if (st != NV_OK) return st;
+  if (!y_dev || count < 0 || j0 < 0 || nslices < 0 || j0 + nslices > S) return nv_fail(NV_EINVAL, "bad range");
+  if (count == 0 || nslices == 0) return NV_OK;
+  propagate_kernel<RhsChain3<double>><<<(unsigned)((count + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      pp, h, m, nslices, steps->scheme == NV_RK4, count, y_dev);
+  return nv_cuda_check(cudaGetLastError(), "propagate_kernel launch");
+}
+
+extern "C" nv_status nv_mlp_compose(nv_mlp* m, const nv_rhs* rhs, double t0, double T, int32_t S,
+                                    const nv_steps* steps, const int32_t* fallback, int64_t count,
+                                    const double* y0_dev, double* yT_dev, void* stream) {
+  if (!m || !y0_dev || !yT_dev) return nv_fail(NV_EINVAL, "NULL argument");
+  if (count < 128 || count % 128) return nv_fail(NV_EINVAL, "count must be a positive multiple of 128");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  nv_status st = mlp_batch(m, (int)count);
+  if (st != NV_OK) return st;
+  if ((st = nv_cuda_check(cudaMemcpyAsync(yT_dev, y0_dev, sizeof(double) * count * D, cudaMemcpyDeviceToDevice, s),
+                          "state copy")) != NV_OK)
+    return st;
+  for (int j = 0; j < S; ++j) {
+    if (fallback && fallback[j]) {
+      if ((st = nv_propagate(rhs, t0, T, S, steps, j, 1, count, yT_dev, stream)) != NV_OK) return st;
+      continue;
+    }
+    if ((st = mlp_infer(m, yT_dev, count, j, S, s)) != NV_OK) return st;
+    advance_kernel<<<(unsigned)((count * D + 255) / 256), 256, 0, s>>>(yT_dev, count, m->out, m->sd);
+    if ((st = nv_cuda_check(cudaGetLastError(), "advance")) != NV_OK) return st;
+  }
+  return NV_OK;
+}

@@ -1,0 +1,135 @@
+"""GPU parity of the learned-propagator path: training pairs from the method's
+integrator, float64 propagation (judge and fallback), and the MLP's bf16
+tensor-core forward/backward gradients against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import paper_1304_6514_gb300 as nvp
+import workloads
+from oracle import mlp as omlp
+from oracle import nievergelt as nv
+
+from gpu_util import need_gpu, rel_l2, rel_max
+
+pytestmark = pytest.mark.gpu
+
+H, IN = 256, 8
+OFF = {"W1": 0, "b1": H * IN, "W2": H * IN + H, "b2": H * IN + H + H * H, "W3": H * IN + 2 * H + H * H,
+       "b3": H * IN + 2 * H + 2 * H * H, "W4": H * IN + 3 * H + 2 * H * H, "b4": H * IN + 3 * H + 2 * H * H + 8 * H}
+
+
+def unflatten(v):
+    """GPU parameter vector -> oracle dict ([out, in] weights, padding removed)."""
+    v = np.asarray(v, dtype=np.float64)
+    return {"W1": v[OFF["W1"]:OFF["b1"]].reshape(H, IN)[:, :7], "b1": v[OFF["b1"]:OFF["W2"]],
+            "W2": v[OFF["W2"]:OFF["b2"]].reshape(H, H), "b2": v[OFF["b2"]:OFF["W3"]],
+            "W3": v[OFF["W3"]:OFF["b3"]].reshape(H, H), "b3": v[OFF["b3"]:OFF["W4"]],
+            "W4": v[OFF["W4"]:OFF["b4"]].reshape(8, H)[:6], "b4": v[OFF["b4"]:OFF["b4"] + 6]}
+
+
+def _bf16(x):
+    a = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_pairs_match_oracle(prec, tol):
+    """Samples are the published SplitMix64 stream (bit-exact); end states are
+    the oracle's RK4 solves over each slice."""
+    torch = need_gpu()
+    S, M, seed = 3, 256, 3
+    w = workloads.chain3(S=S, M=M, T=3 * 0.15625)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    y0 = torch.empty(S * M * 6, dtype=dt, device="cuda")
+    ye = torch.empty_like(y0)
+    nvp.build_pairs(nvp.rhs("chain3", 6), w.t0, w.T, S, nvp.steps("rk4", w.dt, 0, prec), M, seed, -1.0, 1.0,
+                    y0, ye)
+    torch.cuda.synchronize()
+    g0 = y0.cpu().numpy().reshape(S, M, 6)
+    ge = ye.cpu().numpy().reshape(S, M, 6)
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, S, m)
+    Tj = nv.slice_times(w.t0, w.T, S)
+    f = nv.rhs_chain3(*w.params)
+    for j in range(S):
+        xs = workloads.chain3_samples(seed, S, M, j)                 # (6, M)
+        if prec == "fp64":
+            assert np.array_equal(g0[j], xs.T)
+        oe = nv.integrate(f, "rk4", Tj[j], xs, h, m)
+        assert rel_max(ge[j], oe.T) <= tol, j
+
+
+def test_propagate_matches_oracle():
+    torch = need_gpu()
+    S = 4
+    w = workloads.chain3(S=S, M=128, T=4 * 0.15625)
+    rng = np.random.default_rng(7)
+    Y0 = rng.uniform(-1, 1, (256, 6))
+    y = torch.tensor(Y0, dtype=torch.float64, device="cuda")
+    nvp.propagate(nvp.rhs("chain3", 6), w.t0, w.T, S, nvp.steps("rk4", w.dt), 1, 3, y)
+    torch.cuda.synchronize()
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, S, m)
+    f = nv.rhs_chain3(*w.params)
+    oy = Y0.T.copy()
+    for j in range(1, 4):
+        oy = nv.integrate(f, "rk4", nv.slice_times(w.t0, w.T, S)[j], oy, h, m)
+    assert rel_max(y.cpu().numpy(), oy.T) <= 1e-11
+
+
+def test_mlp_gradients_match_oracle():
+    """Forward and backward of the GPU network (bf16 tensor-core layers 2, 3)
+    against the FP64 oracle given the same bf16-rounded weights: loss and every
+    parameter gradient within 2e-2 relative (bf16 activations carry 2^-9)."""
+    torch = need_gpu()
+    net = nvp.MLP(seed=5)
+    P = net.params()
+    rng = np.random.default_rng(11)
+    B = 256
+    X = np.zeros((B, IN), dtype=np.float32)
+    X[:, :6] = rng.uniform(-1.7, 1.7, (B, 6))
+    X[:, 6] = rng.uniform(0, 1, B)
+    Y = np.zeros((B, 8), dtype=np.float32)
+    Y[:, :6] = rng.normal(0, 1, (B, 6))
+    g, loss = net.grads(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    G = unflatten(g.cpu().numpy())
+    p = unflatten(P)
+    p["W2"], p["W3"] = _bf16(p["W2"]), _bf16(p["W3"])
+    oloss, og = omlp.loss_and_grads(p, X[:, :7].astype(np.float64), Y[:, :6].astype(np.float64))
+    assert abs(loss - oloss) <= 1e-2 * abs(oloss)
+    for k in og:
+        assert rel_l2(G[k], og[k]) <= 2e-2, k
+    net.destroy()
+
+
+def test_mlp_forward_matches_oracle_and_full_fallback_is_exact():
+    """Composition through the learned map equals the oracle's map applied
+    slice by slice (to bf16 tolerance), and with every slice on the fallback it
+    equals the float64 fine solve exactly."""
+    torch = need_gpu()
+    S, count = 3, 256
+    w = workloads.chain3(S=S, M=128, T=3 * 0.15625)
+    net = nvp.MLP(seed=6)
+    sx, sd = [0.6] * 6, [0.05] * 6
+    net.set_scales(sx, sd)
+    rng = np.random.default_rng(12)
+    Y0 = rng.uniform(-1, 1, (count, 6))
+    y0 = torch.tensor(Y0, dtype=torch.float64, device="cuda")
+    yT = torch.empty_like(y0)
+    st = nvp.steps("rk4", w.dt)
+    r = nvp.rhs("chain3", 6)
+    net.compose(r, w.t0, w.T, S, st, y0, yT)
+    p = unflatten(net.params())
+    p["W2"], p["W3"] = _bf16(p["W2"]), _bf16(p["W3"])
+    lam = Y0.copy()
+    for j in range(S):
+        lam = omlp.apply_map(p, lam, j / S, np.array(sx), np.array(sd))
+    assert rel_l2(yT.cpu().numpy(), lam) <= 1e-3
+    y1 = torch.empty_like(y0)
+    net.compose(r, w.t0, w.T, S, st, y0, y1, fallback=[1] * S)
+    y2 = y0.clone()
+    nvp.propagate(r, w.t0, w.T, S, st, 0, S, y2)
+    torch.cuda.synchronize()
+    assert np.array_equal(y1.cpu().numpy(), y2.cpu().numpy())
+    net.destroy()
