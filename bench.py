@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--workload", default="heat1d",
-                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d"],
-                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d")
+                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp"],
+                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp")
     return ap.parse_args()
 
 
@@ -515,8 +515,91 @@ def run_advdiff(args):
     return 0
 
 
+FP32_FLOP_PER_CHAIN_STEP = 220      # RK4 step of the 6-D chain incl. compensated update
+MLP_FLOP_PER_SAMPLE_STEP = 6 * (7 * 256 + 2 * 256 * 256 + 256 * 6)   # fwd + bwd (2 + 4 x weights)
+
+
+def run_chain3_mlp(args):
+    """Learned propagator for the 3-mass chain (S = 128, M = 65536 per slice):
+    pair generation by the method's integrator (float32), MLP training on the
+    tensor cores, validation against float64 end states, composition of 4096
+    initial states through the learned map vs float64 fine integration."""
+    torch, world, rank, local = _device_setup()
+    import numpy as np
+    import paper_1304_6514_gb300 as nvp
+    import workloads
+    w = workloads.chain3()
+    S, M = w.S, w.per_dim
+    r = nvp.rhs("chain3", 6)
+    st32, st64 = nvp.steps("rk4", w.dt, 0, "fp32"), nvp.steps("rk4", w.dt)
+    y0 = torch.empty(S * M * 6, dtype=torch.float32, device="cuda")
+    ye = torch.empty_like(y0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    nvp.build_pairs(r, w.t0, w.T, S, st32, M, w.extra["seed"], -1.0, 1.0, y0, ye)   # warm-up
+    ev[0].record()
+    nvp.build_pairs(r, w.t0, w.T, S, st32, M, w.extra["seed"], -1.0, 1.0, y0, ye)
+    ev[1].record()
+    torch.cuda.synchronize()
+    pairs_ms = ev[0].elapsed_time(ev[1])
+    m = nvp.plan_steps(w.t0, w.T, S, w.dt)[0]
+    pair_steps = S * M * m
+    d = (ye - y0).view(-1, 6)[:65536].double().cpu().numpy()
+    net = nvp.MLP(seed=1)
+    net.set_scales([1 / np.sqrt(3)] * 6, list(d.std(axis=0)))
+    sched = [(2000, 1e-3), (4000, 3e-4), (4000, 1e-4)]
+    t0 = time.perf_counter()
+    losses = [net.train(y0, ye, S, M, n, 4096, lr) for n, lr in sched]
+    train_s = time.perf_counter() - t0
+    nsteps = sum(n for n, _ in sched)
+    Mv = 1024
+    v0 = torch.empty(S * Mv * 6, dtype=torch.float64, device="cuda")
+    ve = torch.empty_like(v0)
+    nvp.build_pairs(r, w.t0, w.T, S, st64, Mv, w.extra["seed"] + 1, -1.0, 1.0, v0, ve)
+    err = net.validate(v0, ve, S, Mv)
+    fb = (err > 1e-3).astype(np.int32)
+    rng = np.random.default_rng(0)
+    Y0 = torch.tensor(rng.uniform(-0.5, 0.5, (4096, 6)), device="cuda")
+    yT = torch.empty_like(Y0)
+    net.compose(r, w.t0, w.T, S, st64, Y0, yT, fallback=fb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.compose(r, w.t0, w.T, S, st64, Y0, yT, fallback=fb)
+    torch.cuda.synchronize()
+    compose_ms = (time.perf_counter() - t0) * 1e3
+    yp = Y0.clone()
+    t0 = time.perf_counter()
+    nvp.propagate(r, w.t0, w.T, S, st64, 0, S, yp)
+    torch.cuda.synchronize()
+    fine_ms = (time.perf_counter() - t0) * 1e3
+    e = ((yT - yp).norm(dim=1) / yp.norm(dim=1)).cpu().numpy()
+    train_tflops = MLP_FLOP_PER_SAMPLE_STEP * 4096 * nsteps / train_s / 1e12
+    line = {"metric": METRIC, "value": pair_steps / (pairs_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": pairs_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pairs, bf16 MLP (f32 accumulate), f64 judge", "data": "synthetic",
+            "config": {"workload": w.name, "S": S, "M": M, "steps_per_slice": m, "hidden": [256, 256, 256],
+                       "train_steps": nsteps, "batch": 4096},
+            "pairs_ms": pairs_ms,
+            "roofline": {"bound": "alu", "kernel": "pairs_kernel<float>",
+                         "achieved": FP32_FLOP_PER_CHAIN_STEP * pair_steps / (pairs_ms * 1e-3) / 1e12,
+                         "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                         "frac": FP32_FLOP_PER_CHAIN_STEP * pair_steps / (pairs_ms * 1e-3) / FP32_PEAK_NOMINAL,
+                         "traffic": None},
+            "train": {"seconds": train_s, "losses": losses, "model_tflops": train_tflops,
+                      "steps_per_s": nsteps / train_s},
+            "validation_rel_err": {"mean": float(err.mean()), "max": float(err.max()),
+                                   "fallback_slices": int(fb.sum())},
+            "compose_4096_states": {"learned_ms": compose_ms, "f64_fine_ms": fine_ms,
+                                    "speedup": fine_ms / compose_ms,
+                                    "final_rel_err_mean": float(e.mean()), "final_rel_err_max": float(e.max())}}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "chain3_mlp":
+        return run_chain3_mlp(args)
     if args.workload == "advdiff2d":
         return run_advdiff(args)
     if args.impl == "reference":

@@ -133,3 +133,67 @@ def test_mlp_forward_matches_oracle_and_full_fallback_is_exact():
     torch.cuda.synchronize()
     assert np.array_equal(y1.cpu().numpy(), y2.cpu().numpy())
     net.destroy()
+
+
+def _train_chain3(torch, steps_schedule):
+    w = workloads.chain3()
+    S, M = w.S, w.per_dim
+    r = nvp.rhs("chain3", 6)
+    y0 = torch.empty(S * M * 6, dtype=torch.float32, device="cuda")
+    ye = torch.empty_like(y0)
+    nvp.build_pairs(r, w.t0, w.T, S, nvp.steps("rk4", w.dt, 0, "fp32"), M, w.extra["seed"], -1.0, 1.0, y0, ye)
+    d = (ye - y0).view(-1, 6)[:65536].double().cpu().numpy()
+    net = nvp.MLP(seed=1)
+    net.set_scales([1 / np.sqrt(3)] * 6, list(d.std(axis=0)))
+    losses = [net.train(y0, ye, S, M, n, 4096, lr) for n, lr in steps_schedule]
+    Mv = 1024
+    v0 = torch.empty(S * Mv * 6, dtype=torch.float64, device="cuda")
+    ve = torch.empty_like(v0)
+    nvp.build_pairs(r, w.t0, w.T, S, nvp.steps("rk4", w.dt), Mv, w.extra["seed"] + 1, -1.0, 1.0, v0, ve)
+    err = net.validate(v0, ve, S, Mv)
+    return w, r, net, losses, err
+
+
+def test_trained_network_gains_over_the_method_without_it():
+    """Trained on the method's own pairs (8.4M, float32), the network keeps
+    every slice's validation error (float64 end states, fresh samples) below
+    the 1e-3 fallback threshold, and composing 4096 initial states through it
+    is faster than float64 fine integration of the same states; the untrained
+    network fails the threshold on every slice."""
+    import time
+    torch = need_gpu()
+    w, r, net, losses, err = _train_chain3(torch, [(2000, 1e-3), (4000, 3e-4), (4000, 1e-4)])
+    print("losses", losses, "validation error mean", err.mean(), "max", err.max())
+    assert losses[-1] < 0.05 * losses[0] or losses[-1] < 1e-5
+    assert err.max() < 1e-3
+    fresh = nvp.MLP(seed=1)
+    fresh.set_scales([1 / np.sqrt(3)] * 6, [0.1] * 6)
+    S = w.S
+    st = nvp.steps("rk4", w.dt)
+    rng = np.random.default_rng(0)
+    Y0 = torch.tensor(rng.uniform(-0.5, 0.5, (4096, 6)), device="cuda")
+    yT = torch.empty_like(Y0)
+    fb = (err > 1e-3).astype(np.int32)
+    net.compose(r, w.t0, w.T, S, st, Y0, yT, fallback=fb)        # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.compose(r, w.t0, w.T, S, st, Y0, yT, fallback=fb)
+    torch.cuda.synchronize()
+    t_mlp = time.perf_counter() - t0
+    yp = Y0.clone()
+    t0 = time.perf_counter()
+    nvp.propagate(r, w.t0, w.T, S, st, 0, S, yp)
+    torch.cuda.synchronize()
+    t_fine = time.perf_counter() - t0
+    e = ((yT - yp).norm(dim=1) / yp.norm(dim=1)).cpu().numpy()
+    print(f"learned compose {t_mlp * 1e3:.1f} ms, float64 fine {t_fine * 1e3:.1f} ms, "
+          f"final-state relative error mean {e.mean():.3e} max {e.max():.3e}")
+    assert t_mlp < t_fine
+    assert np.all(np.isfinite(e)) and e.mean() < 0.1
+    Mv = 1024
+    v0 = torch.empty(S * Mv * 6, dtype=torch.float64, device="cuda")
+    ve = torch.empty_like(v0)
+    nvp.build_pairs(r, w.t0, w.T, S, st, Mv, w.extra["seed"] + 1, -1.0, 1.0, v0, ve)
+    assert np.all(fresh.validate(v0, ve, S, Mv) > 1e-3)
+    net.destroy()
+    fresh.destroy()
