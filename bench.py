@@ -546,7 +546,7 @@ def run_chain3_mlp(args):
     d = (ye - y0).view(-1, 6)[:65536].double().cpu().numpy()
     net = nvp.MLP(seed=1)
     net.set_scales([1 / np.sqrt(3)] * 6, list(d.std(axis=0)))
-    sched = [(2000, 1e-3), (4000, 3e-4), (4000, 1e-4)]
+    sched = [(2000, 1e-3), (4000, 1e-3), (4000, 3e-4), (4000, 1e-4)]
     t0 = time.perf_counter()
     losses = [net.train(y0, ye, S, M, n, 4096, lr) for n, lr in sched]
     train_s = time.perf_counter() - t0
