@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default="heat1d",
                     choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp"],
                     help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp")
+    ap.add_argument("--instances", type=int, default=0, help="vdp_batch: use the first N instances")
+    ap.add_argument("--train-steps", type=int, default=0, help="chain3_mlp: total Adam steps (profiling)")
     return ap.parse_args()
 
 
@@ -319,6 +321,9 @@ def run_vdp_batch(args):
     import paper_1304_6514_gb300 as nvp
     import workloads
     vb = workloads.vdp_batch()
+    if args.instances > 0:
+        k = args.instances
+        vb = workloads.VdpBatch(vb.mu[:k], vb.T[:k], vb.S[:k], vb.y0[:k])
     P = vb.per_dim
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -461,7 +466,7 @@ def run_advdiff(args):
     import numpy as np
     import paper_1304_6514_gb300 as nvp
     import workloads
-    w = workloads.advdiff2d()
+    w = workloads.advdiff2d(S=args.slices, T=args.slices / 512) if args.slices > 0 else workloads.advdiff2d()
     stream = torch.cuda.Stream()
     r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
     peaks, _ = read_peaks()
@@ -547,6 +552,8 @@ def run_chain3_mlp(args):
     net = nvp.MLP(seed=1)
     net.set_scales([1 / np.sqrt(3)] * 6, list(d.std(axis=0)))
     sched = [(2000, 1e-3), (4000, 1e-3), (4000, 3e-4), (4000, 1e-4)]
+    if args.train_steps > 0:
+        sched = [(args.train_steps, 1e-3)]
     t0 = time.perf_counter()
     losses = [net.train(y0, ye, S, M, n, 4096, lr) for n, lr in sched]
     train_s = time.perf_counter() - t0

@@ -178,7 +178,8 @@ static nv_status alloc_maps(nv_maps* P) {
   e = nv_cuda_check(cudaMalloc(&P->data, (size_t)P->bytes), "map allocation");
   if (e != NV_OK) { P->data = nullptr; return e; }
   const size_t xoff = 256;
-  const size_t coff = align256(xoff + sizeof(double) * 2 * (size_t)P->dim);
+  // 2 float64 chain vectors + a triple buffer of chain states (tiled chain) + slack
+  const size_t coff = align256(xoff + sizeof(double) * 5 * (size_t)P->dim + 64);
   P->ws_bytes = coff + sizeof(double) * (size_t)(P->coef_per_slice * P->S);
   e = nv_cuda_check(cudaMalloc(&P->ws, P->ws_bytes), "workspace allocation");
   if (e != NV_OK) { cudaFree(P->data); P->data = nullptr; P->ws = nullptr; return e; }

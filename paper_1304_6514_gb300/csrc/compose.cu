@@ -326,33 +326,42 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   }
 }
 
-// Grid-wide chain for large d (d > 512, d a multiple of 4): like
-// affine_chain_kernel, but every thread owns VEC = 16 / sizeof(MT) consecutive
-// rows and reads them with one 16-byte load per column, so each SM keeps
-// enough bytes in flight for the chain to stream the maps at HBM speed.
+// Grid-wide chain for large d (d > 512, d a multiple of 4).  CTA (rb, cb)
+// owns a tile of the slice map: rows [rb*RB, rb*RB + RB) of the column block
+// [cb*cpc, (cb+1)*cpc) of [b_j | A_j].  A column of the tile is RB contiguous
+// values (4 KB for float32), so the map streams in long runs; each thread reads
+// VEC = 16 / sizeof(MT) consecutive rows with one 16-byte load per column.
+// Partial row sums of the column blocks meet in global memory by atomic adds
+// into one of three rotating state buffers (step k adds into buffer k % 3,
+// reads buffer (k-1) % 3 and clears buffer (k+1) % 3 for the next step), and
+// one bounded grid barrier per step orders the steps.
 template <typename MT, typename AT>
-__global__ void __launch_bounds__(256) affine_chain_vec_kernel(AffineChainArgs a) {
+__global__ void __launch_bounds__(256) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
+                                                                AT* xb) {
   constexpr int VEC = 16 / (int)sizeof(MT);
   using V = typename std::conditional<sizeof(MT) == 4, float4, double2>::type;
-  extern __shared__ __align__(16) unsigned char sxv_raw[];
-  AT* sx = reinterpret_cast<AT*>(sxv_raw);   // n + 1
-  AT* red = sx + (a.n + 1);                  // ncg x rpc partial sums
+  extern __shared__ __align__(16) unsigned char sxt_raw[];
+  AT* sx = reinterpret_cast<AT*>(sxt_raw);   // the cpc state values of this column block
   __shared__ int flag;
-  const int n = a.n, rpc = a.rpc;
-  const int nq = rpc / VEC;                  // row groups per CTA
+  const int n = a.n;
+  const int RB = VEC * blockDim.x;
+  const int rb = blockIdx.x % nrb, cb = blockIdx.x / nrb;
   const int tid = threadIdx.x;
-  const int rq = tid % nq, cg = tid / nq, ncg = blockDim.x / nq;
-  const int row0 = blockIdx.x * rpc + rq * VEC;
-  const bool active = (cg < ncg) && (row0 < n);
+  const int row0 = rb * RB + tid * VEC;
+  const bool active = row0 < n;
+  const int c0 = cb * cpc, c1 = min(n + 1, c0 + cpc);
   const unsigned G = gridDim.x;
   const MT* maps = reinterpret_cast<const MT*>(a.maps);
   const int64_t slice_elems = (int64_t)n * (n + 1);
   if (blockIdx.x == 0 && a.lambdas)
     for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i];
   for (int k = 0; k < a.S; ++k) {
-    const double* xin = (k == 0) ? a.y0 : a.xbuf + ((k - 1) & 1) * n;
-    for (int i = tid; i < n; i += blockDim.x) sx[i + 1] = (AT)__ldcg(xin + i);
-    if (tid == 0) sx[0] = (AT)1;
+    AT* acc_buf = xb + (k % 3) * n;
+    const AT* in_buf = xb + ((k + 2) % 3) * n;
+    AT* clr_buf = xb + ((k + 1) % 3) * n;
+    for (int c = c0 + tid; c < c1; c += blockDim.x)
+      sx[c - c0] = c == 0 ? (AT)1 : (k == 0 ? (AT)a.y0[c - 1] : __ldcg(in_buf + c - 1));
+    for (int i = blockIdx.x * blockDim.x + tid; i < n; i += G * blockDim.x) clr_buf[i] = (AT)0;
     __syncthreads();
     AT acc[VEC];
 #pragma unroll
@@ -360,27 +369,31 @@ __global__ void __launch_bounds__(256) affine_chain_vec_kernel(AffineChainArgs a
     if (active) {
       const MT* A = maps + (int64_t)k * slice_elems + row0;
 #pragma unroll 16
-      for (int c = cg; c <= n; c += ncg) {
+      for (int c = c0; c < c1; ++c) {
         const V t = __ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n));
-        const AT xc = sx[c];
-        const MT* tv = reinterpret_cast<const MT*>(&t);
+        const AT xc = sx[c - c0];
+        if constexpr (VEC == 4) {
+          acc[0] = fma((AT)t.x, xc, acc[0]);
+          acc[1] = fma((AT)t.y, xc, acc[1]);
+          acc[2] = fma((AT)t.z, xc, acc[2]);
+          acc[3] = fma((AT)t.w, xc, acc[3]);
+        } else {
+          acc[0] = fma((AT)t.x, xc, acc[0]);
+          acc[1] = fma((AT)t.y, xc, acc[1]);
+        }
+      }
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] = fma((AT)tv[v], xc, acc[v]);
+      for (int v = 0; v < VEC; ++v) atomicAdd(acc_buf + row0 + v, acc[v]);
+    }
+    if (!grid_barrier(a.bar, (unsigned)(k + 1) * G, a.status, &flag)) return;
+    if (cb == 0 && active) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const double xv = (double)__ldcg(acc_buf + row0 + v);
+        if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row0 + v] = xv;
+        if (k == a.S - 1) a.yT[row0 + v] = xv;
       }
     }
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) red[cg * rpc + rq * VEC + v] = acc[v];
-    __syncthreads();
-    const int row = blockIdx.x * rpc + tid;
-    if (tid < rpc && row < n) {
-      double s = 0.0;
-      for (int g = 0; g < ncg; ++g) s += (double)red[g * rpc + tid];
-      a.xbuf[(k & 1) * n + row] = s;
-      if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row] = s;
-      if (k == a.S - 1) a.yT[row] = s;
-    }
-    if (k + 1 < a.S)
-      if (!grid_barrier(a.bar, (unsigned)(k + 1) * G, a.status, &flag)) return;
   }
 }
 
@@ -537,51 +550,56 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   return launch_chains(a, f64, s, want_csize);
 }
 
-// Grid-wide chain with 16-byte loads (d > 512, d % 4 == 0).
-static nv_status launch_affine_chain_vec(const nv_maps* M, const double* y0, double* yT, double* lambdas,
-                                         cudaStream_t s, int rows_per_cta) {
+// Tiled grid-wide chain (d > 512, d % 4 == 0): one CTA per SM, row blocks of
+// 1024 (float32) / 512 (float64) rows, column blocks sized to fill the grid.
+static nv_status launch_affine_chain_tile(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                                          cudaStream_t s) {
   const int n = M->dim;
   const int block = 256;
   const bool f64 = M->prec == NV_FP64;
   const int vec = f64 ? 2 : 4;
-  int rpc = rows_per_cta > 0 ? rows_per_cta : (f64 ? 8 : 16);
-  rpc = std::max(vec, std::min(rpc, 256) / vec * vec);
-  while ((block % (rpc / vec)) != 0) rpc -= vec;
-  const int G = (n + rpc - 1) / rpc;
-  const int ncg = block / (rpc / vec);
-  const size_t esz = f64 ? sizeof(double) : sizeof(float);
-  const size_t smem = esz * ((size_t)(n + 1) + (size_t)ncg * rpc);
-  const void* fn = f64 ? (const void*)affine_chain_vec_kernel<double, double>
-                       : (const void*)affine_chain_vec_kernel<float, float>;
-  nv_status st;
-  if (smem > 48 * 1024 &&
-      (st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                          "chain smem attribute")) != NV_OK)
-    return st;
-  int dev = 0, sms = 0, per_sm = 0;
+  const int RB = vec * block;
+  const int nrb = (n + RB - 1) / RB;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ncb = std::max(1, sms / nrb);
+  const int cpc = (n + 1 + ncb - 1) / ncb;
+  const int G = nrb * ncb;
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  const size_t smem = esz * (size_t)cpc;
+  const void* fn = f64 ? (const void*)affine_chain_tile_kernel<double, double>
+                       : (const void*)affine_chain_tile_kernel<float, float>;
+  nv_status st;
+  int per_sm = 0;
   if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem),
                           "chain occupancy")) != NV_OK)
     return st;
   if ((int64_t)per_sm * sms < G)
     return nv_fail(NV_ENOTSUP, "chain needs %d resident CTAs, device holds %d", G, per_sm * sms);
-  if ((st = nv_cuda_check(cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s), "barrier reset")) != NV_OK)
+  // state triple buffer in the maps workspace tail: 3 * n values
+  if (M->ws_bytes < 256 + sizeof(double) * 2 * (size_t)n + esz * 3 * (size_t)n)
+    return nv_fail(NV_ENOTSUP, "workspace too small for the tiled chain");
+  void* xb = reinterpret_cast<char*>(M->xbuf) + sizeof(double) * 2 * (size_t)n;
+  xb = reinterpret_cast<void*>(((uintptr_t)xb + 15) & ~(uintptr_t)15);
+  if ((st = nv_cuda_check(cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s), "barrier reset")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemsetAsync(xb, 0, esz * (size_t)n, s), "chain state reset")) != NV_OK)
     return st;
   AffineChainArgs a{};
   a.maps = M->data;
   a.n = n;
   a.S = M->S;
-  a.rpc = rpc;
+  a.rpc = 0;
   a.y0 = y0;
   a.yT = yT;
   a.lambdas = lambdas;
   a.xbuf = M->xbuf;
   a.bar = M->bar;
   a.status = M->status;
-  void* args[] = {&a};
+  int nrb_arg = nrb, cpc_arg = cpc;
+  void* args[] = {&a, &nrb_arg, &cpc_arg, &xb};
   return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
-                       "affine_chain_vec_kernel cooperative launch");
+                       "affine_chain_tile_kernel cooperative launch");
 }
 
 nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
@@ -591,7 +609,7 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
     nv_status st = launch_affine_chain_cluster(M, y0, yT, lambdas, s, g_tune.chain_cluster);
     if (st != NV_ENOTSUP) return st;
   }
-  if (n > 512 && n % 4 == 0) return launch_affine_chain_vec(M, y0, yT, lambdas, s, rows_per_cta);
+  if (n > 512 && n % 4 == 0) return launch_affine_chain_tile(M, y0, yT, lambdas, s);
   const int block = 256;
   int rpc = rows_per_cta > 0 ? rows_per_cta : 16;
   rpc = std::min(rpc, block);
