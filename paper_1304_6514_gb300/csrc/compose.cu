@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
 // reads buffer (k-1) % 3 and clears buffer (k+1) % 3 for the next step), and
 // one bounded grid barrier per step orders the steps.
 template <typename MT, typename AT>
-__global__ void __launch_bounds__(256) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
+__global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
                                                                 AT* xb) {
   constexpr int VEC = 16 / (int)sizeof(MT);
   using V = typename std::conditional<sizeof(MT) == 4, float4, double2>::type;
@@ -368,10 +368,7 @@ __global__ void __launch_bounds__(256) affine_chain_tile_kernel(AffineChainArgs 
     for (int v = 0; v < VEC; ++v) acc[v] = 0;
     if (active) {
       const MT* A = maps + (int64_t)k * slice_elems + row0;
-#pragma unroll 16
-      for (int c = c0; c < c1; ++c) {
-        const V t = __ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n));
-        const AT xc = sx[c - c0];
+      auto madd = [&](const V& t, AT xc) {
         if constexpr (VEC == 4) {
           acc[0] = fma((AT)t.x, xc, acc[0]);
           acc[1] = fma((AT)t.y, xc, acc[1]);
@@ -381,7 +378,18 @@ __global__ void __launch_bounds__(256) affine_chain_tile_kernel(AffineChainArgs 
           acc[0] = fma((AT)t.x, xc, acc[0]);
           acc[1] = fma((AT)t.y, xc, acc[1]);
         }
+      };
+      // batches of kBatch independent 16-byte loads in flight per thread
+      constexpr int kBatch = 16;
+      int c = c0;
+      for (; c + kBatch <= c1; c += kBatch) {
+        V t[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) t[q] = __ldg(reinterpret_cast<const V*>(A + (int64_t)(c + q) * n));
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) madd(t[q], sx[c + q - c0]);
       }
+      for (; c < c1; ++c) madd(__ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n)), sx[c - c0]);
 #pragma unroll
       for (int v = 0; v < VEC; ++v) atomicAdd(acc_buf + row0 + v, acc[v]);
     }
@@ -551,11 +559,11 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
 }
 
 // Tiled grid-wide chain (d > 512, d % 4 == 0): one CTA per SM, row blocks of
-// 1024 (float32) / 512 (float64) rows, column blocks sized to fill the grid.
+// 2048 (float32) / 1024 (float64) rows, column blocks sized to fill the grid.
 static nv_status launch_affine_chain_tile(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                                           cudaStream_t s) {
   const int n = M->dim;
-  const int block = 256;
+  const int block = 512;
   const bool f64 = M->prec == NV_FP64;
   const int vec = f64 ? 2 : 4;
   const int RB = vec * block;
