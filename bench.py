@@ -289,6 +289,24 @@ def gpu_peak_probe(torch):
     return out
 
 
+# DRAM bytes (read + write) per unit of output from one ncu capture of each
+# dominant kernel, scaled to the bench's launch by the units it writes (the
+# captures ran smaller cases of the same kernels; see profiles/):
+#   heat FP64 build, S = 512 capture: 207.34 MB for 131 072 homogeneous columns
+#   advection-diffusion FP32 build, S = 8 capture: 476.02 MB for 32 776 columns
+#   Van der Pol batch build, 512 instances: 502.0 MB for 561 987 584 table bytes
+NCU_TRAFFIC_PER_UNIT = {
+    "heat_horner_kernel<double,8,0>": (207.34e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
+    "advdiff_block_kernel": (476.02e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
+    "batch_build_kernel<RhsVdp<float>,float,4,1>": (502.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
+}
+
+
+def ncu_traffic(kernel, units):
+    per, src = NCU_TRAFFIC_PER_UNIT[kernel]
+    return per * units, src
+
+
 FP32_FLOP_PER_VDP_STEP = 52   # RK4 step of the 2-D Van der Pol system incl. compensated update
 
 
@@ -373,9 +391,13 @@ def run_vdp_batch(args):
                        "cta_threads_autotuned": best, "l2": "flushed before every timed step"},
             "build_ms": statistics.mean(build), "compose_ms": statistics.mean(comp),
             "graph_run_ms": graph_ms, "out_of_range_evaluations": oob,
-            "roofline": {"bound": "alu", "kernel": "batch_build_kernel<RhsVdp<float>>",
+            "roofline": {"bound": "alu", "kernel": "batch_build_kernel<RhsVdp<float>,float,4,1>",
                          "achieved": achieved / 1e12, "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_NOMINAL, "traffic": None,
+                         "frac": achieved / FP32_PEAK_NOMINAL,
+                         "traffic": ncu_traffic("batch_build_kernel<RhsVdp<float>,float,4,1>",
+                                                info["table_bytes"])[0],
+                         "traffic_source": ncu_traffic("batch_build_kernel<RhsVdp<float>,float,4,1>", 1)[1],
+                         "algorithmic_bytes": info["table_bytes"],
                          "peak_source": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"},
             "gpu_launches": 2 * K, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
@@ -472,6 +494,8 @@ def run_advdiff(args):
     peaks, _ = read_peaks()
     out = {}
     K = max(1, args.steps)
+    W = max(3, args.warmup)
+    clocks = None
     for prec in ("fp32", "fp64"):
         st = nvp.steps("rk4", w.dt, 0, prec)
         y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
@@ -479,8 +503,17 @@ def run_advdiff(args):
         with torch.cuda.stream(stream):
             maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, stream=stream)
             nvp.compose(maps, y0, yT, stream=stream)
+            # float32: W warm-up steps in all, then K timed; float64 (a reported
+            # variant, 3.4 s per build): one warm-up, one timed
+            for _ in range(W - 1 if prec == "fp32" else 0):
+                nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, maps=maps, stream=stream)
+                nvp.compose(maps, y0, yT, stream=stream)
             reps = K if prec == "fp32" else 1
             ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+            sampler = ClockSampler(local) if prec == "fp32" else None
+            if sampler:
+                stream.synchronize()
+                sampler.start()
             for k in range(reps):
                 ev[k][0].record(stream)
                 nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, maps=maps, stream=stream)
@@ -488,6 +521,8 @@ def run_advdiff(args):
                 nvp.compose(maps, y0, yT, stream=stream)
                 ev[k][2].record(stream)
             stream.synchronize()
+            if sampler:
+                clocks = sampler.stop()
             nvp.maps_check(maps, stream=stream)
         d = nvp.maps_info(maps)
         b = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
@@ -507,14 +542,23 @@ def run_advdiff(args):
     for v in out.values():
         v.pop("yT")
     line = {"metric": METRIC, "value": units / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
-            "steps": K, "warmup": 1, "ms_per_step": step_ms, "higher_is_better": True,
+            "steps": K, "warmup": W, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 maps, f32 chain", "data": "synthetic",
             "config": {"workload": w.name, "n": w.dim, "S": w.S, "l2": "maps (34 GB) larger than L2"},
             "variants": out, "fp32_rel_err_vs_fp64_gpu": rel,
             "time_to_solution_ms": {"fp32": step_ms, "fp64": f64["build_ms"] + f64["compose_ms"]},
-            "roofline": {"bound": "hbm", "kernel": "affine_chain_kernel<float,float>",
-                         "achieved": f32["chain_hbm_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": f32["chain_frac_of_hbm"], "traffic": None}}
+            "roofline": {"bound": "alu", "kernel": "advdiff_block_kernel",
+                         "achieved": f32["build_tflops"], "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                         "frac": f32["build_tflops"] * 1e12 / FP32_PEAK_NOMINAL,
+                         "traffic": ncu_traffic("advdiff_block_kernel", w.S * (w.dim + 1))[0],
+                         "traffic_source": ncu_traffic("advdiff_block_kernel", 1)[1],
+                         "algorithmic_bytes": f32["map_bytes"],
+                         "peak_source": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                         "flop_per_launch": FLOP_PER_ADV_COMPONENT_STEP * w.S * (w.dim + 1) * 10 * w.dim},
+            "chain_roofline": {"bound": "hbm", "kernel": "affine_chain_tile_kernel<float,float>",
+                               "achieved": f32["chain_hbm_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                               "frac": f32["chain_frac_of_hbm"], "traffic": None},
+            "gpu_launches": 2 * K, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
     return 0
@@ -700,9 +744,13 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_solution_ms": statistics.mean(res["step_ms"]),
         "wall_s_timed_region": wall,
-        "roofline": {"bound": "alu", "kernel": "heat_affine_build_kernel<double,8>",
+        "roofline": {"bound": "alu", "kernel": "heat_horner_kernel<double,8,0>",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL,
+                     "traffic": ncu_traffic("heat_horner_kernel<double,8,0>", w.S * w.dim)[0],
+                     "traffic_source": ncu_traffic("heat_horner_kernel<double,8,0>", 1)[1],
+                     "algorithmic_bytes": w.S * w.dim * w.dim * 8,
+                     "timed": "the build call (forcing-column kernel + this kernel, 99 % of it), CUDA events",
                      "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)",
                      "flop_per_launch": flop},
         "gpu_launches": 3 * K,

@@ -183,10 +183,41 @@ __device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double h, cons
   }
 }
 
+// Store a lane-blocked column (lane l holds rows l*R .. l*R+R-1) so that each
+// warp store covers 32 consecutive rows: the warp stages the column in its own
+// shared-memory slot (lane stride R+1 to spread the banks) and reads row
+// k*32+l back in lane l. Every store instruction then writes whole 32-byte
+// sectors, where the blocked order left each sector partly written and the L2
+// had to fill it from DRAM. buf holds 32*(R+1) values for this warp.
+template <int R, bool TF32OUT, typename T>
+__device__ __forceinline__ void store_column(const T* y, T* buf, T* col, int lane, int n) {
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < R; ++i) buf[lane * (R + 1) + i] = y[i];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int r = k * 32 + lane;
+    const int src = r / R;
+    const T v = buf[src * (R + 1) + (r - src * R)];
+    if (r < n) {
+      if constexpr (TF32OUT) col[r] = round_tf32(v);
+      else col[r] = v;
+    }
+  }
+}
+
+// Per-warp staging slots of store_column for a CTA of at most 256 threads.
+template <int R, typename T>
+__device__ __forceinline__ T* column_stage() {
+  __shared__ T stage[8 * 32 * (R + 1)];
+  return stage + (threadIdx.x >> 5) * 32 * (R + 1);
+}
+
 // Homogeneous columns of a time-invariant operator (c = 1..d): Horner-form
 // RK4 only, so a thread holds just y and v (2R values) and many warps fit.
 template <typename T, int R, bool TF32OUT>
-__global__ void __launch_bounds__(256) heat_horner_kernel(HeatArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 1) heat_horner_kernel(HeatArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -203,16 +234,7 @@ __global__ void __launch_bounds__(256) heat_horner_kernel(HeatArgs a) {
 #pragma unroll
     for (int i = 0; i < R; ++i) y[i] = (lane * R + i == c - 1) ? (T)1 : (T)0;
     for (int64_t i = 0; i < a.m; ++i) heat_horner_step<R>(y, v, cdx, h, lane, n);
-    T* col = out + ((int64_t)j * cols + c) * n;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const int r = lane * R + i;
-      if constexpr (TF32OUT) {
-        if (r < n) col[r] = round_tf32(y[i]);
-      } else {
-        if (r < n) col[r] = y[i];
-      }
-    }
+    store_column<R, TF32OUT>(y, column_stage<R, T>(), out + ((int64_t)j * cols + c) * n, lane, n);
   }
 }
 
@@ -254,12 +276,7 @@ __global__ void __launch_bounds__(256) heat_literal_kernel(HeatArgs a, int all_c
       if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
       heat_rk4_step<R>(y, z, acc, a.h, step_coefs<T>(hc, i, i0, cdx), sx, forced, lane, n);
     }
-    T* col = out + ((int64_t)j * cols + c) * n;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const int r = lane * R + i;
-      if (r < n) col[r] = y[i];
-    }
+    store_column<R, false>(y, column_stage<R, T>(), out + ((int64_t)j * cols + c) * n, lane, n);
   }
 }
 
@@ -425,6 +442,108 @@ __global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
 #pragma unroll
     for (int r = 0; r < kAdvRows; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
     __syncthreads();   // shared halos are reused by the next column
+  }
+}
+
+// Float32 build with 8 x 8 blocks: one CTA of 64 threads integrates one basis
+// column, thread (tx, ty) = (t % 8, t / 8) holding the grid block
+// ix = 8 tx .. 8 tx + 7, iy = 8 ty .. 8 ty + 7 in registers. A stage exchanges
+// only the block's four edges (32 values for 64 points, against two shuffles
+// per point in the strip layout): each thread writes its edges to
+// double-buffered shared memory as 128-bit stores, one __syncthreads, and
+// reads its four neighbours' facing edges (periodic in both directions).
+// The arithmetic per point and its order are those of advdiff_affine_kernel.
+constexpr int kAdvB = 8;                       // block edge
+constexpr int kAdvBlockThreads = (kAdvNx / kAdvB) * (kAdvNx / kAdvB);   // 64
+
+__global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvArgs a) {
+  constexpr int n = kAdvNx * kAdvNx;
+  constexpr int TB = kAdvNx / kAdvB;           // 8 blocks per direction
+  // edges[buffer][side][half][thread]: side 0 left column, 1 right column,
+  // 2 top row, 3 bottom row; half h holds edge points 4h .. 4h+3
+  __shared__ float4 edges[2][4][2][kAdvBlockThreads];
+  const int t = threadIdx.x, tx = t % TB, ty = t / TB;
+  const int ix0 = kAdvB * tx, iy0 = kAdvB * ty;
+  const int t_left = ty * TB + (tx + TB - 1) % TB, t_right = ty * TB + (tx + 1) % TB;
+  const int t_up = ((ty + TB - 1) % TB) * TB + tx, t_down = ((ty + 1) % TB) * TB + tx;
+  float* out = reinterpret_cast<float*>(a.out);
+  const int64_t total = (int64_t)a.S * (n + 1);
+  int buf = 0;
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int j = (int)(w / (n + 1));
+    const int c = (int)(w - (int64_t)j * (n + 1));     // 0: solve from 0 (no forcing), else e_{c-1}
+    float y[kAdvB][kAdvB], v[kAdvB][kAdvB];
+#pragma unroll
+    for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+      for (int q = 0; q < kAdvB; ++q) y[r][q] = ((iy0 + r) * kAdvNx + ix0 + q == c - 1) ? 1.f : 0.f;
+    for (int64_t i = 0; i < a.m; ++i) {
+#pragma unroll
+      for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+        for (int q = 0; q < kAdvB; ++q) v[r][q] = y[r][q];
+#pragma unroll 1
+      for (int kk = 4; kk >= 1; --kk) {
+        const float* cw = a.cw32[4 - kk];
+        const float cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
+        float4(*e)[2][kAdvBlockThreads] = edges[buf];
+        e[0][0][t] = make_float4(v[0][0], v[1][0], v[2][0], v[3][0]);
+        e[0][1][t] = make_float4(v[4][0], v[5][0], v[6][0], v[7][0]);
+        e[1][0][t] = make_float4(v[0][7], v[1][7], v[2][7], v[3][7]);
+        e[1][1][t] = make_float4(v[4][7], v[5][7], v[6][7], v[7][7]);
+        e[2][0][t] = make_float4(v[0][0], v[0][1], v[0][2], v[0][3]);
+        e[2][1][t] = make_float4(v[0][4], v[0][5], v[0][6], v[0][7]);
+        e[3][0][t] = make_float4(v[7][0], v[7][1], v[7][2], v[7][3]);
+        e[3][1][t] = make_float4(v[7][4], v[7][5], v[7][6], v[7][7]);
+        __syncthreads();
+        // x - 1 of column 0: the left block's right column; x + 1 of column 7:
+        // the right block's left column; y - 1 of row 0: the upper block's
+        // bottom row; y + 1 of row 7: the lower block's top row
+        const float4 l0 = e[1][0][t_left], l1 = e[1][1][t_left];
+        const float4 r0 = e[0][0][t_right], r1 = e[0][1][t_right];
+        const float4 u0 = e[3][0][t_up], u1 = e[3][1][t_up];
+        const float4 d0 = e[2][0][t_down], d1 = e[2][1][t_down];
+        const float hl[kAdvB] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        const float hr[kAdvB] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const float hu[kAdvB] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const float hd[kAdvB] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+        float prev[kAdvB];                     // row r - 1 before this stage
+#pragma unroll
+        for (int q = 0; q < kAdvB; ++q) prev[q] = hu[q];
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r) {
+          float nrow[kAdvB];
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) {
+            const float xm = q == 0 ? hl[r] : v[r][q - 1];
+            const float xp = q == kAdvB - 1 ? hr[r] : v[r][q + 1];
+            const float yp = r == kAdvB - 1 ? hd[q] : v[r + 1][q];
+            float acc = fmaf(c0, v[r][q], y[r][q]);
+            acc = fmaf(cxm, xm, acc);
+            acc = fmaf(cxp, xp, acc);
+            acc = fmaf(cym, prev[q], acc);
+            nrow[q] = fmaf(cyp, yp, acc);
+          }
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) {
+            prev[q] = v[r][q];
+            v[r][q] = nrow[q];
+          }
+        }
+        buf ^= 1;
+      }
+#pragma unroll
+      for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+        for (int q = 0; q < kAdvB; ++q) y[r][q] = v[r][q];
+    }
+    float* col = out + ((int64_t)j * (n + 1) + c) * n;
+#pragma unroll
+    for (int r = 0; r < kAdvB; ++r) {
+      float4* dst = reinterpret_cast<float4*>(col + (iy0 + r) * kAdvNx + ix0);
+      dst[0] = make_float4(y[r][0], y[r][1], y[r][2], y[r][3]);
+      dst[1] = make_float4(y[r][4], y[r][5], y[r][6], y[r][7]);
+    }
   }
 }
 
@@ -657,9 +776,11 @@ nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
     if (st != NV_OK) return st;
     advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
   } else {
-    st = persistent_grid(advdiff_affine_kernel<float>, 256, cols * 8, &grid);
+    // columns start at j * (n + 1) * n floats: 16-byte aligned for the
+    // float4 stores since n = 4096 and the map buffer is 256-byte aligned
+    st = persistent_grid(advdiff_block_kernel, kAdvBlockThreads, cols * 2, &grid);
     if (st != NV_OK) return st;
-    advdiff_affine_kernel<float><<<grid, 256, 0, s>>>(a);
+    advdiff_block_kernel<<<grid, kAdvBlockThreads, 0, s>>>(a);
   }
   return nv_cuda_check(cudaGetLastError(), "advdiff_affine_kernel launch");
 }
