@@ -13,6 +13,8 @@ Modules
   chebyshev    backward Euler + Lagrange interpolation on Chebyshev-Lobatto
                nodes, the configuration of the paper's Table 1
   mlp          FP64 forward/backward of the slice-conditioned MLP propagator
+  wave         Chebyshev spectral wave equation with leapfrog steps on the
+               doubled state (Section 5), its affine maps and serial solve
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a paper value or brute force, except where its docstring says

@@ -164,6 +164,22 @@ def chain3_samples(seed: int, S: int, M: int, slice_index: int) -> np.ndarray:
     return (-1.0 + 2.0 * u).reshape(M, 6).T.copy()
 
 
+def wave1d(M: int = 80, S: int = 512, T: float = 20.0) -> Workload:
+    """u_tt = u_xx on [-1, 1], Dirichlet, Chebyshev points x_i = cos(i pi/M),
+    leapfrog dt = 8/M^2 (Section 5, Table wave80 for M = 80, T = 20; Table
+    wave40 for M = 40, T = 16).  State (u^n, u^{n-1}) of dimension 2(M-1); the
+    initial state depends on the planned step h: see wave1d_initial."""
+    return Workload(f"wave_cheb{M}_S{S}_leapfrog", "wave", 2 * (M - 1), 0.0, T, S, "leapfrog",
+                    8.0 / (M * M), 0, "affine", params=(float(M),))
+
+
+def wave1d_initial(M: int, h: float, width: float = 200.0) -> np.ndarray:
+    """(u(x, 0), u(x, -h)) at the interior Chebyshev points for the single
+    left-moving peak u(x, t) = exp(-width (x + t)^2)."""
+    x = np.cos(np.pi * np.arange(1, M) / M)
+    return np.concatenate([np.exp(-width * x ** 2), np.exp(-width * (x - h) ** 2)])
+
+
 def square_paper(dt_exp: int = 14, S: int = 32, M: int = 4) -> Workload:
     """y' = y^2 on [0, 1/2], the scalar model problem of Section 3 (Table 3 sweep shape)."""
     return Workload(f"square_dt2^-{dt_exp}_N{S}_M{M}", "square", 1, 0.0, 0.5, S, "euler",
