@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--workload", default="heat1d",
-                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp"],
-                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp")
+                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp", "wave"],
+                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp | wave")
     ap.add_argument("--instances", type=int, default=0, help="vdp_batch: use the first N instances")
     ap.add_argument("--train-steps", type=int, default=0, help="chain3_mlp: total Adam steps (profiling)")
     return ap.parse_args()
@@ -564,6 +564,100 @@ def run_advdiff(args):
     return 0
 
 
+def wave_flop_per_column_step(d):
+    """Leapfrog on one basis column: the dense d x d product (d^2 FMA) and the
+    update 2u - u_old + h^2 w (2 FMA per point), FMA = 2."""
+    return 2 * d * (d + 2)
+
+
+def run_wave(args):
+    """Chebyshev spectral wave equation, M = 80 (d = 79, state 158), S = 512,
+    T = 20, leapfrog dt = 8/M^2 (m = 32): float64 and float32 maps of the
+    doubled state and their composition."""
+    torch, world, rank, local = _device_setup()
+    import numpy as np
+    import paper_1304_6514_gb300 as nvp
+    import workloads
+    w = workloads.wave1d(S=args.slices, T=20.0 * args.slices / 512) if args.slices > 0 else workloads.wave1d()
+    M = int(w.params[0])
+    d = M - 1
+    stream = torch.cuda.Stream()
+    r = nvp.rhs("wave", w.dim, w.params)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    K, W = max(1, args.steps), max(3, args.warmup)
+    out, clocks, m, h = {}, None, 0, 0.0
+    for prec in ("fp64", "fp32"):
+        st = nvp.steps("leapfrog", w.dt, 0, prec)
+        with torch.cuda.stream(stream):
+            maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, stream=stream)
+            info = nvp.maps_info(maps)
+            m, h = info.steps_per_slice, info.h
+            y0 = torch.tensor(workloads.wave1d_initial(M, h), device="cuda")
+            yT = torch.empty_like(y0)
+            for _ in range(W):
+                nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, maps=maps, stream=stream)
+                nvp.compose(maps, y0, yT, stream=stream)
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+            sampler = ClockSampler(local) if prec == "fp64" else None
+            stream.synchronize()
+            if sampler:
+                sampler.start()
+            for k in range(K):
+                flush.fill_(k & 0xFF)                       # maps fit in L2: flush before every step
+                ev[k][0].record(stream)
+                nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st, maps=maps, stream=stream)
+                ev[k][1].record(stream)
+                nvp.compose(maps, y0, yT, stream=stream)
+                ev[k][2].record(stream)
+            stream.synchronize()
+            if sampler:
+                clocks = sampler.stop()
+            nvp.maps_check(maps, stream=stream)
+        b = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+        c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+        units = w.S * (w.dim + 1) * m
+        out[prec] = {"build_ms": b, "compose_ms": c, "map_bytes": info.bytes,
+                     "build_tflops": wave_flop_per_column_step(d) * units / (b * 1e-3) / 1e12,
+                     "yT": yT.cpu().numpy()}
+        maps.destroy()
+    f64, f32 = out["fp64"], out["fp32"]
+    units = w.S * (w.dim + 1) * m
+    step_ms = f64["build_ms"] + f64["compose_ms"]
+    value, dev_s, _ = aggregate_over_ranks(units * K, step_ms * 1e-3 * K)
+    f32["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(f32["yT"] - f64["yT"]) / np.linalg.norm(f64["yT"]))
+    yT64 = f64["yT"]
+    for v in out.values():
+        v.pop("yT")
+    flop = wave_flop_per_column_step(d) * units
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "M": M, "n": w.dim, "S": w.S, "steps_per_slice": m,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "variants": out, "time_to_solution_ms": {"fp64": step_ms, "fp32": f32["build_ms"] + f32["compose_ms"]},
+            "roofline": {"bound": "alu", "kernel": "wave_build_kernel<double,80,2>",
+                         "achieved": f64["build_tflops"], "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                         "frac": f64["build_tflops"] * 1e12 / FP64_PEAK_NOMINAL, "traffic": None,
+                         "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)", "flop_per_launch": flop},
+            "gpu_launches": 3 * K, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import wave as owave
+        ns = min(w.S, 64)
+        t0 = time.perf_counter()
+        owave.build_affine(M, ns, m, h)
+        el = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ys = owave.serial_fine(M, w.S, m, h, workloads.wave1d_initial(M, h))
+        serial_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns * (w.dim + 1) * m / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 numpy oracle maps of {ns} of {w.S} slices ({el:.1f} s); "
+                                          f"serial leapfrog solve {serial_s:.2f} s"}
+        line["rel_err_vs_oracle_serial"] = float(np.linalg.norm(yT64 - ys) / np.linalg.norm(ys))
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 FP32_FLOP_PER_CHAIN_STEP = 220      # RK4 step of the 6-D chain incl. compensated update
 MLP_FLOP_PER_SAMPLE_STEP = 6 * (7 * 256 + 2 * 256 * 256 + 256 * 6)   # fwd + bwd (2 + 4 x weights)
 
@@ -653,6 +747,8 @@ def main():
         return run_chain3_mlp(args)
     if args.workload == "advdiff2d":
         return run_advdiff(args)
+    if args.workload == "wave":
+        return run_wave(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "vdp_batch":

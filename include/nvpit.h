@@ -63,8 +63,13 @@ typedef enum {
                                  state (x1,x2,x3,v1,v2,v3);         dim 6, params {k, k3, c}      */
   NV_RHS_ADVDIFF2D = 6,       /* u_t = nu lap5(u) - (ax D-x u + ay D-y u), periodic nx*nx grid,
                                  spacing 1/nx, index iy*nx+ix;      dim nx*nx, params {nu, ax, ay} */
-  NV_RHS_HEAT1D_VARCOEF = 7   /* Section 5, eq. heatequation: u_t = (1 + sin(t)/4) u_xx + b(t,x),
+  NV_RHS_HEAT1D_VARCOEF = 7,  /* Section 5, eq. heatequation: u_t = (1 + sin(t)/4) u_xx + b(t,x),
                                  b making cos(t) sin(pi x) exact;   dim n                         */
+  NV_RHS_WAVE_CHEB = 8        /* Section 5, eq. waveequation: u_tt = u_xx on [-1,1], u(+-1) = 0,
+                                 Chebyshev spectral D2 on x_i = cos(i pi/M), interior d = M-1
+                                 points; state (u^n, u^{n-1}) (the doubled initial-value space
+                                 of Section 5);                    dim 2(M-1) <= 160, params {M}
+                                 (optional: M = dim/2 + 1); scheme NV_LEAPFROG only            */
 } nv_rhs_kind;
 
 typedef struct {
@@ -74,7 +79,11 @@ typedef struct {
   int32_t nparams;
 } nv_rhs;
 
-typedef enum { NV_EULER = 0, NV_RK4 = 1 } nv_scheme;
+/* NV_LEAPFROG: u^{n+1} = 2u^n - u^{n-1} + h^2 D2 u^n on the two-level state of
+   NV_RHS_WAVE_CHEB (Section 5: "explicit second-order leapfrog"); one step
+   advances (u^n, u^{n-1}) to (u^{n+1}, u^n).  The state at a slice boundary
+   T_j is (u(T_j), u(T_j - h)) with the planned h = H/m.                      */
+typedef enum { NV_EULER = 0, NV_RK4 = 1, NV_LEAPFROG = 2 } nv_scheme;
 
 typedef enum {
   NV_MAP_PL1D = 0,         /* d = 1: piecewise-linear table on M equispaced nodes      */

@@ -23,8 +23,8 @@ HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "nvpit.h")
 # enums (include/nvpit.h)
 NV_OK, NV_EINVAL, NV_ENOMEM, NV_ECUDA, NV_EDOMAIN, NV_EBADMAP, NV_ETIMEOUT, NV_ENOTSUP = range(8)
 RHS = {"linear_scalar": 0, "square": 1, "cos_cubic": 2, "heat1d": 3, "vdp": 4, "chain3": 5,
-       "advdiff2d": 6, "heat1d_varcoef": 7}
-SCHEME = {"euler": 0, "rk4": 1}
+       "advdiff2d": 6, "heat1d_varcoef": 7, "wave": 8}
+SCHEME = {"euler": 0, "rk4": 1, "leapfrog": 2}
 MAP = {"pl1d": 0, "bilinear2d": 1, "affine": 2}
 PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2}
 OOB = {"extrapolate": 0, "error": 1}

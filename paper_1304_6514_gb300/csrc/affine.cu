@@ -690,6 +690,7 @@ static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s, boo
 }
 
 nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s);
+nv_status launch_wave_build(const nv_maps* M, cudaStream_t s);
 
 nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
   if (M->rhs_kind == NV_RHS_HEAT1D || M->rhs_kind == NV_RHS_HEAT1D_VARCOEF) {
@@ -701,6 +702,7 @@ nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
     return launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE);
   }
   if (M->rhs_kind == NV_RHS_ADVDIFF2D) return launch_advdiff_build(M, s);
+  if (M->rhs_kind == NV_RHS_WAVE_CHEB) return launch_wave_build(M, s);
   return nv_fail(NV_ENOTSUP, "affine maps are not built for rhs kind %d", M->rhs_kind);
 }
 

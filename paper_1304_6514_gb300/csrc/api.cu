@@ -15,6 +15,8 @@ nv_status launch_serial_table(int32_t rhs_kind, const double* params, double t0,
                               double* yT, cudaStream_t s);
 nv_status launch_serial_heat(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
+nv_status launch_serial_wave(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
+int64_t wave_aux_elems(int d);
 
 nv_tunables g_tune = {0, 0, 0, 0, 0, 0};
 
@@ -104,6 +106,12 @@ static nv_status check_rhs(const nv_rhs* rhs, double* params, int32_t* nparams) 
       else if (rhs->nparams < 3) return nv_fail(NV_EINVAL, "advection-diffusion needs {nu, ax, ay}");
       break;
     }
+    case NV_RHS_WAVE_CHEB: {
+      if (d < 2 || d > 160 || d % 2) return nv_fail(NV_EINVAL, "wave rhs dim must be 2(M-1) with 2 <= M <= 81");
+      if (rhs->nparams == 0) { params[0] = d / 2 + 1; *nparams = 1; }
+      if (params[0] != (double)(d / 2 + 1)) return nv_fail(NV_EINVAL, "wave rhs: dim must be 2(M-1)");
+      break;
+    }
     default:
       return nv_fail(NV_EINVAL, "unknown rhs kind %d", rhs->kind);
   }
@@ -111,7 +119,15 @@ static nv_status check_rhs(const nv_rhs* rhs, double* params, int32_t* nparams) 
 }
 
 static bool is_linear_kind(int k) {
-  return k == NV_RHS_HEAT1D || k == NV_RHS_HEAT1D_VARCOEF || k == NV_RHS_ADVDIFF2D;
+  return k == NV_RHS_HEAT1D || k == NV_RHS_HEAT1D_VARCOEF || k == NV_RHS_ADVDIFF2D || k == NV_RHS_WAVE_CHEB;
+}
+
+// Leapfrog belongs to the two-level wave state and the wave state to leapfrog.
+static nv_status check_scheme(int32_t kind, int32_t scheme) {
+  if (scheme != NV_EULER && scheme != NV_RK4 && scheme != NV_LEAPFROG) return nv_fail(NV_EINVAL, "unknown scheme");
+  if ((kind == NV_RHS_WAVE_CHEB) != (scheme == NV_LEAPFROG))
+    return nv_fail(NV_EINVAL, "NV_LEAPFROG is the scheme of NV_RHS_WAVE_CHEB and only of it");
+  return NV_OK;
 }
 
 static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_samples* sm,
@@ -121,7 +137,7 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
   if (e != NV_OK) return e;
   if (!sm || !st) return nv_fail(NV_EINVAL, "samples and steps must not be NULL");
   if (S < 1 || S > (1 << 24)) return nv_fail(NV_EINVAL, "S must be 1..2^24");
-  if (st->scheme != NV_EULER && st->scheme != NV_RK4) return nv_fail(NV_EINVAL, "unknown scheme");
+  if ((e = check_scheme(rhs->kind, st->scheme)) != NV_OK) return e;
   if (st->prec < NV_FP64 || st->prec > NV_TF32_REFINE) return nv_fail(NV_EINVAL, "unknown precision");
   e = nv_plan_steps(t0, T, S, st->dt, st->steps_per_slice, &P->m, &P->h);
   if (e != NV_OK) return e;
@@ -158,7 +174,12 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
     }
     case NV_MAP_AFFINE:
       if (!is_linear_kind(rhs->kind)) return nv_fail(NV_EINVAL, "affine maps need a linear rhs");
-      if (st->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "affine maps are built with RK4");
+      if (rhs->kind == NV_RHS_WAVE_CHEB) {
+        if (st->prec == NV_TF32_REFINE) return nv_fail(NV_ENOTSUP, "TF32 refinement is built for the heat equation");
+        P->aux_elems = wave_aux_elems(d / 2);
+      } else if (st->scheme != NV_RK4) {
+        return nv_fail(NV_ENOTSUP, "affine maps are built with RK4");
+      }
       P->elems_per_slice = (int64_t)d * (d + 1);
       break;
     default:
@@ -180,7 +201,8 @@ static nv_status alloc_maps(nv_maps* P) {
   const size_t xoff = 256;
   // 2 float64 chain vectors + a triple buffer of chain states (tiled chain) + slack
   const size_t coff = align256(xoff + sizeof(double) * 5 * (size_t)P->dim + 64);
-  P->ws_bytes = coff + sizeof(double) * (size_t)(P->coef_per_slice * P->S);
+  const size_t aoff = align256(coff + sizeof(double) * (size_t)(P->coef_per_slice * P->S));
+  P->ws_bytes = aoff + sizeof(double) * (size_t)P->aux_elems;
   e = nv_cuda_check(cudaMalloc(&P->ws, P->ws_bytes), "workspace allocation");
   if (e != NV_OK) { cudaFree(P->data); P->data = nullptr; P->ws = nullptr; return e; }
   char* w = static_cast<char*>(P->ws);
@@ -189,6 +211,7 @@ static nv_status alloc_maps(nv_maps* P) {
   P->bar = reinterpret_cast<unsigned*>(w + 16);
   P->xbuf = reinterpret_cast<double*>(w + xoff);
   P->coef = P->coef_per_slice ? reinterpret_cast<double*>(w + coff) : nullptr;
+  P->aux = P->aux_elems ? reinterpret_cast<double*>(w + aoff) : nullptr;
   return nv_cuda_check(cudaMemset(P->ws, 0, 256), "workspace reset");
 }
 
@@ -212,11 +235,11 @@ extern "C" nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T
   nv_maps* M = *maps;
   if (M) {
     if (M->bytes != P.bytes || M->map != P.map || M->prec != P.prec || M->dim != P.dim ||
-        M->S != P.S || M->coef_per_slice != P.coef_per_slice)
+        M->S != P.S || M->coef_per_slice != P.coef_per_slice || M->aux_elems != P.aux_elems)
       return nv_fail(NV_EINVAL, "existing maps have different sizes; destroy them first");
     // keep storage and scratch, take the new problem description
     P.data = M->data; P.ws = M->ws; P.ws_bytes = M->ws_bytes; P.status = M->status;
-    P.oob = M->oob; P.bar = M->bar; P.xbuf = M->xbuf; P.coef = M->coef;
+    P.oob = M->oob; P.bar = M->bar; P.xbuf = M->xbuf; P.coef = M->coef; P.aux = M->aux;
     P.scan_ws = M->scan_ws; P.scan_ws_bytes = M->scan_ws_bytes; P.device = M->device;
     *M = P;
   } else {
@@ -286,7 +309,7 @@ extern "C" nv_status nv_serial_fine(const nv_rhs* rhs, double t0, double T, int3
   nv_status e = check_rhs(rhs, P.params, &P.nparams);
   if (e != NV_OK) return e;
   if (S < 1) return nv_fail(NV_EINVAL, "S must be >= 1");
-  if (steps->scheme != NV_EULER && steps->scheme != NV_RK4) return nv_fail(NV_EINVAL, "unknown scheme");
+  if ((e = check_scheme(rhs->kind, steps->scheme)) != NV_OK) return e;
   e = nv_plan_steps(t0, T, S, steps->dt, steps->steps_per_slice, &P.m, &P.h);
   if (e != NV_OK) return e;
   P.rhs_kind = rhs->kind;
@@ -305,6 +328,7 @@ extern "C" nv_status nv_serial_fine(const nv_rhs* rhs, double t0, double T, int3
     if (steps->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "advection-diffusion serial solve uses RK4");
     return launch_serial_advdiff(&P, y0_dev, yT_dev, s);
   }
+  if (rhs->kind == NV_RHS_WAVE_CHEB) return launch_serial_wave(&P, y0_dev, yT_dev, s);
   return launch_serial_table(rhs->kind, P.params, t0, P.H, P.h, S, P.m, steps->scheme, y0_dev,
                              yT_dev, s);
 }

@@ -41,6 +41,8 @@ struct nv_maps {
   double* xbuf;                // 2 * dim doubles (ping-pong chain state)
   double* coef;                // per-slice staged coefficients (may be NULL)
   int64_t coef_per_slice;
+  double* aux;                 // operator storage (wave: D and D2), may be NULL
+  int64_t aux_elems;
   // reduced-precision composition scratch (NV_TF32_REFINE), allocated lazily
   void* scan_ws;
   size_t scan_ws_bytes;

@@ -77,6 +77,26 @@ def test_build_rejects_bad_grid(lib):
         r, 0.0, 1.0, 4, s, nvp.steps("euler", 1e-3, prec="tf32_refine"), stream=0))
 
 
+def test_wave_scheme_and_dimension_checks(lib):
+    """The leapfrog scheme belongs to the two-level wave state and only to it;
+    the wave state has dimension 2(M-1); its maps have no TF32 path."""
+    aff = nvp.samples("affine")
+    wv = nvp.rhs("wave", 158)
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(wv, 0.0, 1.0, 4, aff, nvp.steps("rk4", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(nvp.rhs("heat1d", 16), 0.0, 1.0, 4, aff,
+                                                         nvp.steps("leapfrog", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(nvp.rhs("wave", 157), 0.0, 1.0, 4, aff,
+                                                         nvp.steps("leapfrog", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(nvp.rhs("wave", 162), 0.0, 1.0, 4, aff,
+                                                         nvp.steps("leapfrog", 1e-3), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(nvp.rhs("wave", 158, (40.0,)), 0.0, 1.0, 4, aff,
+                                                         nvp.steps("leapfrog", 1e-3), stream=0))
+    _expect(nvp.NV_ENOTSUP, lambda: nvp.build_propagators(wv, 0.0, 1.0, 4, aff,
+                                                          nvp.steps("leapfrog", 1e-3, prec="tf32_refine"), stream=0))
+    _expect(nvp.NV_EINVAL, lambda: nvp.build_propagators(wv, 0.0, 1.0, 4, nvp.samples("pl1d", 8, (-1,), (1,)),
+                                                         nvp.steps("leapfrog", 1e-3), stream=0))
+
+
 def test_null_handles(lib):
     assert lib.nv_compose(None, None, None, None, None) == nvp.NV_EBADMAP
     assert lib.nv_maps_info(None, None) == nvp.NV_EINVAL

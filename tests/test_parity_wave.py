@@ -1,0 +1,137 @@
+"""GPU parity of the wave-equation affine path (Section 5, eq. waveequation;
+Tables wave40 / wave80) against the FP64 oracle: slice maps on the doubled
+leapfrog state, their composition, and the serial leapfrog solve.
+
+Tolerances: float64 maps 1e-11 of max |A| (m <= 100 leapfrog steps of a
+dense 79 x 79 product, different summation order than numpy's BLAS); float64
+composed state 1e-10 (512 slices of a neutrally stable map: the oracle's own
+composition and serial solve differ by 7e-12).  float32 maps 1e-5 of max |A|
+(the oracle's steps run in numpy float32 reach 3.0e-6 at M = 80, m = 32);
+float32 composed state 2e-2 of the float64 result: all 512 slice maps are
+the same matrix, so their float32 rounding compounds coherently and without
+damping (the same emulation gives 6.3e-3)."""
+import numpy as np
+import pytest
+
+import paper_1304_6514_gb300 as nvp
+import workloads
+from oracle import nievergelt as nv
+from oracle import wave
+
+from gpu_util import need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(w):
+    m = nv.steps_per_slice(w.t0, w.T, w.S, w.dt)
+    return m, nv.step_size(w.t0, w.T, w.S, m)
+
+
+def _build(torch, w, prec):
+    r = nvp.rhs("wave", w.dim, w.params)
+    st = nvp.steps("leapfrog", w.dt, 0, prec)
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), st)
+    torch.cuda.synchronize()
+    return r, st, maps
+
+
+def _slice_map(maps, j, n, dtype):
+    blk = nvp.maps_slice(maps, j).cpu().numpy().astype(np.float64).reshape(n + 1, n)   # column-major: row = column
+    return blk[1:].T, blk[0]                                              # A_j (n, n), b_j (n,)
+
+
+@pytest.mark.parametrize("M,S,T", [(12, 5, 0.5), (40, 7, 1.0), (41, 3, 0.3), (42, 4, 0.4), (2, 3, 0.5)])
+def test_small_maps_elementwise_fp64(M, S, T):
+    """Every slice map, every element: d = 11 (one row group), 39 and 40 (the
+    40-row tile, full and ragged), 41 (the 80-row tile), 1 (M = 2); column
+    counts S (2d+1) that leave a ragged last tile."""
+    torch = need_gpu()
+    w = workloads.wave1d(M=M, S=S, T=T)
+    m, h = _plan(w)
+    r, st, maps = _build(torch, w, "fp64")
+    A, b = wave.build_affine(M, S, m, h)
+    n = w.dim
+    for j in range(S):
+        Aj, bj = _slice_map(maps, j, n, np.float64)
+        assert np.max(np.abs(Aj - A[j])) <= 1e-11 * np.abs(A[j]).max(), j
+        assert np.array_equal(bj, np.zeros(n))
+    y0 = workloads.wave1d_initial(M, h)
+    y = torch.tensor(y0, device="cuda")
+    yT = torch.empty_like(y)
+    lam = torch.empty((S + 1, n), dtype=torch.float64, device="cuda")
+    nvp.compose(maps, y, yT, lambdas=lam)
+    torch.cuda.synchronize()
+    ol = wave.compose(A, b, y0)
+    assert rel_l2(lam.cpu().numpy(), ol) <= 1e-11
+    maps.destroy()
+
+
+def test_full_size_fp64_sampled_slices_and_composition():
+    """M = 80, S = 512, T = 20 (Table wave80's largest N): whole maps of three
+    slices, and the composed state against the oracle's serial leapfrog solve
+    of all 16 384 steps."""
+    torch = need_gpu()
+    w = workloads.wave1d()
+    m, h = _plan(w)
+    r, st, maps = _build(torch, w, "fp64")
+    assert nvp.maps_info(maps).steps_per_slice == m == 32
+    A, _ = wave.build_affine(80, 1, m, h)
+    for j in (0, 255, 511):
+        Aj, bj = _slice_map(maps, j, w.dim, np.float64)
+        assert np.max(np.abs(Aj - A[0])) <= 1e-11 * np.abs(A[0]).max(), j
+        assert not np.any(bj)
+    y0 = workloads.wave1d_initial(80, h)
+    y = torch.tensor(y0, device="cuda")
+    yT = torch.empty_like(y)
+    nvp.compose(maps, y, yT)
+    torch.cuda.synchronize()
+    ys = wave.serial_fine(80, w.S, m, h, y0)
+    assert rel_l2(yT.cpu().numpy(), ys) <= 1e-10
+    maps.destroy()
+
+
+def test_full_size_fp32():
+    torch = need_gpu()
+    w = workloads.wave1d()
+    m, h = _plan(w)
+    r, st, maps = _build(torch, w, "fp32")
+    A, _ = wave.build_affine(80, 1, m, h)
+    for j in (0, 511):
+        Aj, _ = _slice_map(maps, j, w.dim, np.float32)
+        assert np.max(np.abs(Aj - A[0])) <= 1e-5 * np.abs(A[0]).max(), j
+    y0 = workloads.wave1d_initial(80, h)
+    y = torch.tensor(y0, device="cuda")
+    yT = torch.empty_like(y)
+    nvp.compose(maps, y, yT)
+    torch.cuda.synchronize()
+    ys = wave.serial_fine(80, w.S, m, h, y0)
+    assert rel_l2(yT.cpu().numpy(), ys) <= 2e-2
+    maps.destroy()
+
+
+def test_serial_fine_gpu_matches_oracle():
+    torch = need_gpu()
+    w = workloads.wave1d(M=40, S=64, T=16.0)          # Table wave40: M = 40, T = 16
+    m, h = _plan(w)
+    y0 = workloads.wave1d_initial(40, h)
+    y = torch.tensor(y0, device="cuda")
+    yT = torch.empty_like(y)
+    nvp.serial_fine(nvp.rhs("wave", w.dim), w.t0, w.T, w.S, nvp.steps("leapfrog", w.dt), y, yT)
+    torch.cuda.synchronize()
+    ys = wave.serial_fine(40, w.S, m, h, y0)
+    assert rel_l2(yT.cpu().numpy(), ys) <= 1e-11
+
+
+def test_solve_one_call_matches_serial():
+    """nv_solve (allocate, build, compose, free) on Table wave40's problem."""
+    torch = need_gpu()
+    w = workloads.wave1d(M=40, S=128, T=16.0)
+    m, h = _plan(w)
+    y0 = workloads.wave1d_initial(40, h)
+    y = torch.tensor(y0, device="cuda")
+    yT = torch.empty_like(y)
+    nvp.solve(nvp.rhs("wave", w.dim), w.t0, w.T, w.S, nvp.samples("affine"), nvp.steps("leapfrog", w.dt), y, yT)
+    torch.cuda.synchronize()
+    ys = wave.serial_fine(40, w.S, m, h, y0)
+    assert rel_l2(yT.cpu().numpy(), ys) <= 1e-10
