@@ -295,7 +295,9 @@ def gpu_peak_probe(torch):
 #   heat FP64 build, S = 512 capture: 207.34 MB for 131 072 homogeneous columns
 #   advection-diffusion FP32 build, S = 8 capture: 476.02 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 502.0 MB for 561 987 584 table bytes
+#   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 NCU_TRAFFIC_PER_UNIT = {
+    "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
     "heat_horner_kernel<double,8,0>": (207.34e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (476.02e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (502.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
@@ -637,7 +639,11 @@ def run_wave(args):
             "variants": out, "time_to_solution_ms": {"fp64": step_ms, "fp32": f32["build_ms"] + f32["compose_ms"]},
             "roofline": {"bound": "alu", "kernel": "wave_build_kernel<double,80,2>",
                          "achieved": f64["build_tflops"], "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                         "frac": f64["build_tflops"] * 1e12 / FP64_PEAK_NOMINAL, "traffic": None,
+                         "frac": f64["build_tflops"] * 1e12 / FP64_PEAK_NOMINAL,
+                         "traffic": ncu_traffic("wave_build_kernel<double,80,2>", w.S * (w.dim + 1))[0]
+                         if M == 80 else None,
+                         "traffic_source": ncu_traffic("wave_build_kernel<double,80,2>", 1)[1],
+                         "algorithmic_bytes": f64["map_bytes"],
                          "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)", "flop_per_launch": flop},
             "gpu_launches": 3 * K, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

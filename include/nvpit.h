@@ -367,7 +367,13 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
  *   key 5: float64 correction passes of NV_TF32_REFINE (default 0 = three
  *          passes; a negative value returns the unrefined tensor-core states)
- * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key. */
+ *   key 6: form of the RK4 step for the homogeneous heat columns: 0 auto (the
+ *          nine-point stencil where every lane holds >= 4 whole rows, else
+ *          Horner stages), 1 Horner stages, 2 nine-point stencil where it
+ *          applies.  Both are the classical RK4 step of y' = Ly exactly; they
+ *          differ in rounding only.
+ * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
+ * or an out-of-range value of key 6. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

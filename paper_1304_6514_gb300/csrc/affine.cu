@@ -28,6 +28,7 @@ struct HeatArgs {
   double t0, H, h;
   double kappa, amp;     // NV_RHS_HEAT1D parameters
   int varcoef;           // NV_RHS_HEAT1D_VARCOEF
+  double poly9[5];       // nine-point form of the RK4 step: weights c_0..c_4
 };
 
 // Neighbour values of a lane-blocked vector: left of row lane*R, right of row
@@ -234,6 +235,72 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 1) heat_horne
 #pragma unroll
     for (int i = 0; i < R; ++i) y[i] = (lane * R + i == c - 1) ? (T)1 : (T)0;
     for (int64_t i = 0; i < a.m; ++i) heat_horner_step<R>(y, v, cdx, h, lane, n);
+    store_column<R, TF32OUT>(y, column_stage<R, T>(), out + ((int64_t)j * cols + c) * n, lane, n);
+  }
+}
+
+// Homogeneous columns of a time-invariant operator, the RK4 step as one
+// nine-point stencil.  For y' = Ly with L = cdx [1,-2,1] the classical RK4
+// step is y <- P(hL) y with P(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, and the
+// powers of the [1,-2,1] stencil ([1,-4,6,-4,1], ...) make P(hL) a symmetric
+// stencil of half-width 4 with weights c_0..c_4, polynomials in a = h cdx.
+// The Dirichlet ends hold exactly under odd reflection about the zero
+// boundary value (y_{-1-k} = -y_{-1+k}), which L and so every power of L
+// preserves.  Nine multiply-adds per point and step (four sums, one multiply,
+// four FMAs) against twelve for the Horner stages.  Lane l holds rows
+// l*R .. l*R+R-1; R >= 4 so the four-row halo comes from one neighbour lane,
+// and n is a multiple of R so the right end falls on a lane boundary.
+template <typename T, int R, bool TF32OUT>
+__global__ void __launch_bounds__(256, (sizeof(T) * R <= 64 && R <= 8) ? 4 : 1) heat_poly9_kernel(HeatArgs a) {
+  static_assert(R >= 4, "the halo must fit in one neighbour lane");
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n, cols = n + 1;
+  const int last = n / R - 1;                       // lane holding row n-1
+  const int64_t total = (int64_t)a.S * n;
+  const T c0 = (T)a.poly9[0], c1 = (T)a.poly9[1], c2 = (T)a.poly9[2], c3 = (T)a.poly9[3], c4 = (T)a.poly9[4];
+  T* out = reinterpret_cast<T*>(a.out);
+  for (int64_t w = warp0; w < total; w += nwarps) {
+    const int j = (int)(w / n);
+    const int c = 1 + (int)(w - (int64_t)j * n);
+    T y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = (lane * R + i == c - 1) ? (T)1 : (T)0;
+    for (int64_t step = 0; step < a.m; ++step) {
+      T e[R + 8];                                   // rows lane*R-4 .. lane*R+R+3
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        e[q] = __shfl_up_sync(0xffffffffu, y[R - 4 + q], 1);
+        e[R + 4 + q] = __shfl_down_sync(0xffffffffu, y[q], 1);
+      }
+      if (lane == 0) {                              // rows -4..-1 = -y2, -y1, -y0, 0
+        e[0] = -y[2];
+        e[1] = -y[1];
+        e[2] = -y[0];
+        e[3] = (T)0;
+      }
+      if (lane == last) {                           // rows n..n+3 = 0, -y_{n-1}, -y_{n-2}, -y_{n-3}
+        e[R + 4] = (T)0;
+        e[R + 5] = -y[R - 1];
+        e[R + 6] = -y[R - 2];
+        e[R + 7] = -y[R - 3];
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) e[i + 4] = y[i];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        T acc = c4 * (e[i] + e[i + 8]);
+        acc = fma(c3, e[i + 1] + e[i + 7], acc);
+        acc = fma(c2, e[i + 2] + e[i + 6], acc);
+        acc = fma(c1, e[i + 3] + e[i + 5], acc);
+        y[i] = fma(c0, e[i + 4], acc);
+      }
+      if (lane > last) {                            // lanes past the last row stay zero
+#pragma unroll
+        for (int i = 0; i < R; ++i) y[i] = (T)0;
+      }
+    }
     store_column<R, TF32OUT>(y, column_stage<R, T>(), out + ((int64_t)j * cols + c) * n, lane, n);
   }
 }
@@ -629,6 +696,17 @@ static HeatArgs heat_args(const nv_maps* M) {
   a.varcoef = M->rhs_kind == NV_RHS_HEAT1D_VARCOEF;
   a.kappa = (!a.varcoef && M->nparams > 0) ? M->params[0] : 1.0;
   a.amp = (!a.varcoef && M->nparams > 1) ? M->params[1] : 1.0;
+  // P(hL) with L = cdx [1,-2,1]: sum over k of (h cdx)^k / k! times the k-th
+  // power of the stencil, whose weights at offsets 0..4 are, for k = 1..4,
+  // (-2, 1), (6, -4, 1), (-20, 15, -6, 1), (70, -56, 28, -8, 1)
+  const double dx = 1.0 / (double)(a.n + 1);
+  const double z = a.h * (a.kappa / (dx * dx));
+  const double z2 = z * z / 2.0, z3 = z * z * z / 6.0, z4 = z * z * z * z / 24.0;
+  a.poly9[0] = 1.0 - 2.0 * z + 6.0 * z2 - 20.0 * z3 + 70.0 * z4;
+  a.poly9[1] = z - 4.0 * z2 + 15.0 * z3 - 56.0 * z4;
+  a.poly9[2] = z2 - 6.0 * z3 + 28.0 * z4;
+  a.poly9[3] = z3 - 8.0 * z4;
+  a.poly9[4] = z4;
   return a;
 }
 
@@ -663,6 +741,22 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
   heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
   st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   if (st != NV_OK) return st;
+  if constexpr (R >= 4) {
+    if (g_tune.heat_step_form != 1 && a.n % R == 0) {
+      if constexpr (sizeof(T) == 4) {
+        if (tf32out) {
+          st = persistent_grid(heat_poly9_kernel<T, R, true>, block, (int64_t)a.S * a.n, &grid);
+          if (st != NV_OK) return st;
+          heat_poly9_kernel<T, R, true><<<grid, block, 0, s>>>(a);
+          return nv_cuda_check(cudaGetLastError(), "heat_poly9_kernel launch");
+        }
+      }
+      st = persistent_grid(heat_poly9_kernel<T, R, false>, block, (int64_t)a.S * a.n, &grid);
+      if (st != NV_OK) return st;
+      heat_poly9_kernel<T, R, false><<<grid, block, 0, s>>>(a);
+      return nv_cuda_check(cudaGetLastError(), "heat_poly9_kernel launch");
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (tf32out) {
       st = persistent_grid(heat_horner_kernel<T, R, true>, block, (int64_t)a.S * a.n, &grid);

@@ -104,5 +104,6 @@ struct nv_tunables {
   int chain_cluster;       // CTAs per cluster of the d <= 512 chain (0 auto, < 0 grid-wide)
   int scan_block;          // slices per block of the tensor-core scan (0 auto)
   int refine_passes;       // float64 correction passes of NV_TF32_REFINE (0 = 1, < 0 none)
+  int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil
 };
 extern nv_tunables g_tune;

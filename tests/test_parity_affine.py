@@ -44,6 +44,32 @@ def test_heat_small_elementwise_fp64(n, S):
     assert rel_l2(yT, olam[-1]) <= 1e-11
 
 
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("n,S", [(128, 3), (200, 4), (256, 3), (512, 2)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_heat_step_forms_elementwise(form, n, S, prec, tol):
+    """Both forms of the homogeneous RK4 step (1: Horner stages, 2: the
+    nine-point stencil with odd reflection at the Dirichlet ends) give the
+    oracle's maps: n = 128 (four rows per lane), 200 (eight rows, lanes 25..31
+    idle, right end inside the warp), 256, 512 (sixteen rows).  Step size at
+    the RK4 stability edge, h cdx |lambda_max| = 2."""
+    torch = need_gpu()
+    dt = 2.0 / (4.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=S * 3 * dt, dt=dt)
+    nvp.tune_set(6, form)
+    try:
+        _, A, b, yT, lam = _heat(torch, w, prec)
+    finally:
+        nvp.tune_set(6, 0)
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    assert rel_max(A, oA) <= tol
+    assert rel_max(b, ob) <= tol
+    olam = nv.compose_affine(oA, ob, w.y0)
+    assert rel_l2(lam, olam) <= (1e-11 if prec == "fp64" else 1e-4)
+
+
 def test_heat_small_fp32():
     torch = need_gpu()
     w = workloads.heat1d(n=40, S=7, T=0.003, dt=1e-4)
