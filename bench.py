@@ -292,13 +292,13 @@ def gpu_peak_probe(torch):
 # DRAM bytes (read + write) per unit of output from one ncu capture of each
 # dominant kernel, scaled to the bench's launch by the units it writes (the
 # captures ran smaller cases of the same kernels; see profiles/):
-#   heat FP64 build, S = 512 capture: 207.34 MB for 131 072 homogeneous columns
+#   heat FP64 build (nine-point form), S = 512 capture: 206.55 MB for 131 072 columns
 #   advection-diffusion FP32 build, S = 8 capture: 476.02 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 502.0 MB for 561 987 584 table bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 NCU_TRAFFIC_PER_UNIT = {
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
-    "heat_horner_kernel<double,8,0>": (207.34e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
+    "heat_poly9_kernel<double,8,0>": (206.55e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (476.02e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (502.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
 }
@@ -846,11 +846,13 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_solution_ms": statistics.mean(res["step_ms"]),
         "wall_s_timed_region": wall,
-        "roofline": {"bound": "alu", "kernel": "heat_horner_kernel<double,8,0>",
+        "roofline": {"bound": "alu", "kernel": "heat_poly9_kernel<double,8,0>",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL,
-                     "traffic": ncu_traffic("heat_horner_kernel<double,8,0>", w.S * w.dim)[0],
-                     "traffic_source": ncu_traffic("heat_horner_kernel<double,8,0>", 1)[1],
+                     "flop_per_unit": "20 per component-step: the Horner-form RK4 step; the kernel's "
+                                      "nine-point form executes 9 FP64 instructions (13 FLOP) for it",
+                     "traffic": ncu_traffic("heat_poly9_kernel<double,8,0>", w.S * w.dim)[0],
+                     "traffic_source": ncu_traffic("heat_poly9_kernel<double,8,0>", 1)[1],
                      "algorithmic_bytes": w.S * w.dim * w.dim * 8,
                      "timed": "the build call (forcing-column kernel + this kernel, 99 % of it), CUDA events",
                      "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, FMA = 2)",

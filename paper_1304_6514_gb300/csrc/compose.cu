@@ -186,13 +186,25 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
   }
 }
 
-// TMA-fed variant (d <= 256, rows per CTA rpc <= 16): each CTA's rows of A_j
-// (rpc x d, one 3-D box) are copied by the tensor memory accelerator into a
-// ring of kRing shared-memory stages, kRing - 1 slices ahead, completing on an
-// mbarrier.  The copies run in the async proxy, so the release half of the
-// cluster barrier does not wait for them and HBM latency leaves the
-// dependency chain.  Stage layout: element (row r, column c) at c*rpc + r.
+// TMA-fed variant (64 <= d <= 256, d % 16 == 0; 16 CTAs x 16 rows): each
+// CTA's rows of A_j (16 x d, one 3-D box) are copied by the tensor memory
+// accelerator into a ring of kRing shared-memory stages, kRing - 1 slices
+// ahead, completing on an mbarrier; the copies run in the async proxy, so no
+// load sits on the dependency chain.  Stage layout: element (row r, column c)
+// at c*16 + r.
+//
+// The new state is exchanged without a cluster barrier: the lane that owns a
+// row stores it into the matching state buffer of every CTA of the cluster
+// with st.async, which completes bytes on that CTA's state mbarrier, and a CTA
+// starts step k+1 as soon as its own barrier has counted all d values of
+// x_{k+1}.  Two state buffers alternate; buffer (k+2) & 1 is rewritten only
+// by senders that already hold x_{k+1}, which every CTA sends after it has
+// read x_k, so no CTA overwrites a state another is still reading.  The
+// final state x_len is written to global memory only.  Every wait is bounded
+// (1 s of globaltimer); a CTA that gives up records NV_ETIMEOUT, stops
+// sending and leaves the loop, so the others give up at their next wait.
 constexpr int kRing = 3;
+constexpr int kChainRpc = 16;   // rows per CTA of the TMA chain
 
 __device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -215,38 +227,88 @@ __device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// Wait for a phase completed by other CTAs' st.async: acquire at cluster scope.
+__device__ __forceinline__ bool state_wait(uint64_t* bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+        "selp.b32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(cta_smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void arm_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cta_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+               "l"(__double_as_longlong(v)), "r"(bar)
+               : "memory");
+}
+
 template <typename MT, typename AT>
 __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 ChainsArgs a, int* status) {
+  constexpr int rpc = kChainRpc;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
   const int q = (int)(blockIdx.x / csize);
   extern __shared__ __align__(128) unsigned char ring_smem[];
-  const int n = a.n, rpc = a.rpc;
+  const int n = a.n;
   const int stage_elems = rpc * n;
   MT* ring = reinterpret_cast<MT*>(ring_smem);                          // kRing stages
   // per stage also rpc values of v_j and of add_{j+1}, as doubles (16-byte slots)
   double* vring = reinterpret_cast<double*>(ring + kRing * stage_elems);
   double* aring = vring + kRing * rpc;
   AT* xs = reinterpret_cast<AT*>(aring + kRing * rpc);                 // two state buffers
-  AT* red = xs + 2 * n;                                                // blockDim partials
+  AT* red = xs + 2 * n;                                                // per-warp row partials
   uint64_t* full = reinterpret_cast<uint64_t*>(
       ((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);
+  uint64_t* xbar = full + kRing;                                       // state buffers 0, 1
   __shared__ int abort_flag;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int r = tid % rpc, cgi = tid / rpc, ncg = blockDim.x / rpc;
-  const int row = (int)rank * rpc + r;
-  const bool active = (cgi < ncg) && (row < n);
+  const int my_row = (int)rank * rpc + (lane & (rpc - 1));              // row of a lane in warp 0
+  const bool active = (int)rank * rpc + r < n;
+  // CTAs past row n - 1 (d < 256) own no rows: they neither read nor send a
+  // state and take no part in the exchange
+  const unsigned owners = (unsigned)(n / rpc);
+  const bool has_rows = rank < owners;
   const int j0 = q * a.len;
   const int len = min(a.len, a.S - j0);
   const int vsz = a.v_double ? 8 : (int)sizeof(MT);
   const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT)) + (uint32_t)(rpc * vsz) +
                                (a.add ? (uint32_t)(rpc * 8) : 0u);
+  const uint32_t state_bytes = (uint32_t)(n * sizeof(AT));
 
   if (tid == 0) {
-    for (int i = 0; i < kRing; ++i)
+    for (int i = 0; i < kRing + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cta_smem_u32(&full[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (has_rows && len >= 2) arm_tx(&xbar[1], state_bytes);   // x_1, sent during step 0
+    if (has_rows && len >= 3) arm_tx(&xbar[0], state_bytes);   // x_2, sent during step 1
     abort_flag = 0;
   }
   __syncthreads();
@@ -277,7 +339,7 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
     }
   };
   int issued = 0;   // copies issued so far (thread 0)
-  if (tid == 0)
+  if (tid == 0 && has_rows)
     for (; issued < min(kRing - 1, len); ++issued) issue(issued);
 
   const double* x0 = a.x0 ? a.x0 + (int64_t)q * a.x0_stride : nullptr;
@@ -285,45 +347,80 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   if (q == 0 && rank == 0 && a.write_state0 && a.states)
     for (int i = tid; i < n; i += blockDim.x)
       a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
-  cl.sync();
+  cl.sync();   // barriers initialised and armed, x_0 in place, before any st.async
+
+  // remote addresses of the two state buffers and their barriers in CTA p = lane
+  uint32_t rx0 = 0u, rx1 = 0u, rb0 = 0u, rb1 = 0u;
+  if (warp == 0 && lane < (int)owners) {
+    rx0 = cluster_addr(cta_smem_u32(xs), (unsigned)lane);
+    rx1 = cluster_addr(cta_smem_u32(xs + n), (unsigned)lane);
+    rb0 = cluster_addr(cta_smem_u32(&xbar[0]), (unsigned)lane);
+    rb1 = cluster_addr(cta_smem_u32(&xbar[1]), (unsigned)lane);
+  }
 
   int consumed = len;
-  for (int k = 0; k < len; ++k) {
+  for (int k = 0; has_rows && k < len; ++k) {
     const int j = j0 + k;
     const int st = k % kRing;
-    if (!ring_wait(&full[st], (uint32_t)((k / kRing) & 1))) {
-      abort_flag = 1;
-      if (consumed == len) consumed = k;
+    bool ok = true;
+    if (k >= 1) ok = state_wait(&xbar[k & 1], (uint32_t)(((k - 1) >> 1) & 1));
+    if (ok) ok = ring_wait(&full[st], (uint32_t)((k / kRing) & 1));
+    if (!ok) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      consumed = k;
+      break;
+    }
+    if (tid == 0) {
+      if (k >= 1 && k + 2 <= len - 1) arm_tx(&xbar[k & 1], state_bytes);   // x_{k+2}
+      if (issued < len) issue(issued++);   // stage (k-1) % kRing, read during step k-1
     }
     const AT* x = xs + (k & 1) * n;
     const MT* Aj = ring + st * stage_elems;
     AT acc = 0;
     if (active)
       for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
-    red[tid] = acc;
+    // lanes l and l ^ 16 hold the same row (rpc = 16)
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (lane < rpc) red[warp * rpc + lane] = acc;
     __syncthreads();
-    if (tid < rpc && row < n) {
+    if (warp == 0) {
+      const int rr = lane & (rpc - 1), half = lane >> 4;
       AT s = 0;
-      for (int g = 0; g < ncg; ++g) s += red[g * rpc + tid];
-      const AT vj = a.v_double ? (AT)vring[st * rpc + r]
-                               : (AT)reinterpret_cast<const MT*>(vring + st * rpc)[r];
-      s += vj;
-      const int nb = ((k + 1) & 1) * n + row;
-      for (unsigned p = 0; p < csize; ++p) cl.map_shared_rank(xs, p)[nb] = s;
-      const int64_t o = (int64_t)(j + 1) * n + row;
-      const double out = (double)s + (a.add ? aring[st * rpc + r] : 0.0);
-      if (a.states) a.states[o] = out;
-      if (a.yT && j == a.S - 1) a.yT[row] = out;
-      if (a.finals && k == len - 1) a.finals[(int64_t)q * n + row] = (double)s;
+      for (int w = half * (nw >> 1); w < (half + 1) * (nw >> 1); ++w) s += red[w * rpc + rr];
+      s += __shfl_xor_sync(0xffffffffu, s, 16);
+      const bool own = lane < rpc && my_row < n;
+      if (own) {
+        const AT vj = a.v_double ? (AT)vring[st * rpc + rr]
+                                 : (AT)reinterpret_cast<const MT*>(vring + st * rpc)[rr];
+        s += vj;
+      }
+      // x_{k+1} to every CTA of the cluster (not sent after the last step)
+      if (k + 1 < len) {
+        const bool odd = (k + 1) & 1;
+        const uint32_t mx = odd ? rx1 : rx0, mb = odd ? rb1 : rb0;
+        for (unsigned p = 0; p < owners; ++p) {
+          const uint32_t ax = __shfl_sync(0xffffffffu, mx, (int)p);
+          const uint32_t ab = __shfl_sync(0xffffffffu, mb, (int)p);
+          if (own) st_async(ax + (uint32_t)(my_row * sizeof(AT)), s, ab);
+        }
+      }
+      if (own) {
+        const int64_t o = (int64_t)(j + 1) * n + my_row;
+        const double out = (double)s + (a.add ? aring[st * rpc + rr] : 0.0);
+        if (a.states) a.states[o] = out;
+        if (a.yT && j == a.S - 1) a.yT[my_row] = out;
+        if (a.finals && k == len - 1) a.finals[(int64_t)q * n + my_row] = (double)s;
+      }
     }
-    cl.sync();   // also: stage st (matrix, v and add slots) fully read, it may be refilled
-    if (tid == 0 && issued < len && !abort_flag) issue(issued++);
+    __syncthreads();   // red and the stage slots are reused
   }
   if (abort_flag && tid == 0) {
     record_status(status, NV_ETIMEOUT);
     for (int kk = min(consumed, issued); kk < issued; ++kk)   // copies in flight (bounded waits)
       ring_wait(&full[kk % kRing], (uint32_t)((kk / kRing) & 1));
   }
+  cl.sync();   // no CTA leaves while another may still address its shared memory
 }
 
 // Grid-wide chain for large d (d > 512, d a multiple of 4).  CTA (rb, cb)
@@ -440,7 +537,7 @@ static nv_status chain_encode_fn(EncodeTiledFnC* out) {
 // does not allow it (the caller then takes the register-prefetch kernel).
 static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStream_t s, int* status) {
   const int n = args_in.n;
-  const int block = 256, csize = 16, rpc = 16;
+  const int block = 256, csize = 16, rpc = kChainRpc;
   const size_t esz = f64 ? 8 : 4;
   if (n > 256 || n < 64 || n % 16 != 0) return NV_ENOTSUP;
   if (((uintptr_t)args_in.A % 16) || ((args_in.a_stride * esz) % 16)) return NV_ENOTSUP;
@@ -463,7 +560,7 @@ static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStre
   const void* fn = f64 ? (const void*)affine_chains_tma_kernel<double, double>
                        : (const void*)affine_chains_tma_kernel<float, float>;
   const size_t smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc +
-                      esz * (2 * (size_t)n + block) + 8 * kRing + 16;
+                      esz * (2 * (size_t)n + block) + 8 * (kRing + 2) + 16;
   if ((st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                           "cluster size attribute")) != NV_OK)
     return st;
