@@ -257,15 +257,29 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, unsigned rank) 
   return r;
 }
 
-__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
-               "r"(__float_as_uint(v)), "r"(bar)
+// 16 bytes to another CTA's shared memory, completing on its mbarrier.
+__device__ __forceinline__ void st_async16(uint32_t addr, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                           uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   addr),
+               "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(bar)
                : "memory");
 }
-__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
-               "l"(__double_as_longlong(v)), "r"(bar)
-               : "memory");
+
+// Eight consecutive row values (this lane's half of the CTA's 16 rows) as
+// 32 (float) or 64 (double) bytes of 16-byte stores.
+__device__ __forceinline__ void send_rows(const float* v, uint32_t addr, uint32_t bar) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    st_async16(addr + 16 * q, __float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
+               __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]), bar);
+}
+__device__ __forceinline__ void send_rows(const double* v, uint32_t addr, uint32_t bar) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const unsigned long long u0 = __double_as_longlong(v[2 * q]), u1 = __double_as_longlong(v[2 * q + 1]);
+    st_async16(addr + 16 * q, (uint32_t)u0, (uint32_t)(u0 >> 32), (uint32_t)u1, (uint32_t)(u1 >> 32), bar);
+  }
 }
 
 template <typename MT, typename AT>
@@ -349,13 +363,18 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
       a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
   cl.sync();   // barriers initialised and armed, x_0 in place, before any st.async
 
-  // remote addresses of the two state buffers and their barriers in CTA p = lane
+  // Sending: lane l of warp 0 stores rows 8 (l / 16) .. +7 of this CTA into
+  // CTA p = l % 16; its remote addresses of both state buffers and barriers.
+  const unsigned peer = (unsigned)(lane & 15);
+  const int half_rows = (lane >> 4) * 8;
+  const bool sender = warp == 0 && peer < owners;
   uint32_t rx0 = 0u, rx1 = 0u, rb0 = 0u, rb1 = 0u;
-  if (warp == 0 && lane < (int)owners) {
-    rx0 = cluster_addr(cta_smem_u32(xs), (unsigned)lane);
-    rx1 = cluster_addr(cta_smem_u32(xs + n), (unsigned)lane);
-    rb0 = cluster_addr(cta_smem_u32(&xbar[0]), (unsigned)lane);
-    rb1 = cluster_addr(cta_smem_u32(&xbar[1]), (unsigned)lane);
+  if (sender) {
+    const uint32_t off = (uint32_t)(((int)rank * rpc + half_rows) * sizeof(AT));
+    rx0 = cluster_addr(cta_smem_u32(xs), peer) + off;
+    rx1 = cluster_addr(cta_smem_u32(xs + n), peer) + off;
+    rb0 = cluster_addr(cta_smem_u32(&xbar[0]), peer);
+    rb1 = cluster_addr(cta_smem_u32(&xbar[1]), peer);
   }
 
   int consumed = len;
@@ -395,15 +414,13 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
                                  : (AT)reinterpret_cast<const MT*>(vring + st * rpc)[rr];
         s += vj;
       }
-      // x_{k+1} to every CTA of the cluster (not sent after the last step)
+      // x_{k+1} to every CTA that owns rows (not sent after the last step)
       if (k + 1 < len) {
+        AT v8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v8[i] = __shfl_sync(0xffffffffu, s, half_rows + i);
         const bool odd = (k + 1) & 1;
-        const uint32_t mx = odd ? rx1 : rx0, mb = odd ? rb1 : rb0;
-        for (unsigned p = 0; p < owners; ++p) {
-          const uint32_t ax = __shfl_sync(0xffffffffu, mx, (int)p);
-          const uint32_t ab = __shfl_sync(0xffffffffu, mb, (int)p);
-          if (own) st_async(ax + (uint32_t)(my_row * sizeof(AT)), s, ab);
-        }
+        if (sender) send_rows(v8, odd ? rx1 : rx0, odd ? rb1 : rb0);
       }
       if (own) {
         const int64_t o = (int64_t)(j + 1) * n + my_row;
@@ -413,7 +430,8 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
         if (a.finals && k == len - 1) a.finals[(int64_t)q * n + my_row] = (double)s;
       }
     }
-    __syncthreads();   // red and the stage slots are reused
+    // red and the stage slots are next written after the barrier that opens
+    // the next step, which warp 0 reaches only when it is done with them
   }
   if (abort_flag && tid == 0) {
     record_status(status, NV_ETIMEOUT);
