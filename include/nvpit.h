@@ -372,8 +372,13 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          Horner stages), 1 Horner stages, 2 nine-point stencil where it
  *          applies.  Both are the classical RK4 step of y' = Ly exactly; they
  *          differ in rounding only.
+ *   key 7: test hook, 0..4 (default 0): participants that never arrive, added to the
+ *          grid barrier of the cooperative row chain (selected by key 3 < 0).  Every
+ *          CTA then gives up at its first bounded wait (~0.4 s), records NV_ETIMEOUT
+ *          in the maps' status word (read by nv_maps_check) and returns; the
+ *          context stays usable.  The paper has no counterpart.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of key 6. */
+ * or an out-of-range value of keys 6 and 7. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

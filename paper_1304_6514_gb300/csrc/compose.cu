@@ -32,6 +32,7 @@ struct AffineChainArgs {
   double* xbuf;     // 2 * n
   unsigned* bar;
   int* status;
+  unsigned extra;   // barrier participants that never arrive (test hook; 0 in use)
 };
 
 // Loads issued ahead of the barrier: up to kPre columns per thread.
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256) affine_chain_kernel(AffineChainArgs a) {
     }
     if (k + 1 < a.S) {
       prefetch(k + 1);
-      if (!grid_barrier(a.bar, (unsigned)(k + 1) * G, a.status, &flag)) return;
+      if (!grid_barrier(a.bar, (unsigned)(k + 1) * (G + a.extra), a.status, &flag)) return;
     }
   }
 }
@@ -768,6 +769,7 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
   a.xbuf = M->xbuf;
   a.bar = M->bar;
   a.status = M->status;
+  a.extra = (unsigned)g_tune.test_barrier_extra;
   void* args[] = {&a};
   return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
                        "affine_chain_kernel cooperative launch");

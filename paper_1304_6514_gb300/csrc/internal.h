@@ -105,5 +105,6 @@ struct nv_tunables {
   int scan_block;          // slices per block of the tensor-core scan (0 auto)
   int refine_passes;       // float64 correction passes of NV_TF32_REFINE (0 = 1, < 0 none)
   int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil
+  int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
 };
 extern nv_tunables g_tune;

@@ -167,3 +167,35 @@ def test_chain_launch_shapes(cluster, rpc, prec, tol):
     oA, ob = nv.build_affine(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
                              w.t0, w.T, w.S, m, w.dim)
     assert rel_l2(lam, nv.compose_affine(oA, ob, w.y0)) <= tol
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_survives():
+    """A grid barrier that nothing completes (test hook: one participant that
+    never arrives) makes every CTA of the row chain give up at its bounded
+    wait; the status word reports NV_ETIMEOUT, and the next composition on the
+    same maps and context is correct."""
+    torch = need_gpu()
+    w = workloads.heat1d(n=40, S=7, T=0.003, dt=5e-5)
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), nvp.steps("rk4", w.dt))
+    y0 = torch.tensor(w.y0, device="cuda")
+    yT = torch.empty_like(y0)
+    nvp.tune_set(3, -1)
+    try:
+        nvp.tune_set(7, 1)
+        try:
+            nvp.compose(maps, y0, yT)
+            with pytest.raises(nvp.NvError) as ei:
+                nvp.maps_check(maps)
+            assert ei.value.status == nvp.NV_ETIMEOUT
+        finally:
+            nvp.tune_set(7, 0)
+        nvp.compose(maps, y0, yT)
+        nvp.maps_check(maps)
+    finally:
+        nvp.tune_set(3, 0)
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, w.dim)
+    assert rel_l2(yT.cpu().numpy(), nv.compose_affine(oA, ob, w.y0)[-1]) <= 1e-11
+    maps.destroy()
