@@ -25,6 +25,11 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The oracle timed as the CPU baseline runs on one host thread: no BLAS thread
+# pool behind numpy's products (set before numpy is first imported), so the
+# "cores": 1 in the baseline objects is what it used.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "propagator-build trajectory-steps/s + time-to-solution vs plain at fixed error"
 UNIT = "trajectory-steps/s"

@@ -45,9 +45,23 @@ struct BatchBuildArgs {
 // Largest CTA a variant with SPT samples per thread is compiled for.
 __host__ __device__ constexpr int batch_bound(int spt) { return spt <= 1 ? 1024 : (spt == 2 ? 512 : 256); }
 
+// Node coordinates lo + p d (float64, rounded to nearest, then to T) are the
+// same for every item: a CTA computes them once into shared memory when the
+// grid has at most kNodeCache nodes per axis, so the item loop does no float64
+// work.
+constexpr int kNodeCache = 1024;
+
 template <class R, typename T, int SPT, int RK4>
 __global__ void __launch_bounds__(batch_bound(SPT)) batch_build_kernel(BatchBuildArgs a) {
   __shared__ int item_s;
+  __shared__ T nodes[R::D][kNodeCache];
+  const int naxis = R::D == 1 ? a.samples : a.per_dim;
+  const bool cached = naxis <= kNodeCache;
+  if (cached)
+    for (int i = threadIdx.x; i < naxis; i += blockDim.x) {
+      nodes[0][i] = (T)__dadd_rn(a.lo0, __dmul_rn((double)i, a.d0));
+      if constexpr (R::D == 2) nodes[1][i] = (T)__dadd_rn(a.lo1, __dmul_rn((double)i, a.d1));
+    }
   T* out = reinterpret_cast<T*>(a.out);
   for (;;) {
     if (threadIdx.x == 0) item_s = (int)atomicAdd(a.counter, 1u);
@@ -69,11 +83,13 @@ __global__ void __launch_bounds__(batch_bound(SPT)) batch_build_kernel(BatchBuil
 #pragma unroll
       for (int c = 0; c < R::D; ++c) y[s][c] = comp[s][c] = (T)0;
       if constexpr (R::D == 1) {
-        y[s][0] = (T)__dadd_rn(a.lo0, __dmul_rn((double)k, a.d0));
+        if (act[s]) y[s][0] = cached ? nodes[0][k] : (T)__dadd_rn(a.lo0, __dmul_rn((double)k, a.d0));
       } else {
         const int p = k % a.per_dim, q = k / a.per_dim;
-        y[s][0] = (T)__dadd_rn(a.lo0, __dmul_rn((double)p, a.d0));
-        y[s][1] = (T)__dadd_rn(a.lo1, __dmul_rn((double)q, a.d1));
+        if (act[s]) {
+          y[s][0] = cached ? nodes[0][p] : (T)__dadd_rn(a.lo0, __dmul_rn((double)p, a.d0));
+          y[s][1] = cached ? nodes[1][q] : (T)__dadd_rn(a.lo1, __dmul_rn((double)q, a.d1));
+        }
       }
     }
     for (int64_t i = 0; i < d.m; ++i) {
