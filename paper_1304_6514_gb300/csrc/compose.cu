@@ -397,17 +397,9 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
     }
     const AT* x = xs + (k & 1) * n;
     const MT* Aj = ring + st * stage_elems;
-    // at most 256 / 16 columns per thread: unrolled so that all shared-memory
-    // loads issue together, four independent accumulators
-    AT part[4] = {(AT)0, (AT)0, (AT)0, (AT)0};
-    if (active) {
-#pragma unroll
-      for (int qq = 0; qq < 256 / kChainRpc; ++qq) {
-        const int c = cgi + qq * ncg;
-        if (c < n) part[qq & 3] = fma((AT)Aj[c * rpc + r], x[c], part[qq & 3]);
-      }
-    }
-    AT acc = (part[0] + part[1]) + (part[2] + part[3]);
+    AT acc = 0;
+    if (active)
+      for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
     // lanes l and l ^ 16 hold the same row (rpc = 16)
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     if (lane < rpc) red[warp * rpc + lane] = acc;
