@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--workload", default="heat1d",
-                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp", "wave"],
-                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp | wave")
+                    choices=["heat1d", "vdp_batch", "scalar", "advdiff2d", "chain3_mlp", "wave", "square"],
+                    help="heat1d (default line) | vdp_batch | scalar | advdiff2d | chain3_mlp | wave | square")
     ap.add_argument("--instances", type=int, default=0, help="vdp_batch: use the first N instances")
     ap.add_argument("--train-steps", type=int, default=0, help="chain3_mlp: total Adam steps (profiling)")
     return ap.parse_args()
@@ -669,6 +669,95 @@ def run_wave(args):
     return 0
 
 
+# The paper's GPU table (Section "graphics card implementation", Table gpuresults):
+# y' = y^2 on [0, 1/2], (dt exponent, N slices, M nodes) and the printed time
+# to solution in microseconds on a Tesla C2075 (backward Euler, Chebyshev
+# interpolation, single precision, allocation and transfers included).
+PAPER_GPU_TABLE = [(14, 32, 4, 193.6), (14, 64, 4, 187.5), (14, 128, 4, 208.4),
+                   (15, 32, 5, 253.7), (15, 64, 5, 228.5), (15, 128, 5, 257.8),
+                   (16, 32, 7, 388.3), (16, 64, 7, 338.9), (16, 128, 7, 392.0)]
+
+
+def run_square(args):
+    """The paper-shaped sweep of its GPU table: y' = y^2, y(0) = 1 on [0, 1/2],
+    dt = 2^-14..2^-16, N = 32..128 slices, M = 4..7 nodes, float32 forward
+    Euler with piecewise-linear tables on [0, 2].  Each configuration is timed
+    end to end as the paper times it: nv_solve (allocate, build, compose, free)
+    with the initial value copied from pinned host memory and the result copied
+    back, plus the device time of build + compose on resident maps.  The line's
+    value is the largest configuration's end-to-end throughput."""
+    torch, world, rank, local = _device_setup()
+    import numpy as np
+    import paper_1304_6514_gb300 as nvp
+    import workloads
+    stream = torch.cuda.Stream()
+    K, W = max(5, args.steps), max(3, args.warmup)
+    r = nvp.rhs("square", 1)
+    rows = []
+    for e, S, M, paper_us in PAPER_GPU_TABLE:
+        w = workloads.square_paper(e, S, M)
+        smp = nvp.samples("pl1d", M, w.lo, w.hi)
+        st = nvp.steps("euler", w.dt, 0, "fp32")
+        hy0 = torch.tensor(w.y0, dtype=torch.float64).pin_memory()
+        hyT = torch.empty(1, dtype=torch.float64).pin_memory()
+        dy0 = torch.empty(1, dtype=torch.float64, device="cuda")
+        dyT = torch.empty_like(dy0)
+        with torch.cuda.stream(stream):
+            def e2e():
+                dy0.copy_(hy0, non_blocking=True)
+                nvp.solve(r, w.t0, w.T, w.S, smp, st, dy0, dyT, stream=stream)
+                hyT.copy_(dyT, non_blocking=True)
+            for _ in range(W):
+                e2e()
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for k in range(K):
+                ev[k][0].record(stream)
+                e2e()
+                ev[k][1].record(stream)
+            stream.synchronize()
+            t_e2e = statistics.median(a.elapsed_time(b) for a, b in ev) * 1e3        # us
+            maps = nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, stream=stream)
+            for _ in range(W):
+                nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, maps=maps, stream=stream)
+                nvp.compose(maps, dy0, dyT, stream=stream)
+            for k in range(K):
+                ev[k][0].record(stream)
+                nvp.build_propagators(r, w.t0, w.T, w.S, smp, st, maps=maps, stream=stream)
+                nvp.compose(maps, dy0, dyT, stream=stream)
+                ev[k][1].record(stream)
+            stream.synchronize()
+            t_dev = statistics.median(a.elapsed_time(b) for a, b in ev) * 1e3
+            m = nvp.maps_info(maps).steps_per_slice
+            maps.destroy()
+            ys = torch.empty_like(dy0)
+            nvp.serial_fine(r, w.t0, w.T, w.S, nvp.steps("euler", w.dt, 0, "fp64"), dy0, ys, stream=stream)
+            stream.synchronize()
+        exact = 1.0 / (1.0 - w.T)
+        units = S * M * m
+        rows.append({"dt": f"2^-{e}", "N": S, "M": M, "steps_per_slice": m, "e2e_us": t_e2e,
+                     "device_us": t_dev, "traj_steps_per_s_e2e": units / (t_e2e * 1e-6),
+                     "rel_err_method": abs(float(hyT[0]) - exact) / exact,
+                     "rel_err_serial_fine_fp64": abs(float(ys[0]) - exact) / exact,
+                     "paper_us_tesla_c2075": paper_us,
+                     "paper_traj_steps_per_s": M * round(w.T / w.dt) / (paper_us * 1e-6)})
+    big = rows[-1]
+    line = {"metric": METRIC, "value": big["traj_steps_per_s_e2e"], "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": big["e2e_us"] * 1e-3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 build, f64 composition", "data": "synthetic",
+            "config": {"workload": "square_dt2^-16_N128_M7_euler_pl (paper GPU table shape)",
+                       "l2": "not flushed: the whole problem (3.6 KB of tables) lives in L2 as in the paper's runs"},
+            "e2e": {"value": big["traj_steps_per_s_e2e"], "unit": UNIT, "h2d_bytes_per_step": 8,
+                    "d2h_bytes_per_step": 8, "api": "nv_solve (allocates, builds, composes, frees)"},
+            "sweep": rows,
+            "paper_context": "Tesla C2075 (Fermi), backward Euler + Chebyshev interpolation, single precision; "
+                             "times include allocation, transfers and CPU interpolation",
+            "gpu_launches": 2 * K}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 FP32_FLOP_PER_CHAIN_STEP = 220      # RK4 step of the 6-D chain incl. compensated update
 MLP_FLOP_PER_SAMPLE_STEP = 6 * (7 * 256 + 2 * 256 * 256 + 256 * 6)   # fwd + bwd (2 + 4 x weights)
 
@@ -760,6 +849,8 @@ def main():
         return run_advdiff(args)
     if args.workload == "wave":
         return run_wave(args)
+    if args.workload == "square":
+        return run_square(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "vdp_batch":

@@ -142,3 +142,17 @@ def test_maps_reuse_allocates_nothing_new():
     assert maps2 is maps and np.array_equal(tab1, tab2)
     with pytest.raises(nvp.NvError):
         nvp.build_propagators(r, 0.0, 1.0, 5, smp, st, maps=maps)   # different S
+
+
+@pytest.mark.parametrize("e,S,M", [(14, 32, 4), (16, 128, 7)])
+def test_square_paper_table_shapes_fp32(e, S, M):
+    """The shapes of the paper's GPU table (y' = y^2 on [0, 1/2], dt = 2^-e, N
+    slices, M nodes) in float32 forward Euler with PL tables on [0, 2]: whole
+    tables and every boundary state against the oracle."""
+    torch = need_gpu()
+    w = workloads.square_paper(e, S, M)
+    tab, otab, lam, olam, oob, ooob = _pl_case(torch, "square", (), w.t0, w.T, S, M, 0.0, 2.0,
+                                               "euler", w.dt, 0, 1.0, "fp32")
+    assert rel_max(tab, otab) <= 1e-5
+    assert rel_l2(lam, olam) <= 1e-5
+    assert oob == ooob == 0
