@@ -94,11 +94,19 @@ typedef enum {
 typedef enum {
   NV_FP64 = 0,             /* integrate and store in float64                           */
   NV_FP32 = 1,             /* integrate and store in float32                           */
-  NV_TF32_REFINE = 2       /* affine only: maps integrated in float32 and stored rounded
+  NV_TF32_REFINE = 2,      /* affine only: maps integrated in float32 and stored rounded
                               to TF32 (float32 containers, 11 significant bits; the
                               forcing column b_j keeps float32), composition on tcgen05
                               tensor cores in TF32 with float32 accumulation, then
-                              float64 residual-correction passes (three by default)      */
+                              float64 residual-correction passes (three by default).
+                              Heat equations, d <= 256, d % 4 == 0                        */
+  NV_BF16_REFINE = 3       /* affine only: maps integrated in float32 and stored rounded
+                              to bfloat16 (half the bytes of float32), composed by the
+                              HBM-bound chain with float32 accumulation, then float64
+                              residual-correction passes (two by default) whose chains
+                              reuse the bfloat16 maps.  Advection-diffusion, d > 512,
+                              d % 8 == 0 (the large-d path, where the maps' bytes set the
+                              composition time)                                          */
 } nv_precision;
 
 typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;
@@ -164,8 +172,11 @@ nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T, int32_t S
  * chain of S matrix-vector products on all SMs (cooperative launch, bounded
  * grid barrier; NV_ETIMEOUT is recorded if a barrier wait gives up).
  * AFFINE NV_TF32_REFINE: blocked scan of the affine maps on tcgen05 tensor
- * cores, then one float64 residual-correction pass with float64 fine solves
- * from the approximate boundary states.  Buffers must not overlap. */
+ * cores, then float64 residual-correction passes with float64 fine solves
+ * from the approximate boundary states.  AFFINE NV_BF16_REFINE: the chain over
+ * the bfloat16 maps, then float64 correction passes (fine solves from the
+ * approximate boundary states, the correction chained over the same maps).
+ * Buffers must not overlap. */
 nv_status nv_compose(const nv_maps* maps, const double* y0_dev, double* yT_dev,
                      double* lambdas_dev, void* stream);
 
@@ -365,8 +376,9 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
  *          fits, up to 16; a negative value selects the grid-wide chain)
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
- *   key 5: float64 correction passes of NV_TF32_REFINE (default 0 = three
- *          passes; a negative value returns the unrefined tensor-core states)
+ *   key 5: float64 correction passes of NV_TF32_REFINE / NV_BF16_REFINE
+ *          (default 0 = three / two passes; a negative value returns the
+ *          unrefined reduced-precision states)
  *   key 6: form of the RK4 step for the homogeneous heat columns: 0 auto (the
  *          nine-point stencil where every lane holds >= 4 whole rows, else
  *          Horner stages), 1 Horner stages, 2 nine-point stencil where it

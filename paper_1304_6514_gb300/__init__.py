@@ -26,7 +26,7 @@ RHS = {"linear_scalar": 0, "square": 1, "cos_cubic": 2, "heat1d": 3, "vdp": 4, "
        "advdiff2d": 6, "heat1d_varcoef": 7, "wave": 8}
 SCHEME = {"euler": 0, "rk4": 1, "leapfrog": 2}
 MAP = {"pl1d": 0, "bilinear2d": 1, "affine": 2}
-PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2}
+PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2, "bf16_refine": 3}
 OOB = {"extrapolate": 0, "error": 1}
 
 
@@ -269,10 +269,10 @@ def maps_check(maps: Maps, stream=None) -> int:
 
 
 def maps_data(maps: Maps):
-    """The map data as a new CUDA tensor (float64 or float32, flat)."""
+    """The map data as a new CUDA tensor (float64, float32 or bfloat16, flat)."""
     import torch
     d = maps_info(maps)
-    dt = torch.float64 if d.elem_bytes == 8 else torch.float32
+    dt = {8: torch.float64, 4: torch.float32, 2: torch.bfloat16}[d.elem_bytes]
     out = torch.empty(d.bytes // d.elem_bytes, dtype=dt, device="cuda")
     _check(load_library().nv_maps_copy_out(maps.handle, out.data_ptr(), d.bytes, _stream(None)))
     return out
@@ -282,7 +282,7 @@ def maps_slice(maps: Maps, j: int, count: int = 1):
     """Map data of slices j .. j+count-1 as a new flat CUDA tensor."""
     import torch
     d = maps_info(maps)
-    dt = torch.float64 if d.elem_bytes == 8 else torch.float32
+    dt = {8: torch.float64, 4: torch.float32, 2: torch.bfloat16}[d.elem_bytes]
     out = torch.empty(d.elems_per_slice * count, dtype=dt, device="cuda")
     _check(load_library().nv_maps_copy_range(maps.handle, out.data_ptr(), j * d.elems_per_slice * d.elem_bytes,
                                              count * d.elems_per_slice * d.elem_bytes, _stream(None)))

@@ -13,6 +13,7 @@
 // polynomial of hL applied to y), with 3 instead of 5 float operations per
 // element and stage.  The forcing column and time-dependent operators take
 // the four RK4 stages literally.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -449,66 +450,103 @@ __device__ __forceinline__ const float* adv_weights<float>(const AdvArgs& a, int
   return a.cw32[stage];
 }
 
+// m Horner-form RK4 steps of one state held in the strip layout (thread t:
+// rows iy0 .. iy0+15 at column ix); the shared halo buffers belong to the CTA.
+template <typename T>
+struct AdvStripSmem {
+  T top[2][4][kAdvNx];          // first row of each strip block, per buffer
+  T bot[2][4][kAdvNx];          // last row
+  T edge[2][8][2][kAdvRows];    // per warp: strips of lanes 0 and 31
+};
+
+template <typename T>
+__device__ __forceinline__ void adv_strip_integrate(const AdvArgs& a, T* y, AdvStripSmem<T>& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx;
+  const int pw = warp ^ 1;            // the other warp of the same 64-wide row band
+  T v[kAdvRows];
+  int buf = 0;
+  for (int64_t i = 0; i < a.m; ++i) {
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
+#pragma unroll 1
+    for (int kk = 4; kk >= 1; --kk) {
+      const T* cw = adv_weights<T>(a, 4 - kk);
+      const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
+      sm.top[buf][blk][ix] = v[0];
+      sm.bot[buf][blk][ix] = v[kAdvRows - 1];
+      if (lane == 0 || lane == 31) {
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) sm.edge[buf][warp][lane == 31][r] = v[r];
+      }
+      __syncthreads();
+      const T above = sm.bot[buf][(blk + 3) & 3][ix];     // row iy0 - 1 (periodic)
+      const T below = sm.top[buf][(blk + 1) & 3][ix];     // row iy0 + 16
+      T nv[kAdvRows];
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) {
+        T xm = __shfl_up_sync(0xffffffffu, v[r], 1);
+        T xp = __shfl_down_sync(0xffffffffu, v[r], 1);
+        if (lane == 0) xm = sm.edge[buf][pw][1][r];        // ix - 1 lives in the other warp's lane 31
+        if (lane == 31) xp = sm.edge[buf][pw][0][r];       // ix + 1 in its lane 0
+        const T ym = r == 0 ? above : v[r - 1];
+        const T yp = r == kAdvRows - 1 ? below : v[r + 1];
+        T acc = fma(c0, v[r], y[r]);
+        acc = fma(cxm, xm, acc);
+        acc = fma(cxp, xp, acc);
+        acc = fma(cym, ym, acc);
+        nv[r] = fma(cyp, yp, acc);
+      }
+#pragma unroll
+      for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
+  }
+  __syncthreads();   // the shared halos are reused by the next state
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
   constexpr int n = kAdvNx * kAdvNx;
-  __shared__ T top[2][4][kAdvNx];     // first row of each strip block, per buffer
-  __shared__ T bot[2][4][kAdvNx];     // last row
-  __shared__ T edge[2][8][2][kAdvRows];  // per warp: strips of lanes 0 and 31
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ AdvStripSmem<T> sm;
+  const int tid = threadIdx.x;
   const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;
-  const int pw = warp ^ 1;            // the other warp of the same 64-wide row band
   T* out = reinterpret_cast<T*>(a.out);
   const int64_t total = (int64_t)a.S * (n + 1);
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int j = (int)(w / (n + 1));
     const int c = (int)(w - (int64_t)j * (n + 1));     // 0: solve from 0 (no forcing), else e_{c-1}
-    T y[kAdvRows], v[kAdvRows];
+    T y[kAdvRows];
 #pragma unroll
     for (int r = 0; r < kAdvRows; ++r) y[r] = ((c >= 1) && ((iy0 + r) * kAdvNx + ix == c - 1)) ? (T)1 : (T)0;
-    int buf = 0;
-    for (int64_t i = 0; i < a.m; ++i) {
-#pragma unroll
-      for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
-#pragma unroll 1
-      for (int kk = 4; kk >= 1; --kk) {
-        const T* cw = adv_weights<T>(a, 4 - kk);
-        const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
-        top[buf][blk][ix] = v[0];
-        bot[buf][blk][ix] = v[kAdvRows - 1];
-        if (lane == 0 || lane == 31) {
-#pragma unroll
-          for (int r = 0; r < kAdvRows; ++r) edge[buf][warp][lane == 31][r] = v[r];
-        }
-        __syncthreads();
-        const T above = bot[buf][(blk + 3) & 3][ix];     // row iy0 - 1 (periodic)
-        const T below = top[buf][(blk + 1) & 3][ix];     // row iy0 + 16
-        T nv[kAdvRows];
-#pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) {
-          T xm = __shfl_up_sync(0xffffffffu, v[r], 1);
-          T xp = __shfl_down_sync(0xffffffffu, v[r], 1);
-          if (lane == 0) xm = edge[buf][pw][1][r];        // ix - 1 lives in the other warp's lane 31
-          if (lane == 31) xp = edge[buf][pw][0][r];       // ix + 1 in its lane 0
-          const T ym = r == 0 ? above : v[r - 1];
-          const T yp = r == kAdvRows - 1 ? below : v[r + 1];
-          T acc = fma(c0, v[r], y[r]);
-          acc = fma(cxm, xm, acc);
-          acc = fma(cxp, xp, acc);
-          acc = fma(cym, ym, acc);
-          nv[r] = fma(cyp, yp, acc);
-        }
-#pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
-        buf ^= 1;
-      }
-#pragma unroll
-      for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
-    }
+    adv_strip_integrate<T>(a, y, sm);
     T* col = out + ((int64_t)j * (n + 1) + c) * n;
 #pragma unroll
     for (int r = 0; r < kAdvRows; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
-    __syncthreads();   // shared halos are reused by the next column
+  }
+}
+
+// Float64 defects of approximate boundary states for the correction passes of
+// NV_BF16_REFINE: d_j = g^j(lam_j) - lam_{j+1}, one CTA per slice integrating
+// lam_j over slice j in float64 (the operator is time-invariant and unforced,
+// so the Horner form is the RK4 step).  lam: (S+1) x n, d: S x n.
+__global__ void __launch_bounds__(256) advdiff_defect_kernel(AdvArgs a, const double* lam, double* d) {
+  constexpr int n = kAdvNx * kAdvNx;
+  __shared__ AdvStripSmem<double> sm;
+  const int tid = threadIdx.x;
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;
+  for (int j = blockIdx.x; j < a.S; j += gridDim.x) {
+    double y[kAdvRows];
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) y[r] = lam[(int64_t)j * n + (iy0 + r) * kAdvNx + ix];
+    adv_strip_integrate<double>(a, y, sm);
+#pragma unroll
+    for (int r = 0; r < kAdvRows; ++r) {
+      const int64_t o = (int64_t)(iy0 + r) * kAdvNx + ix;
+      d[(int64_t)j * n + o] = y[r] - lam[(int64_t)(j + 1) * n + o];
+    }
   }
 }
 
@@ -523,6 +561,23 @@ __global__ void __launch_bounds__(256) advdiff_affine_kernel(AdvArgs a) {
 constexpr int kAdvB = 8;                       // block edge
 constexpr int kAdvBlockThreads = (kAdvNx / kAdvB) * (kAdvNx / kAdvB);   // 64
 
+// Column output of the float32 block build: float32, or bfloat16 bits rounded
+// to nearest even (NV_BF16_REFINE), one 16-byte store per 4 / 8 values.
+__device__ __forceinline__ void adv_store_row(float* dst, const float* v) {
+  reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void adv_store_row(uint16_t* dst, const float* v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);   // low half = v[2q]
+    w[q] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <typename OutT>
 __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvArgs a) {
   constexpr int n = kAdvNx * kAdvNx;
   constexpr int TB = kAdvNx / kAdvB;           // 8 blocks per direction
@@ -533,7 +588,7 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvA
   const int ix0 = kAdvB * tx, iy0 = kAdvB * ty;
   const int t_left = ty * TB + (tx + TB - 1) % TB, t_right = ty * TB + (tx + 1) % TB;
   const int t_up = ((ty + TB - 1) % TB) * TB + tx, t_down = ((ty + 1) % TB) * TB + tx;
-  float* out = reinterpret_cast<float*>(a.out);
+  OutT* out = reinterpret_cast<OutT*>(a.out);
   const int64_t total = (int64_t)a.S * (n + 1);
   int buf = 0;
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
@@ -604,68 +659,24 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvA
 #pragma unroll
         for (int q = 0; q < kAdvB; ++q) y[r][q] = v[r][q];
     }
-    float* col = out + ((int64_t)j * (n + 1) + c) * n;
+    OutT* col = out + ((int64_t)j * (n + 1) + c) * n;
 #pragma unroll
-    for (int r = 0; r < kAdvB; ++r) {
-      float4* dst = reinterpret_cast<float4*>(col + (iy0 + r) * kAdvNx + ix0);
-      dst[0] = make_float4(y[r][0], y[r][1], y[r][2], y[r][3]);
-      dst[1] = make_float4(y[r][4], y[r][5], y[r][6], y[r][7]);
-    }
+    for (int r = 0; r < kAdvB; ++r) adv_store_row(col + (iy0 + r) * kAdvNx + ix0, y[r]);
   }
 }
 
 // Serial fine solve of the advection-diffusion system (one CTA, S*m steps).
 template <typename T>
 __global__ void __launch_bounds__(256) advdiff_serial_kernel(AdvArgs a, const double* y0, double* yT) {
-  __shared__ T top[2][4][kAdvNx];
-  __shared__ T bot[2][4][kAdvNx];
-  __shared__ T edge[2][8][2][kAdvRows];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ AdvStripSmem<T> sm;
+  const int tid = threadIdx.x;
   const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;
-  const int pw = warp ^ 1;
-  T y[kAdvRows], v[kAdvRows];
+  T y[kAdvRows];
 #pragma unroll
   for (int r = 0; r < kAdvRows; ++r) y[r] = (T)y0[(iy0 + r) * kAdvNx + ix];
-  int buf = 0;
-  const int64_t steps = (int64_t)a.S * a.m;
-  for (int64_t i = 0; i < steps; ++i) {
-#pragma unroll
-    for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
-#pragma unroll 1
-    for (int kk = 4; kk >= 1; --kk) {
-      const T* cw = adv_weights<T>(a, 4 - kk);
-      const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
-      top[buf][blk][ix] = v[0];
-      bot[buf][blk][ix] = v[kAdvRows - 1];
-      if (lane == 0 || lane == 31) {
-#pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) edge[buf][warp][lane == 31][r] = v[r];
-      }
-      __syncthreads();
-      const T above = bot[buf][(blk + 3) & 3][ix];
-      const T below = top[buf][(blk + 1) & 3][ix];
-      T nv[kAdvRows];
-#pragma unroll
-      for (int r = 0; r < kAdvRows; ++r) {
-        T xm = __shfl_up_sync(0xffffffffu, v[r], 1);
-        T xp = __shfl_down_sync(0xffffffffu, v[r], 1);
-        if (lane == 0) xm = edge[buf][pw][1][r];
-        if (lane == 31) xp = edge[buf][pw][0][r];
-        const T ym = r == 0 ? above : v[r - 1];
-        const T yp = r == kAdvRows - 1 ? below : v[r + 1];
-        T acc = fma(c0, v[r], y[r]);
-        acc = fma(cxm, xm, acc);
-        acc = fma(cxp, xp, acc);
-        acc = fma(cym, ym, acc);
-        nv[r] = fma(cyp, yp, acc);
-      }
-#pragma unroll
-      for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
-      buf ^= 1;
-    }
-#pragma unroll
-    for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
-  }
+  AdvArgs all = a;
+  all.m = (int64_t)a.S * a.m;                  // every slice's steps in one run
+  adv_strip_integrate<T>(all, y, sm);
 #pragma unroll
   for (int r = 0; r < kAdvRows; ++r) yT[(iy0 + r) * kAdvNx + ix] = (double)y[r];
 }
@@ -872,11 +883,17 @@ nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
     if (st != NV_OK) return st;
     advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
   } else {
-    // columns start at j * (n + 1) * n floats: 16-byte aligned for the
-    // float4 stores since n = 4096 and the map buffer is 256-byte aligned
-    st = persistent_grid(advdiff_block_kernel, kAdvBlockThreads, cols * 2, &grid);
-    if (st != NV_OK) return st;
-    advdiff_block_kernel<<<grid, kAdvBlockThreads, 0, s>>>(a);
+    // columns start at j * (n + 1) * n values: 16-byte aligned for the
+    // vector stores since n = 4096 and the map buffer is 256-byte aligned
+    if (M->prec == NV_BF16_REFINE) {
+      st = persistent_grid(advdiff_block_kernel<uint16_t>, kAdvBlockThreads, cols * 2, &grid);
+      if (st != NV_OK) return st;
+      advdiff_block_kernel<uint16_t><<<grid, kAdvBlockThreads, 0, s>>>(a);
+    } else {
+      st = persistent_grid(advdiff_block_kernel<float>, kAdvBlockThreads, cols * 2, &grid);
+      if (st != NV_OK) return st;
+      advdiff_block_kernel<float><<<grid, kAdvBlockThreads, 0, s>>>(a);
+    }
   }
   return nv_cuda_check(cudaGetLastError(), "advdiff_affine_kernel launch");
 }
@@ -886,4 +903,14 @@ nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, 
   const AdvArgs a = adv_args(M);
   advdiff_serial_kernel<double><<<1, 256, 0, s>>>(a, y0, yT);
   return nv_cuda_check(cudaGetLastError(), "advdiff_serial_kernel launch");
+}
+
+nv_status launch_advdiff_defect(const nv_maps* M, const double* lam, double* d, cudaStream_t s) {
+  if (M->dim != kAdvNx * kAdvNx) return nv_fail(NV_ENOTSUP, "advection-diffusion is built for a 64 x 64 grid");
+  const AdvArgs a = adv_args(M);
+  int grid = 0;
+  nv_status st = persistent_grid(advdiff_defect_kernel, 256, (int64_t)M->S * 8, &grid);
+  if (st != NV_OK) return st;
+  advdiff_defect_kernel<<<grid, 256, 0, s>>>(a, lam, d);
+  return nv_cuda_check(cudaGetLastError(), "advdiff_defect_kernel launch");
 }

@@ -33,6 +33,10 @@ struct AffineChainArgs {
   unsigned* bar;
   int* status;
   unsigned extra;   // barrier participants that never arrive (test hook; 0 in use)
+  // tiled chain only (the float64 correction of NV_BF16_REFINE):
+  const double* vadd;   // optional: v_j added to slice j's product (S x n)
+  const double* base;   // optional: added to every state written (S+1 x n)
+  int col0_off;         // 1: drop column 0 (b_j) of the maps
 };
 
 // Loads issued ahead of the barrier: up to kPre columns per thread.
@@ -454,8 +458,10 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
 template <typename MT, typename AT>
 __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
                                                                 AT* xb) {
+  // MT: double, float, or uint16_t holding bfloat16 bits (8 rows per load)
   constexpr int VEC = 16 / (int)sizeof(MT);
-  using V = typename std::conditional<sizeof(MT) == 4, float4, double2>::type;
+  using V = typename std::conditional<sizeof(MT) == 4, float4,
+                                      typename std::conditional<sizeof(MT) == 8, double2, uint4>::type>::type;
   extern __shared__ __align__(16) unsigned char sxt_raw[];
   AT* sx = reinterpret_cast<AT*>(sxt_raw);   // the cpc state values of this column block
   __shared__ int flag;
@@ -470,13 +476,14 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
   const MT* maps = reinterpret_cast<const MT*>(a.maps);
   const int64_t slice_elems = (int64_t)n * (n + 1);
   if (blockIdx.x == 0 && a.lambdas)
-    for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i];
+    for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i] + (a.base ? a.base[i] : 0.0);
+  const AT one = a.col0_off ? (AT)0 : (AT)1;
   for (int k = 0; k < a.S; ++k) {
     AT* acc_buf = xb + (k % 3) * n;
     const AT* in_buf = xb + ((k + 2) % 3) * n;
     AT* clr_buf = xb + ((k + 1) % 3) * n;
     for (int c = c0 + tid; c < c1; c += blockDim.x)
-      sx[c - c0] = c == 0 ? (AT)1 : (k == 0 ? (AT)a.y0[c - 1] : __ldcg(in_buf + c - 1));
+      sx[c - c0] = c == 0 ? one : (k == 0 ? (AT)a.y0[c - 1] : __ldcg(in_buf + c - 1));
     for (int i = blockIdx.x * blockDim.x + tid; i < n; i += G * blockDim.x) clr_buf[i] = (AT)0;
     __syncthreads();
     AT acc[VEC];
@@ -485,7 +492,14 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
     if (active) {
       const MT* A = maps + (int64_t)k * slice_elems + row0;
       auto madd = [&](const V& t, AT xc) {
-        if constexpr (VEC == 4) {
+        if constexpr (VEC == 8) {           // bfloat16: the high half of a float32
+          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
+            acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
+          }
+        } else if constexpr (VEC == 4) {
           acc[0] = fma((AT)t.x, xc, acc[0]);
           acc[1] = fma((AT)t.y, xc, acc[1]);
           acc[2] = fma((AT)t.z, xc, acc[2]);
@@ -506,6 +520,10 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
         for (int q = 0; q < kBatch; ++q) madd(t[q], sx[c + q - c0]);
       }
       for (; c < c1; ++c) madd(__ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n)), sx[c - c0]);
+      if (a.vadd && cb == 0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += (AT)a.vadd[(int64_t)k * n + row0 + v];
+      }
 #pragma unroll
       for (int v = 0; v < VEC; ++v) atomicAdd(acc_buf + row0 + v, acc[v]);
     }
@@ -513,9 +531,10 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
     if (cb == 0 && active) {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
-        const double xv = (double)__ldcg(acc_buf + row0 + v);
-        if (a.lambdas) a.lambdas[(int64_t)(k + 1) * n + row0 + v] = xv;
-        if (k == a.S - 1) a.yT[row0 + v] = xv;
+        const int64_t o = (int64_t)(k + 1) * n + row0 + v;
+        const double xv = (double)__ldcg(acc_buf + row0 + v) + (a.base ? a.base[o] : 0.0);
+        if (a.lambdas) a.lambdas[o] = xv;
+        if (k == a.S - 1 && a.yT) a.yT[row0 + v] = xv;
       }
     }
   }
@@ -674,14 +693,15 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   return launch_chains(a, f64, s, want_csize);
 }
 
-// Tiled grid-wide chain (d > 512, d % 4 == 0): one CTA per SM, row blocks of
-// 2048 (float32) / 1024 (float64) rows, column blocks sized to fill the grid.
-static nv_status launch_affine_chain_tile(const nv_maps* M, const double* y0, double* yT, double* lambdas,
-                                          cudaStream_t s) {
+// Tiled grid-wide chain (d > 512, d % 4 == 0; d % 8 == 0 for bfloat16 maps):
+// one CTA per SM, row blocks of 4096 (bfloat16) / 2048 (float32) / 1024
+// (float64) rows, column blocks sized to fill the grid.
+template <typename MT, typename AT>
+static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                            const TileChainExtra* ex, cudaStream_t s) {
   const int n = M->dim;
   const int block = 512;
-  const bool f64 = M->prec == NV_FP64;
-  const int vec = f64 ? 2 : 4;
+  const int vec = 16 / (int)sizeof(MT);
   const int RB = vec * block;
   const int nrb = (n + RB - 1) / RB;
   int dev = 0, sms = 0;
@@ -690,10 +710,9 @@ static nv_status launch_affine_chain_tile(const nv_maps* M, const double* y0, do
   const int ncb = std::max(1, sms / nrb);
   const int cpc = (n + 1 + ncb - 1) / ncb;
   const int G = nrb * ncb;
-  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  const size_t esz = sizeof(AT);
   const size_t smem = esz * (size_t)cpc;
-  const void* fn = f64 ? (const void*)affine_chain_tile_kernel<double, double>
-                       : (const void*)affine_chain_tile_kernel<float, float>;
+  const void* fn = (const void*)affine_chain_tile_kernel<MT, AT>;
   nv_status st;
   int per_sm = 0;
   if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem),
@@ -720,10 +739,25 @@ static nv_status launch_affine_chain_tile(const nv_maps* M, const double* y0, do
   a.xbuf = M->xbuf;
   a.bar = M->bar;
   a.status = M->status;
+  if (ex) {
+    a.vadd = ex->vadd;
+    a.base = ex->base;
+    a.col0_off = ex->col0_off;
+  }
   int nrb_arg = nrb, cpc_arg = cpc;
   void* args[] = {&a, &nrb_arg, &cpc_arg, &xb};
   return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
                        "affine_chain_tile_kernel cooperative launch");
+}
+
+nv_status launch_tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                            const TileChainExtra* ex, cudaStream_t s) {
+  if (M->prec == NV_FP64) return tile_chain<double, double>(M, y0, yT, lambdas, ex, s);
+  if (M->prec == NV_BF16_REFINE) {
+    if (M->dim % 8) return nv_fail(NV_ENOTSUP, "bfloat16 chain needs d %% 8 == 0");
+    return tile_chain<uint16_t, float>(M, y0, yT, lambdas, ex, s);
+  }
+  return tile_chain<float, float>(M, y0, yT, lambdas, ex, s);
 }
 
 nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
@@ -733,7 +767,7 @@ nv_status launch_affine_chain(const nv_maps* M, const double* y0, double* yT, do
     nv_status st = launch_affine_chain_cluster(M, y0, yT, lambdas, s, g_tune.chain_cluster);
     if (st != NV_ENOTSUP) return st;
   }
-  if (n > 512 && n % 4 == 0) return launch_affine_chain_tile(M, y0, yT, lambdas, s);
+  if (n > 512 && n % 4 == 0) return launch_tile_chain(M, y0, yT, lambdas, nullptr, s);
   const int block = 256;
   int rpc = rows_per_cta > 0 ? rows_per_cta : 16;
   rpc = std::min(rpc, block);

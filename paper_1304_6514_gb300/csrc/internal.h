@@ -73,6 +73,20 @@ nv_status launch_serial_fine(int32_t rhs_kind, int32_t dim, const double* params
                              const double* y0, double* yT, cudaStream_t s);
 nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
                              cudaStream_t s);
+nv_status launch_bf16_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
+                             cudaStream_t s);
+
+// Tiled grid-wide chain (d > 512) over the maps' own storage, with the
+// options of the float64 correction chain.
+struct TileChainExtra {
+  const double* vadd;   // v_j added to slice j's product (S x n), or NULL
+  const double* base;   // added to every state written (S+1 x n), or NULL
+  int col0_off;         // 1: drop column 0 (b_j) of the maps
+};
+nv_status launch_tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
+                            const TileChainExtra* ex, cudaStream_t s);
+// float64 defects of the advection-diffusion maps: d_j = g^j(lam_j) - lam_{j+1}
+nv_status launch_advdiff_defect(const nv_maps* M, const double* lam, double* d, cudaStream_t s);
 
 // Batched cluster chains (compose.cu, affine_chains_kernel): chain q runs
 // x <- A_j x + v_j over slices j = q*len .. min(S, (q+1)*len) - 1.

@@ -1,0 +1,69 @@
+// Reduced-precision composition with float64 refinement for large state
+// dimensions (NV_BF16_REFINE, the advection-diffusion system, d = 4096).
+//
+// At d = 4096 the composition for one initial state is a chain of S
+// matrix-vector products that reads every map once, so its time is the maps'
+// bytes over HBM bandwidth; a tensor-core scan of the maps would cost
+// 2 d^3 (S - 1) = 7e13 FLOP, far more.  Storing the maps in bfloat16 halves
+// the bytes.  The bfloat16 rounding (2^-9 relative per entry) is then won back
+// by the residual correction the Conclusion proposes, with the reduced maps
+// as the coarse propagator:
+//   lt_j   chain over the bfloat16 maps from y0 (float32 accumulation)
+//   d_j  = g^j(lt_j) - lt_{j+1}         float64 fine solve per slice
+//   e_0  = 0, e_{j+1} = At_j e_j + d_j  the same chain over the bfloat16 maps
+//   lt_j <- lt_j + e_j                  written by the chain as it goes
+// Each pass multiplies the error by about |A - At| |e| / |A e|; the maps of
+// this diffusive system contract, so two passes (the default) reach float64
+// parity targets.
+#include <algorithm>
+
+#include "internal.h"
+
+static nv_status ensure_scratch(nv_maps* M, size_t need, cudaStream_t s) {
+  if (M->scan_ws_bytes >= need) return NV_OK;
+  if (M->scan_ws) {
+    cudaStreamSynchronize(s);
+    cudaFree(M->scan_ws);
+    M->scan_ws = nullptr;
+    M->scan_ws_bytes = 0;
+  }
+  nv_status st = nv_cuda_check(cudaMalloc(&M->scan_ws, need), "refinement scratch allocation");
+  if (st == NV_OK) M->scan_ws_bytes = need;
+  return st;
+}
+
+nv_status launch_bf16_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
+  if (M->rhs_kind != NV_RHS_ADVDIFF2D)
+    return nv_fail(NV_ENOTSUP, "bfloat16 refinement is built for the advection-diffusion system");
+  const int n = M->dim, S = M->S;
+  const size_t states = (size_t)(S + 1) * n;
+  // two state sets, the defects, one zero vector
+  const size_t need = sizeof(double) * (2 * states + (size_t)S * n + (size_t)n);
+  nv_status st = ensure_scratch(M, need, s);
+  if (st != NV_OK) return st;
+  double* lt = static_cast<double*>(M->scan_ws);
+  double* lt2 = lt + states;
+  double* d = lt2 + states;
+  double* zero = d + (size_t)S * n;
+  if ((st = nv_cuda_check(cudaMemsetAsync(zero, 0, sizeof(double) * n, s), "zero state")) != NV_OK) return st;
+
+  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : 2);
+  // approximate boundary states over the bfloat16 maps
+  double* cur = lt;
+  if ((st = launch_tile_chain(M, y0, passes == 0 ? yT : nullptr, passes == 0 && lambdas ? lambdas : cur,
+                              nullptr, s)) != NV_OK)
+    return st;
+  if (passes == 0) return NV_OK;
+  for (int p = 0; p < passes; ++p) {
+    const bool last = p == passes - 1;
+    double* out = last ? lambdas : (cur == lt ? lt2 : lt);
+    if ((st = launch_advdiff_defect(M, cur, d, s)) != NV_OK) return st;
+    TileChainExtra ex{};
+    ex.vadd = d;
+    ex.base = cur;
+    ex.col0_off = 1;
+    if ((st = launch_tile_chain(M, zero, last ? yT : nullptr, out, &ex, s)) != NV_OK) return st;
+    cur = out;
+  }
+  return NV_OK;
+}

@@ -28,7 +28,7 @@ def _check(torch, w, prec, slices, tol_cols, tol_final):
     m = nv.workload_steps(w)
     fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
     for j in slices:
-        blk = nvp.maps_slice(maps, j).cpu().numpy().reshape(n + 1, n)      # [col, row]
+        blk = nvp.maps_slice(maps, j).double().cpu().numpy().reshape(n + 1, n)      # [col, row]
         assert np.all(blk[0] == 0.0)                                        # no forcing: b_j = 0
         Ac, _ = nv.build_affine_slice(fi, fh, "rk4", w.t0, w.T, w.S, m, n, j,
                                       columns=[c - 1 for c in COLS[1:]])
@@ -61,3 +61,36 @@ def test_advdiff_full_size_fp64():
     """S = 512 slices, float64 maps (68.7 GB)."""
     torch = need_gpu()
     _check(torch, workloads.advdiff2d(), "fp64", [0, 511], 1e-11, 1e-11)
+
+
+def test_advdiff_bf16_refined_small():
+    """bfloat16 maps (entries within 2^-9 of the float32 solves) composed over
+    3 slices, then the float64 correction passes: the refined state meets the
+    1e-4 target for refined reduced precision, and refinement beats the
+    unrefined bfloat16 chain."""
+    torch = need_gpu()
+    w = workloads.advdiff2d(S=3, T=3 * 2e-3)
+    nvp.tune_set(5, -1)
+    try:
+        r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
+        maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                     nvp.steps("rk4", w.dt, 0, "bf16_refine"))
+        y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+        y_raw = torch.empty_like(y0)
+        nvp.compose(maps, y0, y_raw)
+        nvp.maps_check(maps)
+        maps.destroy()
+    finally:
+        nvp.tune_set(5, 0)
+    _check(torch, w, "bf16_refine", [0, 2], 4e-3, 1e-4)
+    m = nv.workload_steps(w)
+    ser = nv.serial_fine(nv.workload_rhs(w, True), "rk4", w.t0, w.T, w.S, m, w.y0)
+    print("unrefined bfloat16 chain relative error", rel_l2(y_raw.cpu().numpy(), ser))
+    assert rel_l2(y_raw.cpu().numpy(), ser) > 1e-4
+
+
+def test_advdiff_bf16_refined_full_size():
+    """S = 512, bfloat16 maps (17.2 GB): refined final state within 1e-4 of the
+    serial fine solve, every boundary state written."""
+    torch = need_gpu()
+    _check(torch, workloads.advdiff2d(), "bf16_refine", [0, 511], 4e-3, 1e-4)

@@ -155,4 +155,6 @@ def test_square_paper_table_shapes_fp32(e, S, M):
                                                "euler", w.dt, 0, 1.0, "fp32")
     assert rel_max(tab, otab) <= 1e-5
     assert rel_l2(lam, olam) <= 1e-5
-    assert oob == ooob == 0
+    # the chords of this convex map lie above it, so with 4..7 nodes the last
+    # lookup already lands above y = 2 in both (oracle: lambda_{S-1} = 2.03 / 2.005)
+    assert oob == ooob == 1
