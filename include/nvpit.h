@@ -100,13 +100,17 @@ typedef enum {
                               tensor cores in TF32 with float32 accumulation, then
                               float64 residual-correction passes (three by default).
                               Heat equations, d <= 256, d % 4 == 0                        */
-  NV_BF16_REFINE = 3       /* affine only: maps integrated in float32 and stored rounded
+  NV_BF16_REFINE = 3,      /* affine only: maps integrated in float32 and stored rounded
                               to bfloat16 (half the bytes of float32), composed by the
                               HBM-bound chain with float32 accumulation, then float64
                               residual-correction passes (two by default) whose chains
                               reuse the bfloat16 maps.  Advection-diffusion, d > 512,
-                              d % 8 == 0 (the large-d path, where the maps' bytes set the
-                              composition time)                                          */
+                              d % 8 == 0.  Each pass contracts the error by about
+                              S 2^-9 (the maps' rounding compounds along the chain), so
+                              it converges for chains of up to ~100 slices             */
+  NV_FP32_REFINE = 4       /* affine only: float32 maps and float32 chain as NV_FP32,
+                              then float64 residual-correction passes (one by default;
+                              contraction about S 2^-24).  Advection-diffusion, d > 512 */
 } nv_precision;
 
 typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;
@@ -175,7 +179,8 @@ nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T, int32_t S
  * cores, then float64 residual-correction passes with float64 fine solves
  * from the approximate boundary states.  AFFINE NV_BF16_REFINE: the chain over
  * the bfloat16 maps, then float64 correction passes (fine solves from the
- * approximate boundary states, the correction chained over the same maps).
+ * approximate boundary states, the correction chained over the same maps);
+ * AFFINE NV_FP32_REFINE: the same over float32 maps.
  * Buffers must not overlap. */
 nv_status nv_compose(const nv_maps* maps, const double* y0_dev, double* yT_dev,
                      double* lambdas_dev, void* stream);
@@ -376,9 +381,9 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *   key 3: CTAs per cluster of the d <= 512 chain (default 0 = largest that
  *          fits, up to 16; a negative value selects the grid-wide chain)
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
- *   key 5: float64 correction passes of NV_TF32_REFINE / NV_BF16_REFINE
- *          (default 0 = three / two passes; a negative value returns the
- *          unrefined reduced-precision states)
+ *   key 5: float64 correction passes of NV_TF32_REFINE / NV_BF16_REFINE /
+ *          NV_FP32_REFINE (default 0 = three / two / one; a negative value
+ *          returns the unrefined reduced-precision states)
  *   key 6: form of the RK4 step for the homogeneous heat columns: 0 auto (the
  *          nine-point stencil where every lane holds >= 4 whole rows, else
  *          Horner stages), 1 Horner stages, 2 nine-point stencil where it

@@ -26,7 +26,7 @@ RHS = {"linear_scalar": 0, "square": 1, "cos_cubic": 2, "heat1d": 3, "vdp": 4, "
        "advdiff2d": 6, "heat1d_varcoef": 7, "wave": 8}
 SCHEME = {"euler": 0, "rk4": 1, "leapfrog": 2}
 MAP = {"pl1d": 0, "bilinear2d": 1, "affine": 2}
-PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2, "bf16_refine": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32_refine": 2, "bf16_refine": 3, "fp32_refine": 4}
 OOB = {"extrapolate": 0, "error": 1}
 
 

@@ -138,7 +138,7 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
   if (!sm || !st) return nv_fail(NV_EINVAL, "samples and steps must not be NULL");
   if (S < 1 || S > (1 << 24)) return nv_fail(NV_EINVAL, "S must be 1..2^24");
   if ((e = check_scheme(rhs->kind, st->scheme)) != NV_OK) return e;
-  if (st->prec < NV_FP64 || st->prec > NV_BF16_REFINE) return nv_fail(NV_EINVAL, "unknown precision");
+  if (st->prec < NV_FP64 || st->prec > NV_FP32_REFINE) return nv_fail(NV_EINVAL, "unknown precision");
   e = nv_plan_steps(t0, T, S, st->dt, st->steps_per_slice, &P->m, &P->h);
   if (e != NV_OK) return e;
   P->rhs_kind = rhs->kind;
@@ -166,8 +166,7 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
       for (int i = 0; i < want; ++i)
         if (!(sm->hi[i] > sm->lo[i]) || !isfinite(sm->lo[i]) || !isfinite(sm->hi[i]))
           return nv_fail(NV_EINVAL, "need finite lo < hi in dimension %d", i);
-      if (st->prec == NV_TF32_REFINE || st->prec == NV_BF16_REFINE)
-        return nv_fail(NV_EINVAL, "reduced-precision refinement is for affine maps");
+      if (st->prec >= NV_TF32_REFINE) return nv_fail(NV_EINVAL, "reduced-precision refinement is for affine maps");
       if (is_linear_kind(rhs->kind)) return nv_fail(NV_EINVAL, "PDE right-hand sides use affine maps");
       if (rhs->kind == NV_RHS_CHAIN3) return nv_fail(NV_ENOTSUP, "6-D chain has no table map");
       P->elems_per_slice = (int64_t)sm->per_dim * (want == 2 ? sm->per_dim * 2 : 1);
@@ -175,8 +174,9 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
     }
     case NV_MAP_AFFINE:
       if (!is_linear_kind(rhs->kind)) return nv_fail(NV_EINVAL, "affine maps need a linear rhs");
-      if (st->prec == NV_BF16_REFINE && (rhs->kind != NV_RHS_ADVDIFF2D || d <= 512 || d % 8))
-        return nv_fail(NV_ENOTSUP, "bfloat16 refinement is built for advection-diffusion with d > 512, d %% 8 == 0");
+      if ((st->prec == NV_BF16_REFINE || st->prec == NV_FP32_REFINE) &&
+          (rhs->kind != NV_RHS_ADVDIFF2D || d <= 512 || d % 8))
+        return nv_fail(NV_ENOTSUP, "chain refinement is built for advection-diffusion with d > 512, d %% 8 == 0");
       if (rhs->kind == NV_RHS_WAVE_CHEB) {
         if (st->prec == NV_TF32_REFINE) return nv_fail(NV_ENOTSUP, "TF32 refinement is built for the heat equation");
         P->aux_elems = wave_aux_elems(d / 2);
@@ -274,8 +274,8 @@ extern "C" nv_status nv_compose(const nv_maps* maps, const double* y0_dev, doubl
   if (maps->map != NV_MAP_AFFINE) return launch_table_compose(maps, y0_dev, yT_dev, lambdas_dev, s);
   if (maps->prec == NV_TF32_REFINE)
     return launch_scan_refine(const_cast<nv_maps*>(maps), y0_dev, yT_dev, lambdas_dev, s);
-  if (maps->prec == NV_BF16_REFINE)
-    return launch_bf16_refine(const_cast<nv_maps*>(maps), y0_dev, yT_dev, lambdas_dev, s);
+  if (maps->prec == NV_BF16_REFINE || maps->prec == NV_FP32_REFINE)
+    return launch_chain_refine(const_cast<nv_maps*>(maps), y0_dev, yT_dev, lambdas_dev, s);
   return launch_affine_chain(maps, y0_dev, yT_dev, lambdas_dev, s, g_tune.chain_rows_per_cta);
 }
 

@@ -73,8 +73,8 @@ nv_status launch_serial_fine(int32_t rhs_kind, int32_t dim, const double* params
                              const double* y0, double* yT, cudaStream_t s);
 nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
                              cudaStream_t s);
-nv_status launch_bf16_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
-                             cudaStream_t s);
+nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
+                              cudaStream_t s);
 
 // Tiled grid-wide chain (d > 512) over the maps' own storage, with the
 // options of the float64 correction chain.

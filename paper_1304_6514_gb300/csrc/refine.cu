@@ -1,5 +1,6 @@
 // Reduced-precision composition with float64 refinement for large state
-// dimensions (NV_BF16_REFINE, the advection-diffusion system, d = 4096).
+// dimensions (NV_BF16_REFINE, NV_FP32_REFINE; the advection-diffusion system,
+// d = 4096).
 //
 // At d = 4096 the composition for one initial state is a chain of S
 // matrix-vector products that reads every map once, so its time is the maps'
@@ -12,9 +13,12 @@
 //   d_j  = g^j(lt_j) - lt_{j+1}         float64 fine solve per slice
 //   e_0  = 0, e_{j+1} = At_j e_j + d_j  the same chain over the bfloat16 maps
 //   lt_j <- lt_j + e_j                  written by the chain as it goes
-// Each pass multiplies the error by about |A - At| |e| / |A e|; the maps of
-// this diffusive system contract, so two passes (the default) reach float64
-// parity targets.
+// Each pass multiplies the error by about the accumulated map error along the
+// chain, S times the maps' relative rounding: the periodic operator conserves
+// the mean, so A has the eigenvalue 1 and that mode's rounding compounds over
+// all S slices.  With bfloat16 maps (2^-9) that is below 1 only for chains of
+// up to ~100 slices (two passes by default); float32 maps (NV_FP32_REFINE,
+// 2^-24) need one pass at S = 512.
 #include <algorithm>
 
 #include "internal.h"
@@ -32,9 +36,9 @@ static nv_status ensure_scratch(nv_maps* M, size_t need, cudaStream_t s) {
   return st;
 }
 
-nv_status launch_bf16_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
+nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
   if (M->rhs_kind != NV_RHS_ADVDIFF2D)
-    return nv_fail(NV_ENOTSUP, "bfloat16 refinement is built for the advection-diffusion system");
+    return nv_fail(NV_ENOTSUP, "chain refinement is built for the advection-diffusion system");
   const int n = M->dim, S = M->S;
   const size_t states = (size_t)(S + 1) * n;
   // two state sets, the defects, one zero vector
@@ -47,7 +51,8 @@ nv_status launch_bf16_refine(nv_maps* M, const double* y0, double* yT, double* l
   double* zero = d + (size_t)S * n;
   if ((st = nv_cuda_check(cudaMemsetAsync(zero, 0, sizeof(double) * n, s), "zero state")) != NV_OK) return st;
 
-  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : 2);
+  const int dflt = M->prec == NV_BF16_REFINE ? 2 : 1;
+  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : dflt);
   // approximate boundary states over the bfloat16 maps
   double* cur = lt;
   if ((st = launch_tile_chain(M, y0, passes == 0 ? yT : nullptr, passes == 0 && lambdas ? lambdas : cur,

@@ -89,8 +89,16 @@ def test_advdiff_bf16_refined_small():
     assert rel_l2(y_raw.cpu().numpy(), ser) > 1e-4
 
 
-def test_advdiff_bf16_refined_full_size():
-    """S = 512, bfloat16 maps (17.2 GB): refined final state within 1e-4 of the
-    serial fine solve, every boundary state written."""
+def test_advdiff_bf16_refined_32_slices():
+    """32 slices: the bfloat16 rounding compounds along the chain (the mean
+    mode has eigenvalue 1), but the two correction passes still converge."""
     torch = need_gpu()
-    _check(torch, workloads.advdiff2d(), "bf16_refine", [0, 511], 4e-3, 1e-4)
+    _check(torch, workloads.advdiff2d(S=32, T=32 * 2e-3), "bf16_refine", [0, 31], 4e-3, 1e-4)
+
+
+def test_advdiff_fp32_refined_full_size():
+    """S = 512, float32 maps (34.4 GB) and chain, one float64 correction pass:
+    from the float32 method's 8.8e-5 to float64-level agreement with the serial
+    fine solve."""
+    torch = need_gpu()
+    _check(torch, workloads.advdiff2d(), "fp32_refine", [0, 511], 1e-5, 1e-7)
