@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -196,18 +197,38 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static nv_status alloc_maps(nv_maps* P) {
+// Map storage and workspace come from the device's stream-ordered pool on the
+// build stream.  Once per device the pool keeps up to 256 MB of freed memory
+// (instead of returning everything at each synchronisation), so a repeated
+// nv_solve of a small problem does not pay for fresh allocations; larger
+// maps still go back to the driver when freed.
+static nv_status pool_setup(int dev) {
+  static std::mutex mu;
+  static bool done[256] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 256 || done[dev]) return NV_OK;
+  cudaMemPool_t pool;
+  nv_status e = nv_cuda_check(cudaDeviceGetDefaultMemPool(&pool, dev), "default memory pool");
+  if (e != NV_OK) return e;
+  uint64_t keep = 256ull << 20;
+  e = nv_cuda_check(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "pool threshold");
+  if (e == NV_OK) done[dev] = true;
+  return e;
+}
+
+static nv_status alloc_maps(nv_maps* P, cudaStream_t s) {
   nv_status e = nv_cuda_check(cudaGetDevice(&P->device), "cudaGetDevice");
   if (e != NV_OK) return e;
-  e = nv_cuda_check(cudaMalloc(&P->data, (size_t)P->bytes), "map allocation");
+  if ((e = pool_setup(P->device)) != NV_OK) return e;
+  e = nv_cuda_check(cudaMallocAsync(&P->data, (size_t)P->bytes, s), "map allocation");
   if (e != NV_OK) { P->data = nullptr; return e; }
   const size_t xoff = 256;
   // 2 float64 chain vectors + a triple buffer of chain states (tiled chain) + slack
   const size_t coff = align256(xoff + sizeof(double) * 5 * (size_t)P->dim + 64);
   const size_t aoff = align256(coff + sizeof(double) * (size_t)(P->coef_per_slice * P->S));
   P->ws_bytes = aoff + sizeof(double) * (size_t)P->aux_elems;
-  e = nv_cuda_check(cudaMalloc(&P->ws, P->ws_bytes), "workspace allocation");
-  if (e != NV_OK) { cudaFree(P->data); P->data = nullptr; P->ws = nullptr; return e; }
+  e = nv_cuda_check(cudaMallocAsync(&P->ws, P->ws_bytes, s), "workspace allocation");
+  if (e != NV_OK) { cudaFreeAsync(P->data, s); P->data = nullptr; P->ws = nullptr; return e; }
   char* w = static_cast<char*>(P->ws);
   P->status = reinterpret_cast<int*>(w);
   P->oob = reinterpret_cast<unsigned long long*>(w + 8);
@@ -215,13 +236,15 @@ static nv_status alloc_maps(nv_maps* P) {
   P->xbuf = reinterpret_cast<double*>(w + xoff);
   P->coef = P->coef_per_slice ? reinterpret_cast<double*>(w + coff) : nullptr;
   P->aux = P->aux_elems ? reinterpret_cast<double*>(w + aoff) : nullptr;
-  return nv_cuda_check(cudaMemset(P->ws, 0, 256), "workspace reset");
+  return nv_cuda_check(cudaMemsetAsync(P->ws, 0, 256, s), "workspace reset");
 }
 
-static void free_maps(nv_maps* P) {
+// Frees in the order of stream s (the caller has ordered s after all work
+// on the maps).  The reduced-precision scratch is a plain allocation.
+static void free_maps(nv_maps* P, cudaStream_t s) {
   if (!P) return;
-  if (P->data) cudaFree(P->data);
-  if (P->ws) cudaFree(P->ws);
+  if (P->data) cudaFreeAsync(P->data, s);
+  if (P->ws) cudaFreeAsync(P->ws, s);
   if (P->scan_ws) cudaFree(P->scan_ws);
   delete P;
 }
@@ -248,8 +271,8 @@ extern "C" nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T
   } else {
     M = new (std::nothrow) nv_maps(P);
     if (!M) return nv_fail(NV_ENOMEM, "host allocation of the maps object");
-    e = alloc_maps(M);
-    if (e != NV_OK) { free_maps(M); return e; }
+    e = alloc_maps(M, static_cast<cudaStream_t>(stream));
+    if (e != NV_OK) { free_maps(M, static_cast<cudaStream_t>(stream)); return e; }
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (M->map == NV_MAP_AFFINE)
@@ -257,7 +280,7 @@ extern "C" nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T
   else
     e = launch_table_build(M, s, g_tune.table_block > 0 ? g_tune.table_block : 64);
   if (e != NV_OK) {
-    if (!*maps) free_maps(M);
+    if (!*maps) free_maps(M, s);
     return e;
   }
   *maps = M;
@@ -282,7 +305,7 @@ extern "C" nv_status nv_compose(const nv_maps* maps, const double* y0_dev, doubl
 extern "C" nv_status nv_maps_destroy(nv_maps* maps) {
   if (!maps) return NV_OK;
   cudaError_t ce = cudaDeviceSynchronize();
-  free_maps(maps);
+  free_maps(maps, 0);
   return nv_cuda_check(ce, "synchronise before destroy");
 }
 
@@ -292,13 +315,15 @@ extern "C" nv_status nv_solve(const nv_rhs* rhs, double t0, double T, int32_t S,
   nv_maps* M = nullptr;
   nv_status e = nv_build_propagators(rhs, t0, T, S, samples, steps, &M, stream);
   if (e != NV_OK) return e;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   e = nv_compose(M, y0_dev, yT_dev, nullptr, stream);
-  nv_status e2 = nv_cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)),
-                               "solve synchronise");
   int st = NV_OK;
-  if (e == NV_OK && e2 == NV_OK)
-    e2 = nv_cuda_check(cudaMemcpy(&st, M->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
-  free_maps(M);
+  nv_status e2 = NV_OK;
+  if (e == NV_OK)
+    e2 = nv_cuda_check(cudaMemcpyAsync(&st, M->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status read");
+  nv_status e3 = nv_cuda_check(cudaStreamSynchronize(s), "solve synchronise");
+  if (e2 == NV_OK) e2 = e3;
+  free_maps(M, s);
   if (e != NV_OK) return e;
   if (e2 != NV_OK) return e2;
   if (st != NV_OK) return nv_fail((nv_status)st, "device recorded status %d during solve", st);

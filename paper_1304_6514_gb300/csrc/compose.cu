@@ -458,10 +458,13 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
 template <typename MT, typename AT>
 __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
                                                                 AT* xb) {
-  // MT: double, float, or uint16_t holding bfloat16 bits (8 rows per load)
-  constexpr int VEC = 16 / (int)sizeof(MT);
+  // MT: double, float, or uint16_t holding bfloat16 bits.  Rows per thread:
+  // 2 (double), 4 (float, and bfloat16 as 8-byte loads: 8 rows per thread
+  // would halve the column blocks' row count and double the atomic adds per
+  // state row, which then dominate)
+  constexpr int VEC = sizeof(MT) == 2 ? 4 : 16 / (int)sizeof(MT);
   using V = typename std::conditional<sizeof(MT) == 4, float4,
-                                      typename std::conditional<sizeof(MT) == 8, double2, uint4>::type>::type;
+                                      typename std::conditional<sizeof(MT) == 8, double2, uint2>::type>::type;
   extern __shared__ __align__(16) unsigned char sxt_raw[];
   AT* sx = reinterpret_cast<AT*>(sxt_raw);   // the cpc state values of this column block
   __shared__ int flag;
@@ -492,10 +495,10 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
     if (active) {
       const MT* A = maps + (int64_t)k * slice_elems + row0;
       auto madd = [&](const V& t, AT xc) {
-        if constexpr (VEC == 8) {           // bfloat16: the high half of a float32
-          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+        if constexpr (sizeof(MT) == 2) {    // bfloat16: the high half of a float32
+          const uint32_t w[2] = {t.x, t.y};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < 2; ++i) {
             acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
             acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
           }
@@ -693,15 +696,15 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   return launch_chains(a, f64, s, want_csize);
 }
 
-// Tiled grid-wide chain (d > 512, d % 4 == 0; d % 8 == 0 for bfloat16 maps):
-// one CTA per SM, row blocks of 4096 (bfloat16) / 2048 (float32) / 1024
-// (float64) rows, column blocks sized to fill the grid.
+// Tiled grid-wide chain (d > 512, d % 4 == 0): one CTA per SM, row blocks of
+// 2048 (float32, bfloat16) / 1024 (float64) rows, column blocks sized to fill
+// the grid.
 template <typename MT, typename AT>
 static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                             const TileChainExtra* ex, cudaStream_t s) {
   const int n = M->dim;
   const int block = 512;
-  const int vec = 16 / (int)sizeof(MT);
+  const int vec = sizeof(MT) == 2 ? 4 : 16 / (int)sizeof(MT);
   const int RB = vec * block;
   const int nrb = (n + RB - 1) / RB;
   int dev = 0, sms = 0;

@@ -122,10 +122,12 @@ struct ChainArgs {
   int* status;
   unsigned long long* oob;
   int oob_error;
+  int64_t cached;   // > 0: the whole table (this many elements) is first copied to shared memory
 };
 
+// Table value at element i; p is a global or a shared-memory address.
 template <typename T>
-__device__ __forceinline__ double tload(const T* p, int64_t i) { return (double)__ldg(p + i); }
+__device__ __forceinline__ double tload(const T* p, int64_t i) { return (double)p[i]; }
 
 __device__ __forceinline__ int clamp_cell(double u, int cells) {
   // floor(u) clamped to [0, cells-1]; NaN maps to 0 (caught by the finite check)
@@ -135,10 +137,21 @@ __device__ __forceinline__ int clamp_cell(double u, int cells) {
   return (int)f;
 }
 
+// One thread walks the S dependent lookups.  When the table fits in shared
+// memory the CTA first copies it there, so each lookup waits on a shared load
+// instead of a round trip to L2 / HBM.
 template <typename T>
 __global__ void table_chain_kernel(ChainArgs a) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  extern __shared__ __align__(16) unsigned char tab_smem[];
+  if (blockIdx.x != 0) return;
   const T* tab = reinterpret_cast<const T*>(a.table);
+  if (a.cached > 0) {
+    T* st = reinterpret_cast<T*>(tab_smem);
+    for (int64_t i = threadIdx.x; i < a.cached; i += blockDim.x) st[i] = __ldg(tab + i);
+    __syncthreads();
+    tab = st;
+  }
+  if (threadIdx.x != 0) return;
   unsigned long long oob = 0;
   bool bad = false;
   if (a.dim == 1) {
@@ -299,10 +312,27 @@ nv_status launch_table_compose(const nv_maps* M, const double* y0, double* yT, d
   a.status = M->status;
   a.oob = M->oob;
   a.oob_error = M->oob_policy == NV_OOB_ERROR;
+  const int64_t elems = M->elems_per_slice * (int64_t)M->S;
+  const size_t bytes = (size_t)elems * (size_t)M->elem_bytes;
+  const size_t kCacheMax = 200 * 1024;
+  const void* fn = M->prec == NV_FP64 ? (const void*)table_chain_kernel<double>
+                                      : (const void*)table_chain_kernel<float>;
+  size_t smem = 0;
+  int threads = 32;
+  if (bytes <= kCacheMax) {
+    a.cached = elems;
+    smem = bytes;
+    threads = 1024;
+    if (smem > 48 * 1024) {
+      nv_status st = nv_cuda_check(
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "table smem attribute");
+      if (st != NV_OK) return st;
+    }
+  }
   if (M->prec == NV_FP64)
-    table_chain_kernel<double><<<1, 32, 0, s>>>(a);
+    table_chain_kernel<double><<<1, threads, smem, s>>>(a);
   else
-    table_chain_kernel<float><<<1, 32, 0, s>>>(a);
+    table_chain_kernel<float><<<1, threads, smem, s>>>(a);
   return nv_cuda_check(cudaGetLastError(), "table_chain_kernel launch");
 }
 
