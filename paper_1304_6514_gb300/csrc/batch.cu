@@ -117,6 +117,7 @@ struct BatchComposeArgs {
   const void* tables;
   int B, dim, per_dim;
   double lo0, lo1, hi0, hi1, d0, d1;
+  double r0, r1;   // 1 / d0, 1 / d1 (a division is a long dependent FP64 sequence)
   const double* y0;
   double* yT;
   int* status;
@@ -143,8 +144,8 @@ __global__ void batch_compose_kernel(BatchComposeArgs a) {
     const int M = a.per_dim;
     double lam = a.y0[i];
     for (int j = 0; j < d.S; ++j) {
-      const int s = batch_cell((lam - a.lo0) / a.d0, M - 1);
-      const double w = (lam - __dadd_rn(a.lo0, __dmul_rn((double)s, a.d0))) / a.d0;
+      const int s = batch_cell((lam - a.lo0) * a.r0, M - 1);
+      const double w = (lam - __dadd_rn(a.lo0, __dmul_rn((double)s, a.d0))) * a.r0;
       oob += (lam < a.lo0 || lam > a.hi0);
       const int64_t b = (int64_t)j * M + s;
       lam = (1.0 - w) * (double)__ldg(tab + b) + w * (double)__ldg(tab + b + 1);
@@ -155,10 +156,10 @@ __global__ void batch_compose_kernel(BatchComposeArgs a) {
     const int P = a.per_dim;
     double x = a.y0[2 * i], y = a.y0[2 * i + 1];
     for (int j = 0; j < d.S; ++j) {
-      const int p = batch_cell((x - a.lo0) / a.d0, P - 1);
-      const int q = batch_cell((y - a.lo1) / a.d1, P - 1);
-      const double wx = (x - __dadd_rn(a.lo0, __dmul_rn((double)p, a.d0))) / a.d0;
-      const double wy = (y - __dadd_rn(a.lo1, __dmul_rn((double)q, a.d1))) / a.d1;
+      const int p = batch_cell((x - a.lo0) * a.r0, P - 1);
+      const int q = batch_cell((y - a.lo1) * a.r1, P - 1);
+      const double wx = (x - __dadd_rn(a.lo0, __dmul_rn((double)p, a.d0))) * a.r0;
+      const double wy = (y - __dadd_rn(a.lo1, __dmul_rn((double)q, a.d1))) * a.r1;
       oob += !(x >= a.lo0 && x <= a.hi0 && y >= a.lo1 && y <= a.hi1);
       const int64_t b00 = (((int64_t)j * P + q) * P + p) * 2;
       const int64_t b10 = b00 + 2, b01 = b00 + 2 * (int64_t)P, b11 = b01 + 2;
@@ -284,6 +285,8 @@ static nv_status launch_batch_compose(const nv_batch* b, const double* y0, doubl
   a.hi1 = b->hi[1];
   a.d0 = (b->hi[0] - b->lo[0]) / (b->per_dim - 1);
   a.d1 = (b->hi[1] - b->lo[1]) / (b->per_dim - 1);
+  a.r0 = 1.0 / a.d0;
+  a.r1 = a.d1 != 0.0 ? 1.0 / a.d1 : 0.0;
   a.y0 = y0;
   a.yT = yT;
   a.status = b->status;

@@ -116,6 +116,8 @@ struct ChainArgs {
   const void* table;
   int S, per_dim, dim;
   double lo0, lo1, hi0, hi1, d0, d1;
+  double r0, r1;    // 1 / d0, 1 / d1: the single thread's chain multiplies instead of
+                    // dividing (an FP64 division is a long dependent sequence here)
   const double* y0;
   double* yT;
   double* lambdas;
@@ -159,8 +161,8 @@ __global__ void table_chain_kernel(ChainArgs a) {
     double lam = a.y0[0];
     if (a.lambdas) a.lambdas[0] = lam;
     for (int j = 0; j < a.S; ++j) {
-      const int s = clamp_cell((lam - a.lo0) / a.d0, M - 1);
-      const double w = (lam - __dadd_rn(a.lo0, __dmul_rn((double)s, a.d0))) / a.d0;
+      const int s = clamp_cell((lam - a.lo0) * a.r0, M - 1);
+      const double w = (lam - __dadd_rn(a.lo0, __dmul_rn((double)s, a.d0))) * a.r0;
       oob += (lam < a.lo0 || lam > a.hi0);
       const int64_t base = (int64_t)j * M + s;
       lam = (1.0 - w) * tload(tab, base) + w * tload(tab, base + 1);
@@ -173,10 +175,10 @@ __global__ void table_chain_kernel(ChainArgs a) {
     double x = a.y0[0], y = a.y0[1];
     if (a.lambdas) { a.lambdas[0] = x; a.lambdas[1] = y; }
     for (int j = 0; j < a.S; ++j) {
-      const int p = clamp_cell((x - a.lo0) / a.d0, P - 1);
-      const int q = clamp_cell((y - a.lo1) / a.d1, P - 1);
-      const double wx = (x - __dadd_rn(a.lo0, __dmul_rn((double)p, a.d0))) / a.d0;
-      const double wy = (y - __dadd_rn(a.lo1, __dmul_rn((double)q, a.d1))) / a.d1;
+      const int p = clamp_cell((x - a.lo0) * a.r0, P - 1);
+      const int q = clamp_cell((y - a.lo1) * a.r1, P - 1);
+      const double wx = (x - __dadd_rn(a.lo0, __dmul_rn((double)p, a.d0))) * a.r0;
+      const double wy = (y - __dadd_rn(a.lo1, __dmul_rn((double)q, a.d1))) * a.r1;
       oob += !(x >= a.lo0 && x <= a.hi0 && y >= a.lo1 && y <= a.hi1);
       const int64_t b00 = (((int64_t)j * P + q) * P + p) * 2;
       const int64_t b10 = b00 + 2;                 // (p+1, q)
@@ -306,6 +308,8 @@ nv_status launch_table_compose(const nv_maps* M, const double* y0, double* yT, d
   a.hi1 = M->hi[1];
   a.d0 = (M->hi[0] - M->lo[0]) / (M->per_dim - 1);
   a.d1 = (M->hi[1] - M->lo[1]) / (M->per_dim - 1);
+  a.r0 = 1.0 / a.d0;
+  a.r1 = a.d1 != 0.0 ? 1.0 / a.d1 : 0.0;
   a.y0 = y0;
   a.yT = yT;
   a.lambdas = lambdas;
