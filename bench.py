@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nvpit", choices=["nvpit", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="fp32,tf32_refine")
+    ap.add_argument("--variants", default="fp32,tf32_refine,fp32_refine")
     ap.add_argument("--slices", type=int, default=0, help="override S (profiling a reduced case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")

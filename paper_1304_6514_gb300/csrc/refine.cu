@@ -36,9 +36,52 @@ static nv_status ensure_scratch(nv_maps* M, size_t need, cudaStream_t s) {
   return st;
 }
 
+// The heat equations (d <= 512): the same passes with the cluster chain
+// (compose.cu), whose options carry d_j (v), the approximate states (add) and
+// every state written; the defects come from the heat float64 defect kernel.
+static nv_status heat_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
+                                   double* lt, double* lt2, double* d, int passes, cudaStream_t s) {
+  const int n = M->dim, S = M->S;
+  const float* maps = static_cast<const float*>(M->data);
+  ChainsArgs c{};
+  c.n = n;
+  c.nchains = 1;
+  c.len = S;
+  c.S = S;
+  c.A = maps + n;                        // columns 1..d of each slice
+  c.a_stride = (int64_t)n * (n + 1);
+  c.status = M->status;
+  c.write_state0 = 1;
+  ChainsArgs approx = c;                 // lt: the chain over the float32 maps from y0
+  approx.v = maps;                       // column 0, b_j
+  approx.v_stride = (int64_t)n * (n + 1);
+  approx.x0 = y0;
+  approx.states = passes == 0 ? lambdas : lt;
+  approx.yT = passes == 0 ? yT : nullptr;
+  nv_status st = launch_chains(approx, false, s, 16);
+  if (st != NV_OK || passes == 0) return st;
+  double* cur = lt;
+  for (int p = 0; p < passes; ++p) {
+    const bool last = p == passes - 1;
+    double* out = last ? lambdas : (cur == lt ? lt2 : lt);
+    if ((st = launch_heat_defect(M, cur, d, s)) != NV_OK) return st;
+    ChainsArgs corr = c;                 // e_{j+1} = At_j e_j + d_j from e_0 = 0, written as cur + e
+    corr.v = d;
+    corr.v_double = 1;
+    corr.v_stride = n;
+    corr.add = cur;
+    corr.states = out;
+    corr.yT = last ? yT : nullptr;
+    if ((st = launch_chains(corr, false, s, 16)) != NV_OK) return st;
+    cur = out;
+  }
+  return NV_OK;
+}
+
 nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
-  if (M->rhs_kind != NV_RHS_ADVDIFF2D)
-    return nv_fail(NV_ENOTSUP, "chain refinement is built for the advection-diffusion system");
+  const bool heat = M->rhs_kind == NV_RHS_HEAT1D || M->rhs_kind == NV_RHS_HEAT1D_VARCOEF;
+  if (M->rhs_kind != NV_RHS_ADVDIFF2D && !heat)
+    return nv_fail(NV_ENOTSUP, "chain refinement is built for the heat equations and advection-diffusion");
   const int n = M->dim, S = M->S;
   const size_t states = (size_t)(S + 1) * n;
   // two state sets, the defects, one zero vector
@@ -53,6 +96,7 @@ nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* 
 
   const int dflt = M->prec == NV_BF16_REFINE ? 2 : 1;
   const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : dflt);
+  if (heat) return heat_chain_refine(M, y0, yT, lambdas, lt, lt2, d, passes, s);
   // approximate boundary states over the bfloat16 maps
   double* cur = lt;
   if ((st = launch_tile_chain(M, y0, passes == 0 ? yT : nullptr, passes == 0 && lambdas ? lambdas : cur,

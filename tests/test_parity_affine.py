@@ -115,7 +115,8 @@ def _full_oracle():
     return _FULL
 
 
-@pytest.mark.parametrize("prec,tol,final_tol", [("fp64", 1e-11, 1e-11), ("fp32", 1e-5, 2e-4)])
+@pytest.mark.parametrize("prec,tol,final_tol", [("fp64", 1e-11, 1e-11), ("fp32", 1e-5, 2e-4),
+                                                ("fp32_refine", 1e-5, 1e-7)])
 def test_heat_full_size(prec, tol, final_tol):
     """n=256, S=1024 slices, RK4 with m=10: three whole slice maps element by
     element, and the composed final state against the serial fine solve.
@@ -124,7 +125,10 @@ def test_heat_full_size(prec, tol, final_tol):
     are bitwise identical, so their float32 rounding composes coherently:
     rounding the exact maps to float32 alone gives 1.0e-5, computing them in
     float32 ~5e-5 to 9e-5 (bound S * m * u32 * O(1) ~ 6e-4).  The bound here is
-    2e-4; the refined tensor-core path is the one held to the method's target."""
+    2e-4; the refined paths are the ones held to the method's target.  With one
+    float64 correction pass (fp32_refine: defects from the float32 boundary
+    states, the correction chained over the same float32 maps) the error
+    contracts by about S times the maps' float32 rounding: bound 1e-7."""
     torch = need_gpu()
     o = _full_oracle()
     w = o["w"]
@@ -132,8 +136,25 @@ def test_heat_full_size(prec, tol, final_tol):
     for j, (oA, ob) in o["slices"].items():
         assert rel_max(A[j], oA) <= tol, j
         assert rel_max(b[j], ob) <= tol, j
+    print(prec, "final state relative error", rel_l2(yT, o["serial"]))
     assert rel_l2(yT, o["serial"]) <= final_tol
     assert rel_l2(lam[-1], yT) == 0.0
+
+
+@pytest.mark.parametrize("n,S", [(40, 7), (256, 9), (100, 5)])
+def test_heat_fp32_refined_small(n, S):
+    """float32 maps + one float64 correction pass, every boundary state: the
+    cluster chain (d = 256), and the fallback cluster chain (d = 40, 100)."""
+    torch = need_gpu()
+    dt = 2.0 / (4.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=S * 3 * dt, dt=dt)
+    _, A, b, yT, lam = _heat(torch, w, "fp32_refine")
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    assert rel_max(A, oA) <= 1e-5
+    olam = nv.compose_affine(oA, ob, w.y0)
+    assert rel_l2(lam, olam) <= 1e-9
 
 
 def test_heat_serial_fine_gpu():
