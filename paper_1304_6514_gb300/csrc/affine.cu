@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvA
       for (int r = 0; r < kAdvB; ++r)
 #pragma unroll
         for (int q = 0; q < kAdvB; ++q) v[r][q] = y[r][q];
-#pragma unroll 1
+#pragma unroll
       for (int kk = 4; kk >= 1; --kk) {
         const float* cw = a.cw32[4 - kk];
         const float cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
