@@ -298,13 +298,13 @@ def gpu_peak_probe(torch):
 # dominant kernel, scaled to the bench's launch by the units it writes (the
 # captures ran smaller cases of the same kernels; see profiles/):
 #   heat FP64 build (nine-point form), S = 512 capture: 206.55 MB for 131 072 columns
-#   advection-diffusion FP32 build, S = 8 capture: 476.02 MB for 32 776 columns
+#   advection-diffusion FP32 build, S = 8 capture: 475.04 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 502.0 MB for 561 987 584 table bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 NCU_TRAFFIC_PER_UNIT = {
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
     "heat_poly9_kernel<double,8,0>": (206.55e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
-    "advdiff_block_kernel": (476.02e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
+    "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (502.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
 }
 

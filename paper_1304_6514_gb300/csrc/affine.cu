@@ -416,14 +416,17 @@ __global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const doub
 
 // ---------------------------------------------------------------------------
 // Periodic 2-D advection-diffusion on an nx x nx grid (nx = 64, d = 4096):
-// L u = nu lap5(u) - ax D-x u - ay D-y u.  One CTA of 256 threads integrates
-// one basis column.  Thread t holds the strip iy = 16*(t/64) .. +15 at
+// L u = nu lap5(u) - ax D-x u - ay D-y u.  Float64 (the build, the serial
+// solve, the correction defects): one CTA of 256 threads integrates one state
+// (a basis column).  Thread t holds the strip iy = 16*(t/64) .. +15 at
 // ix = t % 64 in registers: its y-neighbours are in the same thread except at
 // the strip ends, its x-neighbours in lanes +-1 (warp shuffles) except at the
 // warp's edge lanes; strip-end rows and edge-lane strips cross through
 // double-buffered shared memory, one __syncthreads per stage.  RK4 runs in
 // Horner form (time-invariant operator), the stage factor h/k folded into the
-// five stencil weights.
+// five stencil weights.  The float32 build uses 8 x 8 blocks instead
+// (advdiff_block_kernel below), where the FP32 pipe, not the FP64 one, is the
+// limit and the strip layout's shuffles would be.
 constexpr int kAdvNx = 64;
 constexpr int kAdvRows = 16;     // rows per thread strip
 
@@ -469,7 +472,7 @@ __device__ __forceinline__ void adv_strip_integrate(const AdvArgs& a, T* y, AdvS
   for (int64_t i = 0; i < a.m; ++i) {
 #pragma unroll
     for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
-#pragma unroll 1
+#pragma unroll
     for (int kk = 4; kk >= 1; --kk) {
       const T* cw = adv_weights<T>(a, 4 - kk);
       const T cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];

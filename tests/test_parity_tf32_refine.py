@@ -1,6 +1,6 @@
 """GPU parity of the refined tensor-core composition (NV_TF32_REFINE):
 float32 maps, block totals as tcgen05 TF32 products, batched cluster chains,
-then one float64 residual-correction pass.  Target after refinement: relative
+then float64 residual-correction passes (three by default).  Target after refinement: relative
 L2 error of the boundary states <= 1e-4 against the FP64 oracle."""
 import numpy as np
 import pytest
