@@ -394,8 +394,10 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          CTA then gives up at its first bounded wait (~0.4 s), records NV_ETIMEOUT
  *          in the maps' status word (read by nv_maps_check) and returns; the
  *          context stays usable.  The paper has no counterpart.
+ *   key 8: split-K of the learned propagator's weight-gradient GEMMs (K = the
+ *          batch): 0 auto, or 1, 2, 4, 8, 16
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6 and 7. */
+ * or an out-of-range value of keys 6, 7 and 8. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

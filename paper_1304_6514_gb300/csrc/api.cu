@@ -19,7 +19,7 @@ nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, 
 nv_status launch_serial_wave(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 int64_t wave_aux_elems(int d);
 
-nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0};
+nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
 static thread_local char g_err[512] = "";
 
@@ -433,6 +433,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 7:
       if (value < 0 || value > 4) return nv_fail(NV_EINVAL, "phantom barrier participants are 0..4");
       g_tune.test_barrier_extra = value;
+      break;
+    case 8:
+      if (value < 0 || value > 16 || (value & (value - 1))) return nv_fail(NV_EINVAL, "split-K is 0 (auto) or 1, 2, 4, 8, 16");
+      g_tune.mlp_wgrad_splits = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }

@@ -120,5 +120,6 @@ struct nv_tunables {
   int refine_passes;       // float64 correction passes of NV_TF32_REFINE (0 = 1, < 0 none)
   int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil
   int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
+  int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
 };
 extern nv_tunables g_tune;

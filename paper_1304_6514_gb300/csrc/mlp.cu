@@ -196,21 +196,51 @@ __global__ void l4_kernel(const float* P, const __nv_bfloat16* H3, const float* 
   }
 }
 
-// dW4 = dOut^T H3, db4 = column sums of dOut (thread per (output, unit))
+// Sum over the CTA of NV per-thread values (blockDim.x a multiple of 32, at
+// most 1024); the totals land in out[0..NV) of thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sums(float* v, float* out) {
+  __shared__ float red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[warp][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      float t = 0.f;
+      for (int w = 0; w < nw; ++w) t += red[w][q];
+      out[q] = t;
+    }
+}
+
+// dW4 = dOut^T H3 and db4 = column sums of dOut.  CTA k < H reduces unit k's
+// six products over the batch (H3t row k is contiguous in the batch index);
+// CTA H reduces the six bias sums.
 __global__ void l4_wgrad_kernel(const float* dOut, const __nv_bfloat16* H3t, int B, float* G) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= D * H + D) return;
-  if (i < D * H) {
-    const int c = i / H, k = i % H;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s = fmaf(dOut[b * OUT + c], __bfloat162float(H3t[(int64_t)k * B + b]), s);
-    G[oW4 + c * H + k] += s;
+  const int k = blockIdx.x;
+  float v[D], t[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) v[c] = 0.f;
+  if (k < H) {
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+      const float hk = __bfloat162float(H3t[(int64_t)k * B + b]);
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[c] = fmaf(dOut[b * OUT + c], hk, v[c]);
+    }
   } else {
-    const int c = i - D * H;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dOut[b * OUT + c];
-    G[ob4 + c] += s;
+    for (int b = threadIdx.x; b < B; b += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[c] += dOut[b * OUT + c];
   }
+  block_sums<D>(v, t);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < D; ++c) G[k < H ? oW4 + c * H + k : ob4 + c] += t[c];
 }
 
 // column sums of a transposed bf16 matrix (rows n, B columns) into G[off + n]
@@ -228,14 +258,21 @@ __global__ void colsum_kernel(const __nv_bfloat16* Mt, int B, float* G, int64_t 
   if (threadIdx.x == 0) G[off + n] += red[0];
 }
 
-// dW1 = dZ1^T X (thread per (unit, input))
+// dW1 = dZ1^T X: CTA n reduces unit n's seven products over the batch.
 __global__ void l1_wgrad_kernel(const __nv_bfloat16* dZ1t, const float* X, int B, float* G) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= H * 7) return;
-  const int n = i / 7, k = i % 7;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b) s = fmaf(__bfloat162float(dZ1t[(int64_t)n * B + b]), X[b * IN + k], s);
-  G[oW1 + n * IN + k] += s;
+  const int n = blockIdx.x;
+  float v[7], t[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) v[k] = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const float g = __bfloat162float(dZ1t[(int64_t)n * B + b]);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = fmaf(g, X[b * IN + k], v[k]);
+  }
+  block_sums<7>(v, t);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) G[oW1 + n * IN + k] += t[k];
 }
 
 __global__ void adam_kernel(float* P, float* G, float* Mm, float* Vv, int* step, float lr) {
@@ -383,10 +420,11 @@ static nv_status mlp_fwd_bwd(nv_mlp* m, int train, cudaStream_t s) {
                                                              m->dZ3t, m->loss, train);
   if ((st = nv_cuda_check(cudaGetLastError(), "l4")) != NV_OK) return st;
   if (!train) return NV_OK;
-  l4_wgrad_kernel<<<(D * H + D + 255) / 256, 256, 0, s>>>(m->dOut, m->H3t, B, m->G);
+  l4_wgrad_kernel<<<H + 1, 256, 0, s>>>(m->dOut, m->H3t, B, m->G);
   colsum_kernel<<<H, 256, 0, s>>>(m->dZ3t, B, m->G, ob3);
   if ((st = nv_cuda_check(cudaGetLastError(), "l4 weight gradients")) != NV_OK) return st;
-  const int splits = std::max(1, std::min(16, B / 256));
+  const int splits = g_tune.mlp_wgrad_splits > 0 ? std::min(g_tune.mlp_wgrad_splits, std::max(1, B / 64))
+                                                 : std::max(1, std::min(16, B / 256));
   // dW3 = dZ3^T H2, dH2 = dZ3 W3 -> dZ2 (db2 in the epilogue)
   if ((st = launch_gemm_bf16(m->dZ3t, m->H2t, H, B, splits, kModeAtomic, m->G + oW3, nullptr, nullptr, nullptr,
                              nullptr, nullptr, nullptr, m->status, s)) != NV_OK)
@@ -401,7 +439,7 @@ static nv_status mlp_fwd_bwd(nv_mlp* m, int train, cudaStream_t s) {
   if ((st = launch_gemm_bf16(m->dZ2, m->W2t, B, H, 1, kModeBwd, nullptr, nullptr, nullptr, m->Z1, m->dZ1, m->dZ1t,
                              m->G + ob1, m->status, s)) != NV_OK)
     return st;
-  l1_wgrad_kernel<<<(H * 7 + 255) / 256, 256, 0, s>>>(m->dZ1t, m->X, B, m->G);
+  l1_wgrad_kernel<<<H, 256, 0, s>>>(m->dZ1t, m->X, B, m->G);
   return nv_cuda_check(cudaGetLastError(), "l1 weight gradients");
 }
 

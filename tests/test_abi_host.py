@@ -105,6 +105,8 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(6, 3) == nvp.NV_EINVAL           # heat step form is 0..2
     assert lib.nv_tune_set(7, 5) == nvp.NV_EINVAL           # phantom barrier participants 0..4
     assert lib.nv_tune_set(7, -1) == nvp.NV_EINVAL
+    assert lib.nv_tune_set(8, 3) == nvp.NV_EINVAL           # split-K is 0 or a power of two <= 16
+    assert lib.nv_tune_set(8, 32) == nvp.NV_EINVAL
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
     h = ctypes.c_void_p()
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL
