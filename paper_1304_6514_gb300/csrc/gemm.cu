@@ -131,37 +131,66 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (!abort_flag) {
     fence_after();
+    // After the last MMA has completed (done) the stage memory is free: each
+    // warp transposes its 32 x 32 chunks there, so that row-major traffic
+    // (float32 results, saved pre-activations, bf16 row-major copies, the
+    // split-K accumulation) moves as 128-byte rows across the lanes instead of
+    // one 1 KB-strided row per lane.  Tile t: 32 x 33 floats per warp.
+    float* t = reinterpret_cast<float*>(base) + warp * 32 * 33;
     const int m = warp * 32 + lane;
     const int row = m0 + m;
+    const int wrow0 = m0 + warp * 32;                  // first row of this warp
+    const int nrows = max(0, min(32, a.M - wrow0));
     for (int c0 = 0; c0 < kBN; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row >= a.M) continue;
       if (a.mode == kAtomic) {
-        float* o = a.out32 + (int64_t)row * kBN + c0;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) atomicAdd(o + i, v[i]);
+        for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+        __syncwarp();
+        for (int r = 0; r < nrows; ++r) atomicAdd(a.out32 + (int64_t)(wrow0 + r) * kBN + c0 + lane, t[r * 33 + lane]);
+        __syncwarp();
       } else if (a.mode == kFwdTrain || a.mode == kFwdInfer) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float z = v[i] + a.bias[c0 + i];
-          if (a.mode == kFwdTrain) a.zsave[(int64_t)row * kBN + c0 + i] = z;
           const __nv_bfloat16 hb = __float2bfloat16(gelu_f(z));
-          a.out_bf[(int64_t)row * kBN + c0 + i] = hb;
-          if (a.mode == kFwdTrain) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
+          if (a.mode == kFwdTrain && row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
+          v[i] = z;
+          t[lane * 33 + i] = __bfloat162float(hb);      // exact: hb is a bf16 value
         }
-      } else {   // kBwd
+        __syncwarp();
+        for (int r = 0; r < nrows; ++r)
+          a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+        __syncwarp();
+        if (a.mode == kFwdTrain) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+          __syncwarp();
+          for (int r = 0; r < nrows; ++r) a.zsave[(int64_t)(wrow0 + r) * kBN + c0 + lane] = t[r * 33 + lane];
+          __syncwarp();
+        }
+      } else {   // kBwd: zin arrives by rows, dz leaves by rows and transposed
+        for (int r = 0; r < nrows; ++r) t[r * 33 + lane] = a.zin[(int64_t)(wrow0 + r) * kBN + c0 + lane];
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float dz = v[i] * gelu_grad_f(a.zin[(int64_t)row * kBN + c0 + i]);
+          const float dz = row < a.M ? v[i] * gelu_grad_f(t[lane * 33 + i]) : 0.f;
           const __nv_bfloat16 db = __float2bfloat16(dz);
-          a.out_bf[(int64_t)row * kBN + c0 + i] = db;
-          a.out_bfT[(int64_t)(c0 + i) * a.M + row] = db;
+          if (row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = db;
+          v[i] = __bfloat162float(db);
           float s = dz;
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
           if (lane == 0) atomicAdd(a.dbias + c0 + i, s);
         }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+        __syncwarp();
+        for (int r = 0; r < nrows; ++r)
+          a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+        __syncwarp();
       }
     }
   }
