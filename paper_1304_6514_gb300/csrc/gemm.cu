@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
         __syncwarp();
-        for (int r = 0; r < nrows; ++r) atomicAdd(a.out32 + (int64_t)(wrow0 + r) * kBN + c0 + lane, t[r * 33 + lane]);
+        #pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < nrows) atomicAdd(a.out32 + (int64_t)(wrow0 + r) * kBN + c0 + lane, t[r * 33 + lane]);
         __syncwarp();
       } else if (a.mode == kFwdTrain || a.mode == kFwdInfer) {
 #pragma unroll
@@ -160,18 +162,24 @@ __global__ void __launch_bounds__(128, 1)
           t[lane * 33 + i] = __bfloat162float(hb);      // exact: hb is a bf16 value
         }
         __syncwarp();
-        for (int r = 0; r < nrows; ++r)
-          a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
         __syncwarp();
         if (a.mode == kFwdTrain) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
           __syncwarp();
-          for (int r = 0; r < nrows; ++r) a.zsave[(int64_t)(wrow0 + r) * kBN + c0 + lane] = t[r * 33 + lane];
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            if (r < nrows) a.zsave[(int64_t)(wrow0 + r) * kBN + c0 + lane] = t[r * 33 + lane];
           __syncwarp();
         }
       } else {   // kBwd: zin arrives by rows, dz leaves by rows and transposed
-        for (int r = 0; r < nrows; ++r) t[r * 33 + lane] = a.zin[(int64_t)(wrow0 + r) * kBN + c0 + lane];
+        // all 32 loads in flight together (a rolled loop would wait on each)
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < nrows) t[r * 33 + lane] = a.zin[(int64_t)(wrow0 + r) * kBN + c0 + lane];
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
@@ -188,8 +196,9 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
         __syncwarp();
-        for (int r = 0; r < nrows; ++r)
-          a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+          if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
         __syncwarp();
       }
     }
