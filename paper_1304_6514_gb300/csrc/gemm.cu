@@ -5,17 +5,19 @@
 // One CTA computes a 128 x 256 tile.  Thread 0 streams K-slabs of 64 bf16
 // (128 B) of A (128 rows) and B (256 rows) with TMA (SWIZZLE_128B) through a
 // four-stage mbarrier ring and issues tcgen05.mma (kind::f16, M=128, N=256,
-// K=16); the four warps then read the accumulator back with tcgen05.ld, one
-// accumulator row per thread.  Split-K: blockIdx.y takes one K range and the
+// K=16); eight warps then read the accumulator back with tcgen05.ld, one
+// accumulator row per thread (warps w and w+4 share the TMEM lane quarter
+// w % 4 and take 128 columns each).  Split-K: blockIdx.y takes one K range and the
 // epilogue accumulates with atomics.  Every wait is bounded (1 s); on timeout
 // the kernel records NV_ETIMEOUT, waits (bounded) for its copies in flight,
 // frees its tensor memory and returns.
 //
 // Epilogues (z = D + bias):
 //   kAtomic   out32[m, n] += D                     (weight gradients, split-K)
-//   kFwdTrain z saved (fp32), h = GELU(z) stored bf16 row-major and transposed
-//   kBwd      dz = D * GELU'(zin) stored bf16 row-major and transposed,
-//             column sums of dz added to dbias
+//   kFwdTrain GELU'(z) saved (fp32, for the backward pass), h = GELU(z) stored
+//             bf16 row-major and transposed (one erf serves both)
+//   kBwd      dz = D * zin (zin = the saved GELU') stored bf16 row-major and
+//             transposed, column sums of dz added to dbias
 //   kFwdInfer h = GELU(z) stored bf16 row-major
 #include <cuda_bf16.h>
 
@@ -48,11 +50,16 @@ struct Args {
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+// GELU(z) = z Phi(z) and GELU'(z) = Phi(z) + z phi(z), sharing Phi's erf
+__device__ __forceinline__ float gelu_with_grad(float z, float* grad) {
+  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+  *grad = cdf + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return z * cdf;
 }
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args a) {
   using namespace tc;
   extern __shared__ unsigned char smem_raw[];
@@ -137,13 +144,14 @@ __global__ void __launch_bounds__(128, 1)
     // split-K accumulation) moves as 128-byte rows across the lanes instead of
     // one 1 KB-strided row per lane.  Tile t: 32 x 33 floats per warp.
     float* t = reinterpret_cast<float*>(base) + warp * 32 * 33;
-    const int m = warp * 32 + lane;
+    const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32q .. 32q+31, columns 128h ..
+    const int m = quarter * 32 + lane;
     const int row = m0 + m;
-    const int wrow0 = m0 + warp * 32;                  // first row of this warp
+    const int wrow0 = m0 + quarter * 32;               // first row of this warp
     const int nrows = max(0, min(32, a.M - wrow0));
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
+    for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 32) {
       float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
       if (a.mode == kAtomic) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
@@ -156,9 +164,11 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float z = v[i] + a.bias[c0 + i];
-          const __nv_bfloat16 hb = __float2bfloat16(gelu_f(z));
+          float gp = 0.f;
+          const float h = a.mode == kFwdTrain ? gelu_with_grad(z, &gp) : gelu_f(z);
+          const __nv_bfloat16 hb = __float2bfloat16(h);
           if (a.mode == kFwdTrain && row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
-          v[i] = z;
+          v[i] = gp;
           t[lane * 33 + i] = __bfloat162float(hb);      // exact: hb is a bf16 value
         }
         __syncwarp();
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(128, 1)
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float dz = row < a.M ? v[i] * gelu_grad_f(t[lane * 33 + i]) : 0.f;
+          const float dz = row < a.M ? v[i] * t[lane * 33 + i] : 0.f;
           const __nv_bfloat16 db = __float2bfloat16(dz);
           if (row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = db;
           v[i] = __bfloat162float(db);
@@ -283,6 +293,6 @@ nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int split
   a.out_bfT = static_cast<__nv_bfloat16*>(out_bfT);
   a.dbias = dbias;
   a.status = status;
-  gemm::gemm_bf16_tn_kernel<<<dim3(M / gemm::kBM, splits), 128, gemm::kSmem, s>>>(ta, tb, a);
+  gemm::gemm_bf16_tn_kernel<<<dim3(M / gemm::kBM, splits), gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a);
   return nv_cuda_check(cudaGetLastError(), "gemm_bf16_tn_kernel launch");
 }

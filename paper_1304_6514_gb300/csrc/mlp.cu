@@ -45,8 +45,11 @@ __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t i) {
 __device__ __forceinline__ double u01(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+// GELU(z) = z Phi(z) and GELU'(z) = Phi(z) + z phi(z), sharing Phi's erf
+__device__ __forceinline__ float gelu_with_grad(float z, float* grad) {
+  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+  *grad = cdf + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return z * cdf;
 }
 
 // ---- training pairs: sample k of slice j, component c is SplitMix64 output
@@ -131,7 +134,8 @@ __global__ void gather_kernel(const float* y0, const float* ye, int64_t N, int64
   Y[b * OUT + 6] = Y[b * OUT + 7] = 0.f;
 }
 
-// layer 1: Z1 = X W1^T + b1 (K = 8), H1 = GELU(Z1)
+// layer 1: z = X W1^T + b1 (K = 8), H1 = GELU(z); when training Z1 keeps
+// GELU'(z) for the backward pass (likewise Z2, Z3 from the GEMM epilogues)
 __global__ void l1_fwd_kernel(const float* P, const float* X, int B, float* Z1, __nv_bfloat16* H1,
                               __nv_bfloat16* H1t, int train) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -140,10 +144,11 @@ __global__ void l1_fwd_kernel(const float* P, const float* X, int B, float* Z1, 
   float z = P[ob1 + n];
 #pragma unroll
   for (int k = 0; k < IN; ++k) z = fmaf(P[oW1 + n * IN + k], X[b * IN + k], z);
-  const __nv_bfloat16 hb = __float2bfloat16(gelu_f(z));
+  float gp = 0.f;
+  const __nv_bfloat16 hb = __float2bfloat16(train ? gelu_with_grad(z, &gp) : gelu_f(z));
   H1[i] = hb;
   if (train) {
-    Z1[i] = z;
+    Z1[i] = gp;                                   // GELU'(z), what the backward pass needs
     H1t[(int64_t)n * B + b] = hb;
   }
 }
@@ -189,7 +194,7 @@ __global__ void l4_kernel(const float* P, const __nv_bfloat16* H3, const float* 
     float dh = 0.f;
 #pragma unroll
     for (int c = 0; c < D; ++c) dh = fmaf(r[c], P[oW4 + c * H + k], dh);
-    const float dz = dh * gelu_grad_f(Z3[(int64_t)b * H + k]);
+    const float dz = dh * Z3[(int64_t)b * H + k];     // Z3 holds GELU'(z3)
     const __nv_bfloat16 db = __float2bfloat16(dz);
     dZ3[(int64_t)b * H + k] = db;
     dZ3t[(int64_t)k * B + b] = db;
