@@ -59,6 +59,8 @@ __device__ __forceinline__ float gelu_with_grad(float z, float* grad) {
 
 constexpr int kThreads = 256;
 
+// MODE: the epilogue (one instantiation each keeps the code per kernel small)
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args a) {
   using namespace tc;
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // warp transposes its 32 x 32 chunks there, so that row-major traffic
     // (float32 results, saved pre-activations, bf16 row-major copies, the
     // split-K accumulation) moves as 128-byte rows across the lanes instead of
-    // one 1 KB-strided row per lane.  Tile t: 32 x 33 floats per warp.
+    // one 1 KB-strided row per lane.  Tile t: 32 x 33 floats per warp (two per
+    // warp for the training forward pass: 67.6 KB of the 192 KB of stages).
     float* t = reinterpret_cast<float*>(base) + warp * 32 * 33;
     const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32q .. 32q+31, columns 128h ..
     const int m = quarter * 32 + lane;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-      if (a.mode == kAtomic) {
+      if constexpr (MODE == kAtomic) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
         __syncwarp();
@@ -160,55 +163,61 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int r = 0; r < 32; ++r)
           if (r < nrows) atomicAdd(a.out32 + (int64_t)(wrow0 + r) * kBN + c0 + lane, t[r * 33 + lane]);
         __syncwarp();
-      } else if (a.mode == kFwdTrain || a.mode == kFwdInfer) {
+      } else if constexpr (MODE == kFwdTrain || MODE == kFwdInfer) {
+        // h and GELU'(z) go straight to two tiles (the second after all eight
+        // warps' first tiles), so no second 32-value array stays live
+        float* t2 = reinterpret_cast<float*>(base) + (kThreads / 32 + warp) * 32 * 33;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float z = v[i] + a.bias[c0 + i];
           float gp = 0.f;
-          const float h = a.mode == kFwdTrain ? gelu_with_grad(z, &gp) : gelu_f(z);
+          const float h = MODE == kFwdTrain ? gelu_with_grad(z, &gp) : gelu_f(z);
           const __nv_bfloat16 hb = __float2bfloat16(h);
-          if (a.mode == kFwdTrain && row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
-          v[i] = gp;
+          if (MODE == kFwdTrain && row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
           t[lane * 33 + i] = __bfloat162float(hb);      // exact: hb is a bf16 value
+          if (MODE == kFwdTrain) t2[lane * 33 + i] = gp;
         }
         __syncwarp();
 #pragma unroll
         for (int r = 0; r < 32; ++r)
-          if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+          if (r < nrows) {
+            a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+            if (MODE == kFwdTrain) a.zsave[(int64_t)(wrow0 + r) * kBN + c0 + lane] = t2[r * 33 + lane];
+          }
         __syncwarp();
-        if (a.mode == kFwdTrain) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (r < nrows) a.zsave[(int64_t)(wrow0 + r) * kBN + c0 + lane] = t[r * 33 + lane];
-          __syncwarp();
-        }
       } else {   // kBwd: zin arrives by rows, dz leaves by rows and transposed
-        // all 32 loads in flight together (a rolled loop would wait on each)
+        // all 32 loads in flight before any is used (rows past M repeat the
+        // last valid row; nrows >= 1 for every warp that has rows)
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-          if (r < nrows) t[r * 33 + lane] = a.zin[(int64_t)(wrow0 + r) * kBN + c0 + lane];
+        for (int h = 0; h < 32; h += 16) {           // two batches of 16 keep the registers in bounds
+          float zr[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r)
+            zr[r] = a.zin[(int64_t)(wrow0 + min(h + r, nrows - 1)) * kBN + c0 + lane];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) t[(h + r) * 33 + lane] = zr[r];
+        }
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float dz = row < a.M ? v[i] * t[lane * 33 + i] : 0.f;
-          const __nv_bfloat16 db = __float2bfloat16(dz);
-          if (row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = db;
-          v[i] = __bfloat162float(db);
-          float s = dz;
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-          if (lane == 0) atomicAdd(a.dbias + c0 + i, s);
+          if (row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = __float2bfloat16(dz);
+          v[i] = dz;
         }
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
         __syncwarp();
+        // lane l: column c0 + l over the warp's 32 rows: bias gradient and the
+        // row-major bf16 copy (rows past M hold dz = 0)
+        float colsum = 0.f;
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-          if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(t[r * 33 + lane]);
+        for (int r = 0; r < 32; ++r) {
+          const float dz = t[r * 33 + lane];
+          colsum += dz;
+          if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(dz);
+        }
+        atomicAdd(a.dbias + c0 + lane, colsum);
         __syncwarp();
       }
     }
@@ -265,9 +274,16 @@ static nv_status bf16_map(CUtensorMap* map, const void* ptr, int rows, int K, in
 
 // Sets the kernel's shared-memory limit once (before any graph capture).
 nv_status gemm_bf16_prepare() {
-  return nv_cuda_check(cudaFuncSetAttribute(gemm::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            gemm::kSmem),
-                       "gemm smem attribute");
+  const void* fns[] = {(const void*)gemm::gemm_bf16_tn_kernel<gemm::kAtomic>,
+                       (const void*)gemm::gemm_bf16_tn_kernel<gemm::kFwdTrain>,
+                       (const void*)gemm::gemm_bf16_tn_kernel<gemm::kBwd>,
+                       (const void*)gemm::gemm_bf16_tn_kernel<gemm::kFwdInfer>};
+  for (const void* f : fns) {
+    nv_status st = nv_cuda_check(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm::kSmem),
+                                 "gemm smem attribute");
+    if (st != NV_OK) return st;
+  }
+  return NV_OK;
 }
 
 // D[M x 256] = A[M x K] B[256 x K]^T with epilogue `mode`; splits > 1 divides K.
@@ -293,6 +309,13 @@ nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int split
   a.out_bfT = static_cast<__nv_bfloat16*>(out_bfT);
   a.dbias = dbias;
   a.status = status;
-  gemm::gemm_bf16_tn_kernel<<<dim3(M / gemm::kBM, splits), gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a);
+  const dim3 grid(M / gemm::kBM, splits);
+  switch (mode) {
+    case gemm::kAtomic: gemm::gemm_bf16_tn_kernel<gemm::kAtomic><<<grid, gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a); break;
+    case gemm::kFwdTrain: gemm::gemm_bf16_tn_kernel<gemm::kFwdTrain><<<grid, gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a); break;
+    case gemm::kBwd: gemm::gemm_bf16_tn_kernel<gemm::kBwd><<<grid, gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a); break;
+    case gemm::kFwdInfer: gemm::gemm_bf16_tn_kernel<gemm::kFwdInfer><<<grid, gemm::kThreads, gemm::kSmem, s>>>(ta, tb, a); break;
+    default: return nv_fail(NV_EINVAL, "unknown gemm epilogue %d", mode);
+  }
   return nv_cuda_check(cudaGetLastError(), "gemm_bf16_tn_kernel launch");
 }
