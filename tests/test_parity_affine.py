@@ -27,10 +27,11 @@ def _heat(torch, w, prec, rhs_name="heat1d"):
     return maps, A, b, yT, lam
 
 
-@pytest.mark.parametrize("n,S", [(40, 7), (64, 3), (1, 4), (97, 5)])
+@pytest.mark.parametrize("n,S", [(40, 7), (64, 3), (1, 4), (97, 5), (40, 1), (256, 1)])
 def test_heat_small_elementwise_fp64(n, S):
     """Every map entry and every boundary state; n = 40 and 97 leave padding
-    rows in the last lanes, n = 1 is the degenerate single-unknown case."""
+    rows in the last lanes, n = 1 is the degenerate single-unknown case, S = 1
+    the single slice (a chain of one step)."""
     torch = need_gpu()
     w = workloads.heat1d(n=n, S=S, T=0.003, dt=5e-5)
     _, A, b, yT, lam = _heat(torch, w, "fp64")

@@ -60,6 +60,16 @@ def test_ragged_pl_sizes(scheme, M):
     assert oob == ooob
 
 
+def test_single_slice_table():
+    """S = 1: the method degenerates to one table and one lookup."""
+    torch = need_gpu()
+    tab, otab, lam, olam, oob, ooob = _pl_case(torch, "cos_cubic", (), 0.0, 1.0, 1, 17, -2.0, 2.0,
+                                               "rk4", 1e-3, 0, 0.5, "fp64")
+    assert rel_max(tab, otab) <= 1e-11
+    assert rel_max(lam, olam) <= 1e-11
+    assert oob == ooob == 0
+
+
 def test_out_of_range_extrapolates_and_counts():
     """y' = y^2 from 1.2 leaves [0, 1.5]: the edge segment is extended (as in
     the oracle) and every evaluation outside is counted."""
