@@ -33,7 +33,8 @@ def test_heat_small_elementwise_fp64(n, S):
     rows in the last lanes, n = 1 is the degenerate single-unknown case, S = 1
     the single slice (a chain of one step)."""
     torch = need_gpu()
-    w = workloads.heat1d(n=n, S=S, T=0.003, dt=5e-5)
+    dt = min(5e-5, 2.0 / (4.0 * (n + 1) ** 2))       # within RK4's stability limit
+    w = workloads.heat1d(n=n, S=S, T=60 * dt, dt=dt)
     _, A, b, yT, lam = _heat(torch, w, "fp64")
     m = nv.workload_steps(w)
     fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
