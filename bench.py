@@ -244,6 +244,24 @@ def time_variant(nvp, torch, w, prec, K, W, flush, stream):
     return {"build_ms": build, "compose_ms": comp, "step_ms": tot, "yT": yT.cpu().numpy(), "m": m}
 
 
+def time_serial_gpu(nvp, torch, w, stream, reps=3):
+    """The plain serial fine solve on the GPU (nv_serial_fine: one warp, all S m
+    RK4 steps in sequence), the other reference the method is judged against."""
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    st = nvp.steps("rk4", w.dt, 0, "fp64")
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    ys = torch.empty_like(y0)
+    with torch.cuda.stream(stream):
+        nvp.serial_fine(r, w.t0, w.T, w.S, st, y0, ys, stream=stream)      # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            nvp.serial_fine(r, w.t0, w.T, w.S, st, y0, ys, stream=stream)
+        ev[1].record(stream)
+        stream.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps, ys.cpu().numpy()
+
+
 def time_e2e(nvp, torch, w, K, W, stream):
     """End to end through nv_solve (allocates, builds, composes, frees) with
     pinned host buffers copied in and out every step."""
@@ -937,6 +955,7 @@ def main():
         e2e_t, h2d, d2h = time_e2e(nvp, torch, w, max(3, K // 4), 2, stream)
     e2e_val = units / statistics.mean(e2e_t)
 
+    serial_ms, serial_gpu = time_serial_gpu(nvp, torch, w, stream)
     peaks_probe = {} if args.no_probe else gpu_peak_probe(torch)
     peaks, peaks_src = read_peaks()
 
@@ -949,6 +968,10 @@ def main():
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "time_to_solution_ms": statistics.mean(res["step_ms"]),
+        "serial_fine_gpu": {"ms": serial_ms,
+                            "rel_diff_method": float(np.linalg.norm(res["yT"] - serial_gpu) / np.linalg.norm(serial_gpu)),
+                            "note": "one warp stepping all S m RK4 steps in sequence: the plain solve the "
+                                    "method parallelises (the method does (d+1) times its work)"},
         "wall_s_timed_region": wall,
         "roofline": {"bound": "alu", "kernel": "heat_poly9_kernel<double,8,0>",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
