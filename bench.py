@@ -317,13 +317,15 @@ def gpu_peak_probe(torch):
 # captures ran smaller cases of the same kernels; see profiles/):
 #   heat FP64 build (nine-point form), S = 512 capture: 206.55 MB for 131 072 columns
 #   advection-diffusion FP32 build, S = 8 capture: 475.04 MB for 32 776 columns
-#   Van der Pol batch build, 512 instances: 502.0 MB for 561 987 584 table bytes
+#   Van der Pol batch build, 512 instances: 503.0 MB for 561 987 584 table bytes
+#   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 NCU_TRAFFIC_PER_UNIT = {
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
     "heat_poly9_kernel<double,8,0>": (206.55e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
-    "batch_build_kernel<RhsVdp<float>,float,4,1>": (502.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
+    "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
+    "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
 }
 
 
@@ -854,7 +856,9 @@ def run_chain3_mlp(args):
                          "achieved": FP32_FLOP_PER_CHAIN_STEP * pair_steps / (pairs_ms * 1e-3) / 1e12,
                          "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": FP32_FLOP_PER_CHAIN_STEP * pair_steps / (pairs_ms * 1e-3) / FP32_PEAK_NOMINAL,
-                         "traffic": None},
+                         "traffic": ncu_traffic("pairs_kernel<float>", S * M * 12 * 4)[0],
+                         "traffic_source": ncu_traffic("pairs_kernel<float>", 1)[1],
+                         "algorithmic_bytes": S * M * 12 * 4},
             "train": {"seconds": train_s, "losses": losses, "model_tflops": train_tflops,
                       "steps_per_s": nsteps / train_s},
             "validation_rel_err": {"mean": float(err.mean()), "max": float(err.max()),
