@@ -201,10 +201,10 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Map storage and workspace come from the device's stream-ordered pool on the
-// build stream.  Once per device the pool keeps up to 256 MB of freed memory
+// build stream.  Once per device the pool keeps up to 1 GB of freed memory
 // (instead of returning everything at each synchronisation), so a repeated
-// nv_solve of a small problem does not pay for fresh allocations; larger
-// maps still go back to the driver when freed.
+// nv_solve of a problem up to that size does not pay for fresh allocations;
+// larger maps still go back to the driver when freed.
 static nv_status pool_setup(int dev) {
   static std::mutex mu;
   static bool done[256] = {};
@@ -213,7 +213,7 @@ static nv_status pool_setup(int dev) {
   cudaMemPool_t pool;
   nv_status e = nv_cuda_check(cudaDeviceGetDefaultMemPool(&pool, dev), "default memory pool");
   if (e != NV_OK) return e;
-  uint64_t keep = 256ull << 20;
+  uint64_t keep = 1ull << 30;
   e = nv_cuda_check(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "pool threshold");
   if (e == NV_OK) done[dev] = true;
   return e;
