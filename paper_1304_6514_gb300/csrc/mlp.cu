@@ -538,19 +538,25 @@ extern "C" nv_status nv_mlp_grads(nv_mlp* m, const float* X_dev, const float* Y_
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   nv_status st = mlp_batch(m, B);
   if (st != NV_OK) return st;
-  cudaMemcpyAsync(m->X, X_dev, sizeof(float) * B * IN, cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(m->Y, Y_dev, sizeof(float) * B * OUT, cudaMemcpyDeviceToDevice, s);
-  cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s);
-  cudaMemsetAsync(m->loss, 0, sizeof(float), s);
+  if ((st = nv_cuda_check(cudaMemcpyAsync(m->X, X_dev, sizeof(float) * B * IN, cudaMemcpyDeviceToDevice, s),
+                          "inputs")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemcpyAsync(m->Y, Y_dev, sizeof(float) * B * OUT, cudaMemcpyDeviceToDevice, s),
+                          "targets")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s), "gradient reset")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemsetAsync(m->loss, 0, sizeof(float), s), "loss reset")) != NV_OK)
+    return st;
   if ((st = mlp_fwd_bwd(m, 1, s)) != NV_OK) return st;
-  cudaMemcpyAsync(grads_dev, m->G, sizeof(float) * NP, cudaMemcpyDeviceToDevice, s);
   float l = 0.f;
-  cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
-  if ((st = nv_cuda_check(cudaStreamSynchronize(s), "mlp grads")) != NV_OK) return st;
-  cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s);
-  if (loss) *loss = l;
   int dst = 0;
-  cudaMemcpy(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if ((st = nv_cuda_check(cudaMemcpyAsync(grads_dev, m->G, sizeof(float) * NP, cudaMemcpyDeviceToDevice, s),
+                          "gradients")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s), "loss")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemcpyAsync(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status")) !=
+          NV_OK ||
+      (st = nv_cuda_check(cudaStreamSynchronize(s), "mlp grads")) != NV_OK)
+    return st;
+  if ((st = nv_cuda_check(cudaMemsetAsync(m->G, 0, sizeof(float) * NP, s), "gradient reset")) != NV_OK) return st;
+  if (loss) *loss = l;
   if (dst != NV_OK) return nv_fail((nv_status)dst, "device status %d in the MLP kernels", dst);
   return NV_OK;
 }
@@ -610,15 +616,19 @@ extern "C" nv_status nv_mlp_train(nv_mlp* m, const float* y0_dev, const float* y
     m->graph_lr = (float)lr;
   }
   for (int64_t k = 0; k < steps; ++k) {
-    if (k == steps - 1) cudaMemsetAsync(m->loss, 0, sizeof(float), s);
+    if (k == steps - 1 &&
+        (st = nv_cuda_check(cudaMemsetAsync(m->loss, 0, sizeof(float), s), "loss reset")) != NV_OK)
+      return st;
     if ((st = nv_cuda_check(cudaGraphLaunch(m->train_graph, s), "training step")) != NV_OK) return st;
   }
   float l = 0.f;
-  cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
-  if ((st = nv_cuda_check(cudaStreamSynchronize(s), "training")) != NV_OK) return st;
-  if (last_loss) *last_loss = l;
   int dst = 0;
-  cudaMemcpy(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if ((st = nv_cuda_check(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s), "loss")) != NV_OK ||
+      (st = nv_cuda_check(cudaMemcpyAsync(&dst, m->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status")) !=
+          NV_OK ||
+      (st = nv_cuda_check(cudaStreamSynchronize(s), "training")) != NV_OK)
+    return st;
+  if (last_loss) *last_loss = l;
   if (dst != NV_OK) return nv_fail((nv_status)dst, "device status %d in the MLP kernels", dst);
   return NV_OK;
 }
@@ -641,7 +651,7 @@ extern "C" nv_status nv_mlp_validate(nv_mlp* m, const double* y0_dev, const doub
   if (st != NV_OK) return st;
   double* acc = nullptr;
   if ((st = nv_cuda_check(cudaMalloc(&acc, sizeof(double) * 2 * S), "validation accumulators")) != NV_OK) return st;
-  cudaMemsetAsync(acc, 0, sizeof(double) * 2 * S, s);
+  st = nv_cuda_check(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * S, s), "accumulator reset");
   for (int j = 0; j < S && st == NV_OK; ++j) {
     const double* y0j = y0_dev + (int64_t)j * Mv * D;
     st = mlp_infer(m, y0j, Mv, j, S, s);
