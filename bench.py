@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nvpit", choices=["nvpit", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="fp32,tf32_refine,fp32_refine")
+    ap.add_argument("--variants", default="fp32,tf32_refine,fp32_refine,fp32_refine:2",
+                    help="precisions timed beside the float64 headline; prec:p sets p correction passes")
     ap.add_argument("--slices", type=int, default=0, help="override S (profiling a reduced case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
@@ -935,11 +936,18 @@ def main():
                          "build_frac_of_fp64_nominal": achieved / FP64_PEAK_NOMINAL}}
     results = {"fp64": res["yT"]}
     for v in [x for x in args.variants.split(",") if x]:
+        # "prec:p" sets p float64 correction passes (nv_tune_set key 5) for that variant
+        prec, _, passes = v.partition(":")
         try:
-            rv = time_variant(nvp, torch, w, v, K, W, flush, stream)
+            if passes:
+                nvp.tune_set(5, int(passes))
+            rv = time_variant(nvp, torch, w, prec, K, W, flush, stream)
         except nvp.NvError as e:
             variants[v] = {"unavailable": str(e)}
             continue
+        finally:
+            if passes:
+                nvp.tune_set(5, 0)
         results[v] = rv["yT"]
         bs = statistics.mean(rv["build_ms"]) * 1e-3
         variants[v] = {"ms_per_step": statistics.mean(rv["step_ms"]),
