@@ -143,6 +143,23 @@ def test_heat_full_size(prec, tol, final_tol):
     assert rel_l2(lam[-1], yT) == 0.0
 
 
+def test_heat_fp32_two_passes_reach_float64_error():
+    """Full size: float32 maps + two float64 correction passes land at the
+    float64 method's own error level against the serial fine solve (both
+    ~1e-13), the equal-error point of the mixed-precision form."""
+    torch = need_gpu()
+    o = _full_oracle()
+    w = o["w"]
+    nvp.tune_set(5, 2)
+    try:
+        _, A, b, yT, lam = _heat(torch, w, "fp32_refine")
+    finally:
+        nvp.tune_set(5, 0)
+    err = rel_l2(yT, o["serial"])
+    print("fp32 + 2 passes final state relative error", err)
+    assert err <= 5e-13
+
+
 @pytest.mark.parametrize("n,S", [(40, 7), (256, 9), (100, 5)])
 def test_heat_fp32_refined_small(n, S):
     """float32 maps + one float64 correction pass, every boundary state: the
