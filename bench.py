@@ -524,7 +524,9 @@ def run_advdiff(args):
     K = max(1, args.steps)
     W = max(3, args.warmup)
     clocks = None
-    for prec in ("fp32", "fp32_refine", "bf16_refine", "fp64"):
+    for name in ("fp32", "fp32_refine", "fp32_refine:2", "bf16_refine", "fp64"):
+        prec, _, passes = name.partition(":")        # prec:p = p float64 correction passes
+        nvp.tune_set(5, int(passes) if passes else 0)
         st = nvp.steps("rk4", w.dt, 0, prec)
         y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
         yT = torch.empty_like(y0)
@@ -556,24 +558,25 @@ def run_advdiff(args):
         b = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
         c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
         comp_steps = w.S * (w.dim + 1) * d.steps_per_slice * w.dim
-        out[prec] = {"build_ms": b, "compose_ms": c, "map_bytes": d.bytes,
+        nvp.tune_set(5, 0)
+        out[name] = {"build_ms": b, "compose_ms": c, "map_bytes": d.bytes,
                      "build_tflops": FLOP_PER_ADV_COMPONENT_STEP * comp_steps / (b * 1e-3) / 1e12,
                      "yT": yT.cpu().numpy()}
         if prec.endswith("_refine"):
             # the approximate chain, then per pass float64 defects + a correction chain
-            nch = 1 + (2 if prec == "bf16_refine" else 1)
-            out[prec]["chains_over_maps"] = nch
-            out[prec]["maps_hbm_gbs_over_compose"] = nch * d.bytes / (c * 1e-3) / 1e9
+            nch = 1 + (int(passes) if passes else (2 if prec == "bf16_refine" else 1))
+            out[name]["chains_over_maps"] = nch
+            out[name]["maps_hbm_gbs_over_compose"] = nch * d.bytes / (c * 1e-3) / 1e9
         else:
-            out[prec]["chain_hbm_gbs"] = d.bytes / (c * 1e-3) / 1e9
-            out[prec]["chain_frac_of_hbm"] = d.bytes / (c * 1e-3) / 1e9 / peaks["hbm_gbs"]
+            out[name]["chain_hbm_gbs"] = d.bytes / (c * 1e-3) / 1e9
+            out[name]["chain_frac_of_hbm"] = d.bytes / (c * 1e-3) / 1e9 / peaks["hbm_gbs"]
         maps.destroy()
         torch.cuda.empty_cache()
     f32, f64 = out["fp32"], out["fp64"]
     units = w.S * (w.dim + 1) * 10
     step_ms = f32["build_ms"] + f32["compose_ms"]
     rel = float(np.linalg.norm(f32["yT"] - f64["yT"]) / np.linalg.norm(f64["yT"]))
-    for v in ("fp32_refine", "bf16_refine"):
+    for v in ("fp32_refine", "fp32_refine:2", "bf16_refine"):
         out[v]["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(out[v]["yT"] - f64["yT"]) / np.linalg.norm(f64["yT"]))
     for v in out.values():
         v.pop("yT")
