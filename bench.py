@@ -408,6 +408,32 @@ def run_vdp_batch(args):
     step_s = _max_over_ranks(torch, world, sum(build) * 1e-3 + sum(comp) * 1e-3)
     graph_ms = gev[0].elapsed_time(gev[1]) / K
     units = info["traj_steps"]
+    # the plain method on the same instances, one at a time: build + compose
+    # per instance through the single-problem API (same tables, precision and
+    # composition), timed on a sample of instances spread over the batch and
+    # scaled by their share of the trajectory-steps
+    yT_b = yT.cpu().numpy()
+    pick = np.linspace(0, len(vb.mu) - 1, min(64, len(vb.mu))).astype(int)
+    plain_ms, plain_units, plain_diff = 0.0, 0, 0.0
+    with torch.cuda.stream(stream):
+        y1 = torch.empty(2, dtype=torch.float64, device="cuda")
+        yo = torch.empty_like(y1)
+        for i in pick:
+            r1 = nvp.rhs("vdp", 2, (float(vb.mu[i]),))
+            y1.copy_(torch.tensor(vb.y0[i], dtype=torch.float64))
+            mp = nvp.build_propagators(r1, 0.0, float(vb.T[i]), int(vb.S[i]), smp, st, stream=stream)
+            nvp.compose(mp, y1, yo, stream=stream)                           # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nvp.build_propagators(r1, 0.0, float(vb.T[i]), int(vb.S[i]), smp, st, maps=mp, stream=stream)
+            nvp.compose(mp, y1, yo, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            plain_units += int(vb.S[i]) * nvp.maps_info(mp).steps_per_slice * P * P
+            plain_diff = max(plain_diff, float(np.abs(yo.cpu().numpy() - yT_b[i]).max()))
+            mp.destroy()
+    plain_total_ms = plain_ms * units / plain_units
     bmean = statistics.mean(build) * 1e-3
     achieved = FP32_FLOP_PER_VDP_STEP * units / bmean
     line = {"metric": METRIC, "value": units * K * world / step_s, "unit": UNIT, "n_gpus": world,
@@ -419,6 +445,10 @@ def run_vdp_batch(args):
                        "cta_threads_autotuned": best, "l2": "flushed before every timed step"},
             "build_ms": statistics.mean(build), "compose_ms": statistics.mean(comp),
             "graph_run_ms": graph_ms, "out_of_range_evaluations": oob,
+            "plain_per_instance": {"ms_for_all_instances": plain_total_ms,
+                                   "speedup_of_batched_graph": plain_total_ms / graph_ms,
+                                   "sample": f"{len(pick)} instances timed one by one, scaled by trajectory-steps",
+                                   "max_abs_diff_vs_batched": plain_diff},
             "roofline": {"bound": "alu", "kernel": "batch_build_kernel<RhsVdp<float>,float,4,1>",
                          "achieved": achieved / 1e12, "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_NOMINAL,
