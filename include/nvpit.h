@@ -396,8 +396,14 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          context stays usable.  The paper has no counterpart.
  *   key 8: split-K of the learned propagator's weight-gradient GEMMs (K = the
  *          batch): 0 auto, or 1, 2, 4, 8, 16
+ *   key 9: kernel of the d > 512 chain: 0 auto (1 for float32 maps, 2 for
+ *          float64 and bfloat16 maps), 1 loads into registers in batches with
+ *          a grid barrier per step, 2 a shared-memory ring fed by bulk
+ *          asynchronous copies with a barrier-free tagged exchange of the
+ *          partial sums.  Same arithmetic in the same order: the results are
+ *          identical.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7 and 8. */
+ * or an out-of-range value of keys 6, 7, 8 and 9. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

@@ -19,7 +19,7 @@ nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, 
 nv_status launch_serial_wave(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 int64_t wave_aux_elems(int d);
 
-nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
 static thread_local char g_err[512] = "";
 
@@ -226,8 +226,15 @@ static nv_status alloc_maps(nv_maps* P, cudaStream_t s) {
   e = nv_cuda_check(cudaMallocAsync(&P->data, (size_t)P->bytes, s), "map allocation");
   if (e != NV_OK) { P->data = nullptr; return e; }
   const size_t xoff = 256;
-  // 2 float64 chain vectors + a triple buffer of chain states (tiled chain) + slack
-  const size_t coff = align256(xoff + sizeof(double) * 5 * (size_t)P->dim + 64);
+  // 2 float64 chain vectors + slack; for d > 512 also the tiled chain's
+  // partial-sum scratch
+  int sms = 0;
+  if (P->dim > 512 &&
+      (e = nv_cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device),
+                         "SM count")) != NV_OK)
+    return e;
+  const size_t part_bytes = P->dim > 512 ? tile_chain_scratch_bytes(P->prec, P->dim, sms) : 0;
+  const size_t coff = align256(xoff + sizeof(double) * 2 * (size_t)P->dim + 16 + part_bytes + 64);
   const size_t aoff = align256(coff + sizeof(double) * (size_t)(P->coef_per_slice * P->S));
   P->ws_bytes = aoff + sizeof(double) * (size_t)P->aux_elems;
   e = nv_cuda_check(cudaMallocAsync(&P->ws, P->ws_bytes, s), "workspace allocation");
@@ -437,6 +444,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 8:
       if (value < 0 || value > 16 || (value & (value - 1))) return nv_fail(NV_EINVAL, "split-K is 0 (auto) or 1, 2, 4, 8, 16");
       g_tune.mlp_wgrad_splits = value;
+      break;
+    case 9:
+      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "tiled chain form is 0, 1 or 2");
+      g_tune.tile_chain_form = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }

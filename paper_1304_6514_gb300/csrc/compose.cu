@@ -449,50 +449,106 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
 // Grid-wide chain for large d (d > 512, d a multiple of 4).  CTA (rb, cb)
 // owns a tile of the slice map: rows [rb*RB, rb*RB + RB) of the column block
 // [cb*cpc, (cb+1)*cpc) of [b_j | A_j].  A column of the tile is RB contiguous
-// values (4 KB for float32), so the map streams in long runs; each thread reads
-// VEC = 16 / sizeof(MT) consecutive rows with one 16-byte load per column.
-// Partial row sums of the column blocks meet in global memory by atomic adds
-// into one of three rotating state buffers (step k adds into buffer k % 3,
-// reads buffer (k-1) % 3 and clears buffer (k+1) % 3 for the next step), and
-// one bounded grid barrier per step orders the steps.
+// values (8 KB for float32), so the map streams in long runs; each thread reads
+// VEC consecutive rows with one 16-byte (bfloat16: 8-byte) load per column.
+// Step k stores the tile's partial row sums, one 16-byte store per thread, in
+// the partial buffer k % 2 (a row of ncb values per state component), and one
+// bounded grid barrier per step orders the steps.  Step k + 1 then sums, for
+// its own column block only, the ncb partials of each state component it
+// multiplies (ncb * cpc L2 reads per CTA) and the row-block-0 CTAs write those
+// states out: no atomics, no buffer to clear, and a fixed summation order.
 template <typename MT, typename AT>
 __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainArgs a, int nrb, int cpc,
-                                                                AT* xb) {
+                                                                AT* part) {
   // MT: double, float, or uint16_t holding bfloat16 bits.  Rows per thread:
   // 2 (double), 4 (float, and bfloat16 as 8-byte loads: 8 rows per thread
-  // would halve the column blocks' row count and double the atomic adds per
-  // state row, which then dominate)
+  // would halve the column blocks' row count and double the partial sums
+  // per state component)
   constexpr int VEC = sizeof(MT) == 2 ? 4 : 16 / (int)sizeof(MT);
+  static_assert(VEC * sizeof(AT) == 16, "one 16-byte partial store per thread");
   using V = typename std::conditional<sizeof(MT) == 4, float4,
                                       typename std::conditional<sizeof(MT) == 8, double2, uint2>::type>::type;
   extern __shared__ __align__(16) unsigned char sxt_raw[];
-  AT* sx = reinterpret_cast<AT*>(sxt_raw);   // the cpc state values of this column block
+  AT* sx = reinterpret_cast<AT*>(sxt_raw);    // the cpc state values of this column block
+  AT* red = sx + ((cpc + 3) & ~3);            // max(blockDim.x, cpc) group sums
   __shared__ int flag;
   const int n = a.n;
   const int RB = VEC * blockDim.x;
   const int rb = blockIdx.x % nrb, cb = blockIdx.x / nrb;
+  const int ncb = gridDim.x / nrb;
   const int tid = threadIdx.x;
   const int row0 = rb * RB + tid * VEC;
   const bool active = row0 < n;
   const int c0 = cb * cpc, c1 = min(n + 1, c0 + cpc);
+  const int ncols = max(0, c1 - c0);
+  const int ngrp = ncols > 0 ? max(1, (int)blockDim.x / ncols) : 1;
   const unsigned G = gridDim.x;
   const MT* maps = reinterpret_cast<const MT*>(a.maps);
   const int64_t slice_elems = (int64_t)n * (n + 1);
   if (blockIdx.x == 0 && a.lambdas)
     for (int i = tid; i < n; i += blockDim.x) a.lambdas[i] = a.y0[i] + (a.base ? a.base[i] : 0.0);
   const AT one = a.col0_off ? (AT)0 : (AT)1;
-  for (int k = 0; k < a.S; ++k) {
-    AT* acc_buf = xb + (k % 3) * n;
-    const AT* in_buf = xb + ((k + 2) % 3) * n;
-    AT* clr_buf = xb + ((k + 1) % 3) * n;
-    for (int c = c0 + tid; c < c1; c += blockDim.x)
-      sx[c - c0] = c == 0 ? one : (k == 0 ? (AT)a.y0[c - 1] : __ldcg(in_buf + c - 1));
-    for (int i = blockIdx.x * blockDim.x + tid; i < n; i += G * blockDim.x) clr_buf[i] = (AT)0;
-    __syncthreads();
-    AT acc[VEC];
+
+  // sx <- the state after kk steps for this block's columns, summed from the
+  // partials of step kk - 1; CTAs of row block 0 write it out (+ base).
+  auto gather = [&](int kk) {
+    const AT* P = part + (size_t)((kk - 1) & 1) * ncb * n;
+    for (int p = tid; p < ncols * ngrp; p += blockDim.x) {
+      const int j = p % ncols, g = p / ncols;
+      const int i = c0 + j - 1;   // state component multiplied by column c0 + j
+      AT sum = 0;
+      if (i >= 0)
+        for (int b0 = g; b0 < ncb; b0 += 8 * ngrp) {
+          AT v[8];
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) acc[v] = 0;
+          for (int q = 0; q < 8; ++q) {
+            const int b = b0 + q * ngrp;
+            v[q] = b < ncb ? __ldcg(P + (size_t)b * n + i) : (AT)0;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) sum += v[q];
+        }
+      red[g * ncols + j] = sum;
+    }
+    __syncthreads();
+    for (int j = tid; j < ncols; j += blockDim.x) {
+      const int c = c0 + j;
+      AT sum = 0;
+      for (int g = 0; g < ngrp; ++g) sum += red[g * ncols + j];
+      sx[j] = c == 0 ? one : sum;
+      if (rb == 0 && c > 0) {
+        const int64_t o = (int64_t)kk * n + c - 1;
+        const double xv = (double)sum + (a.base ? a.base[o] : 0.0);
+        if (a.lambdas) a.lambdas[o] = xv;
+        if (kk == a.S && a.yT) a.yT[c - 1] = xv;
+      }
+    }
+  };
+
+  // batches of kBatch independent loads in flight per thread; the last batch
+  // of a column block is predicated
+  constexpr int kBatch = 16;
+  V t[kBatch];
+  auto load_batch = [&](const MT* A, int c) {
+#pragma unroll
+    for (int q = 0; q < kBatch; ++q)
+      if (c + q < c1) t[q] = __ldg(reinterpret_cast<const V*>(A + (int64_t)(c + q) * n));
+  };
+  // the first batch of every step is loaded before the barrier that ends the
+  // previous step (it does not depend on the state), so the map stream runs
+  // while the grid waits
+  if (active) load_batch(maps + row0, c0);
+  for (int k = 0; k < a.S; ++k) {
+    if (k == 0) {
+      for (int c = c0 + tid; c < c1; c += blockDim.x) sx[c - c0] = c == 0 ? one : (AT)a.y0[c - 1];
+    } else {
+      gather(k);
+    }
+    __syncthreads();
     if (active) {
+      AT acc[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[v] = 0;
       const MT* A = maps + (int64_t)k * slice_elems + row0;
       auto madd = [&](const V& t, AT xc) {
         if constexpr (sizeof(MT) == 2) {    // bfloat16: the high half of a float32
@@ -512,35 +568,340 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
           acc[1] = fma((AT)t.y, xc, acc[1]);
         }
       };
-      // batches of kBatch independent 16-byte loads in flight per thread
-      constexpr int kBatch = 16;
-      int c = c0;
-      for (; c + kBatch <= c1; c += kBatch) {
-        V t[kBatch];
+      for (int c = c0; c < c1; c += kBatch) {
+        if (c != c0) load_batch(A, c);
 #pragma unroll
-        for (int q = 0; q < kBatch; ++q) t[q] = __ldg(reinterpret_cast<const V*>(A + (int64_t)(c + q) * n));
-#pragma unroll
-        for (int q = 0; q < kBatch; ++q) madd(t[q], sx[c + q - c0]);
+        for (int q = 0; q < kBatch; ++q)
+          if (c + q < c1) madd(t[q], sx[c + q - c0]);
       }
-      for (; c < c1; ++c) madd(__ldcs(reinterpret_cast<const V*>(A + (int64_t)c * n)), sx[c - c0]);
       if (a.vadd && cb == 0) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] += (AT)a.vadd[(int64_t)k * n + row0 + v];
       }
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) atomicAdd(acc_buf + row0 + v, acc[v]);
+      AT* dst = part + ((size_t)(k & 1) * ncb + cb) * n + row0;
+      if constexpr (sizeof(AT) == 4)
+        __stcg(reinterpret_cast<float4*>(dst), make_float4(acc[0], acc[1], acc[2], acc[3]));
+      else
+        __stcg(reinterpret_cast<double2*>(dst), make_double2(acc[0], acc[1]));
+      if (k + 1 < a.S) load_batch(A + slice_elems, c0);
     }
     if (!grid_barrier(a.bar, (unsigned)(k + 1) * G, a.status, &flag)) return;
-    if (cb == 0 && active) {
+  }
+  if (rb == 0) gather(a.S);
+}
+
+// The same tiled chain with the map stream decoupled from the arithmetic and
+// no grid barrier.
+//
+// Stream: one producer lane copies the CTA's tile, column segments of RB rows,
+// into a ring of kTileStages shared-memory stages with bulk asynchronous
+// copies that complete on the stage's mbarrier; 16 consumer warps multiply
+// each stage by the state and release it.  The producer's sequence of stages
+// runs over all S steps without regard to the state, so while the consumers
+// wait for the next state it keeps streaming the next map into the free
+// stages.
+//
+// Exchange: each partial row sum is stored as one 64-bit word, a 32-bit
+// payload (a float32, or one half of a float64) beside the 32-bit tag k + 1 of
+// the step that produced it.  An aligned 64-bit store or load is single-copy
+// atomic, so a reader that polls the words it needs until their tags read
+// k + 1 has the values themselves: no fence, no counter, no barrier, and each
+// CTA waits only for the partials its own columns multiply.  Step k writes
+// buffer k % 3.  Overwriting it at step k + 3 is safe: a CTA at step t has
+// read partials of step t - 1 from every column block of some row block,
+// whose columns together span all n + 1 columns, so those CTAs had read the
+// partials of step t - 2 from every CTA, i.e. every CTA had finished reading
+// step t - 3's buffer.  The buffers are cleared before each launch so that no
+// tag from an earlier launch matches.
+//
+// Consumers synchronise among themselves with named barrier 1; the producer
+// warp joins no block-wide barrier after the set-up.  Every wait is bounded
+// (1 s); a thread that gives up records NV_ETIMEOUT in the status word and
+// sets the CTA's abort flag, after which no thread of the CTA waits again, the
+// producer stops issuing and waits for its copies in flight, and the
+// consumers run out their loops without waiting.
+constexpr int kTileConsumers = 512;
+constexpr int kTileStageBytes = 16 * 1024;
+constexpr int kTileStages = 12;
+constexpr int kTagBuffers = 3;
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTileConsumers) : "memory");
+}
+
+__device__ __forceinline__ void ring_release(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cta_smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   cta_smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(cta_smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// 64-bit words per partial value: the value's 32-bit pieces, each with a tag.
+template <typename AT>
+constexpr int tag_words() { return (int)sizeof(AT) / 4; }
+
+__device__ __forceinline__ void tag_pack(float x, uint32_t tag, unsigned long long* w) {
+  w[0] = ((unsigned long long)tag << 32) | __float_as_uint(x);
+}
+__device__ __forceinline__ void tag_pack(double x, uint32_t tag, unsigned long long* w) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  w[0] = ((unsigned long long)tag << 32) | (u & 0xffffffffull);
+  w[1] = ((unsigned long long)tag << 32) | (u >> 32);
+}
+__device__ __forceinline__ float tag_value(const unsigned long long* w, float*) {
+  return __uint_as_float((uint32_t)w[0]);
+}
+__device__ __forceinline__ double tag_value(const unsigned long long* w, double*) {
+  return __longlong_as_double((long long)((w[1] << 32) | (w[0] & 0xffffffffull)));
+}
+
+template <typename MT, typename AT>
+__global__ void __launch_bounds__(kTileConsumers + 32, 1)
+    affine_chain_ring_kernel(AffineChainArgs a, int nrb, int cpc, unsigned long long* part) {
+  constexpr int VEC = sizeof(MT) == 2 ? 4 : 16 / (int)sizeof(MT);
+  constexpr int W = tag_words<AT>();
+  using V = typename std::conditional<sizeof(MT) == 4, float4,
+                                      typename std::conditional<sizeof(MT) == 8, double2, uint2>::type>::type;
+  constexpr int RB = VEC * kTileConsumers;                       // rows of a tile
+  constexpr int CPS = kTileStageBytes / (RB * (int)sizeof(MT));  // columns per stage
+  static_assert(CPS >= 1 && CPS * RB * (int)sizeof(MT) == kTileStageBytes, "whole columns per stage");
+  extern __shared__ __align__(128) unsigned char ring_raw[];
+  MT* ring = reinterpret_cast<MT*>(ring_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring_raw + kTileStages * kTileStageBytes);
+  uint64_t* empty = full + kTileStages;
+  AT* sx = reinterpret_cast<AT*>(empty + kTileStages);   // the cpc state values of this column block
+  AT* red = sx + ((cpc + 3) & ~3);                        // max(kTileConsumers, cpc) group sums
+  __shared__ volatile int s_abort;
+  const int n = a.n;
+  const int rb = blockIdx.x % nrb, cb = blockIdx.x / nrb;
+  const int ncb = gridDim.x / nrb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row0 = rb * RB + tid * VEC;
+  const bool active = tid < kTileConsumers && row0 < n;
+  const int c0 = cb * cpc, c1 = min(n + 1, c0 + cpc);
+  const int ncols = max(0, c1 - c0);
+  const int nst = (ncols + CPS - 1) / CPS;                // stages per step
+  const int rows = min(RB, n - rb * RB);
+  const uint32_t seg_bytes = (uint32_t)rows * (uint32_t)sizeof(MT);
+  const MT* maps = reinterpret_cast<const MT*>(a.maps);
+  const int64_t slice_elems = (int64_t)n * (n + 1);
+  const size_t buf_words = (size_t)ncb * n * W;
+  if (tid == 0) {
+    for (int i = 0; i < kTileStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cta_smem_u32(&full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cta_smem_u32(&empty[i])),
+                   "n"(kTileConsumers / 32)
+                   : "memory");
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kTileConsumers / 32) {   // producer
+    if (lane == 0 && nst > 0) {
+      // stage g = (step k, stage st of the step) in ring slot g % kTileStages;
+      // all cursors advance incrementally (no 64-bit divisions in this loop)
+      const int64_t total = (int64_t)a.S * nst;
+      const MT* tile0 = maps + (int64_t)c0 * n + (int64_t)rb * RB;   // step 0, stage 0
+      const int64_t step_stride = slice_elems, stage_stride = (int64_t)CPS * n;
+      auto stage_cols = [&](int st) { return min(CPS, ncols - st * CPS); };
+      const MT* src = tile0;                 // stage g
+      int st = 0, slot = 0;
+      uint32_t parity = 1;                   // phase parity of the stage's previous use
+      int64_t g = 0;
+      for (; g < total && !s_abort; ++g) {
+        if (g >= kTileStages) {   // wait until the consumers free this stage
+          if (!ring_wait(&empty[slot], parity)) {
+            record_status(a.status, NV_ETIMEOUT);
+            s_abort = 1;
+            break;
+          }
+        }
+        const int cnt = stage_cols(st);
+        arm_tx(&full[slot], (uint32_t)cnt * seg_bytes);
+        MT* dst = ring + (size_t)slot * CPS * RB;
+        for (int q = 0; q < cnt; ++q) bulk_load(dst + q * RB, src + (int64_t)q * n, seg_bytes, &full[slot]);
+        if (++st == nst) {
+          st = 0;
+          src += step_stride - (int64_t)(nst - 1) * stage_stride;
+        } else {
+          src += stage_stride;
+        }
+        if (++slot == kTileStages) {
+          slot = 0;
+          parity ^= 1;
+        }
+      }
+      // no copy may land in the shared memory of an exited CTA: wait for the
+      // last stages issued (the consumers have already taken them unless a
+      // wait gave up)
+      for (int64_t gg = g > kTileStages ? g - kTileStages : 0; gg < g; ++gg)
+        ring_wait(&full[gg % kTileStages], (uint32_t)((gg / kTileStages) & 1));
+    }
+    return;
+  }
+
+  // consumers: threads 0 .. kTileConsumers-1
+  const int ngrp = ncols > 0 ? max(1, kTileConsumers / ncols) : 1;
+  if (blockIdx.x == 0 && a.lambdas)
+    for (int i = tid; i < n; i += kTileConsumers) a.lambdas[i] = a.y0[i] + (a.base ? a.base[i] : 0.0);
+  const AT one = a.col0_off ? (AT)0 : (AT)1;
+  // sx <- the state after kk steps for this block's columns.  First one
+  // thread per source column block polls one sentinel word of that block (the
+  // first state component this CTA needs) until its tag reads kk: a source
+  // block's rows are stored together at the end of its step, so the rest is
+  // then almost always there too, and polling one word per source keeps the
+  // L2 traffic of the wait small.  Then thread (j, g) loads the partials of
+  // column blocks g, g + ngrp, ... for state component c0 + j - 1, re-polls
+  // any whose tag is not yet kk, and sums them in that order; CTAs of row
+  // block 0 write the state out (+ base).
+  const int i_sent = max(c0 - 1, 0);
+  const bool needs_state = c1 - 1 > i_sent;
+  auto gather = [&](int kk) {
+    const unsigned long long* P = part + (size_t)((kk - 1) % kTagBuffers) * buf_words;
+    auto poll = [&](const unsigned long long* p) {   // bounded; returns the word read last
+      unsigned long long v = ld_tagged(p);
+      uint64_t t0 = 0;
+      while ((uint32_t)(v >> 32) != (uint32_t)kk && !s_abort) {
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > 1000000000ull) {
+          record_status(a.status, NV_ETIMEOUT);
+          s_abort = 1;
+        }
+        __nanosleep(20);
+        v = ld_tagged(p);
+      }
+      return v;
+    };
+    if (needs_state)
+      for (int b = tid; b < ncb; b += kTileConsumers) poll(P + ((size_t)b * n + i_sent) * W);
+    consumers_sync();
+    for (int p = tid; p < ncols * ngrp; p += kTileConsumers) {
+      const int j = p % ncols, g = p / ncols;
+      const int i = c0 + j - 1;   // state component multiplied by column c0 + j
+      AT sum = 0;
+      if (i >= 0)
+        for (int b0 = g; b0 < ncb; b0 += 8 * ngrp) {
+          unsigned long long v[8][W];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (b0 + q * ngrp < ncb)
+#pragma unroll
+              for (int w = 0; w < W; ++w) v[q][w] = ld_tagged(P + ((size_t)(b0 + q * ngrp) * n + i) * W + w);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (b0 + q * ngrp < ncb) {
+#pragma unroll
+              for (int w = 0; w < W; ++w)
+                if ((uint32_t)(v[q][w] >> 32) != (uint32_t)kk)
+                  v[q][w] = poll(P + ((size_t)(b0 + q * ngrp) * n + i) * W + w);
+              sum += tag_value(v[q], (AT*)nullptr);
+            }
+        }
+      red[g * ncols + j] = sum;
+    }
+    consumers_sync();
+    for (int j = tid; j < ncols; j += kTileConsumers) {
+      const int c = c0 + j;
+      AT sum = 0;
+      for (int g = 0; g < ngrp; ++g) sum += red[g * ncols + j];
+      sx[j] = c == 0 ? one : sum;
+      if (rb == 0 && c > 0) {
+        const int64_t o = (int64_t)kk * n + c - 1;
+        const double xv = (double)sum + (a.base ? a.base[o] : 0.0);
+        if (a.lambdas) a.lambdas[o] = xv;
+        if (kk == a.S && a.yT) a.yT[c - 1] = xv;
+      }
+    }
+  };
+  int cslot = 0;          // ring slot and phase parity of the next stage
+  uint32_t cphase = 0;
+  for (int k = 0; k < a.S; ++k) {
+    if (k == 0) {
+      for (int c = c0 + tid; c < c1; c += kTileConsumers) sx[c - c0] = c == 0 ? one : (AT)a.y0[c - 1];
+    } else {
+      gather(k);
+    }
+    consumers_sync();
+    AT acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = 0;
+    for (int st = 0; st < nst; ++st) {
+      const int slot = cslot;
+      const uint32_t cpar = cphase;
+      if (++cslot == kTileStages) {
+        cslot = 0;
+        cphase ^= 1;
+      }
+      bool ok = !s_abort;
+      if (ok && !ring_wait(&full[slot], cpar)) {
+        record_status(a.status, NV_ETIMEOUT);
+        s_abort = 1;
+        ok = false;
+      }
+      if (ok && active) {
+        const MT* seg = ring + (size_t)slot * CPS * RB + tid * VEC;
+#pragma unroll
+        for (int q = 0; q < CPS; ++q) {
+          if (st * CPS + q < ncols) {
+            const V t = *reinterpret_cast<const V*>(seg + q * RB);
+            const AT xc = sx[st * CPS + q];
+            if constexpr (sizeof(MT) == 2) {   // bfloat16: the high half of a float32
+              const uint32_t w[2] = {t.x, t.y};
+#pragma unroll
+              for (int i = 0; i < 2; ++i) {
+                acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
+                acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
+              }
+            } else if constexpr (VEC == 4) {
+              acc[0] = fma((AT)t.x, xc, acc[0]);
+              acc[1] = fma((AT)t.y, xc, acc[1]);
+              acc[2] = fma((AT)t.z, xc, acc[2]);
+              acc[3] = fma((AT)t.w, xc, acc[3]);
+            } else {
+              acc[0] = fma((AT)t.x, xc, acc[0]);
+              acc[1] = fma((AT)t.y, xc, acc[1]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) ring_release(&empty[slot]);
+    }
+    if (active) {
+      if (a.vadd && cb == 0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += (AT)a.vadd[(int64_t)k * n + row0 + v];
+      }
+      unsigned long long* dst = part + (size_t)(k % kTagBuffers) * buf_words + ((size_t)cb * n + row0) * W;
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
-        const int64_t o = (int64_t)(k + 1) * n + row0 + v;
-        const double xv = (double)__ldcg(acc_buf + row0 + v) + (a.base ? a.base[o] : 0.0);
-        if (a.lambdas) a.lambdas[o] = xv;
-        if (k == a.S - 1 && a.yT) a.yT[row0 + v] = xv;
+        unsigned long long w[W];
+        tag_pack(acc[v], (uint32_t)(k + 1), w);
+#pragma unroll
+        for (int q = 0; q < W; ++q) st_tagged(dst + v * W + q, w[q]);
       }
     }
   }
+  if (rb == 0) gather(a.S);
 }
 
 }  // namespace nvpit
@@ -696,9 +1057,23 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   return launch_chains(a, f64, s, want_csize);
 }
 
+size_t tile_chain_ring_scratch(int n, int ncb, int value_bytes) {
+  return (size_t)kTagBuffers * ncb * n * (value_bytes / 4) * sizeof(unsigned long long);
+}
+
+size_t tile_chain_scratch_bytes(int prec, int n, int sms) {
+  const bool f64 = prec == NV_FP64;
+  const int rb = f64 ? 2 * 512 : 4 * 512;   // rows per tile: VEC x 512 threads
+  const int ncb = std::max(1, sms / ((n + rb - 1) / rb));
+  const int esz = f64 ? 8 : 4;
+  return std::max(tile_chain_ring_scratch(n, ncb, esz), (size_t)esz * 2 * ncb * n);
+}
+
 // Tiled grid-wide chain (d > 512, d % 4 == 0): one CTA per SM, row blocks of
 // 2048 (float32, bfloat16) / 1024 (float64) rows, column blocks sized to fill
-// the grid.
+// the grid.  Tunable 9 selects the kernel (default: the register kernel for
+// float32 maps, the bulk-copy ring for float64 and bfloat16 maps, whose
+// columns must then be 16-byte aligned).
 template <typename MT, typename AT>
 static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                             const TileChainExtra* ex, cudaStream_t s) {
@@ -714,23 +1089,38 @@ static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, doub
   const int cpc = (n + 1 + ncb - 1) / ncb;
   const int G = nrb * ncb;
   const size_t esz = sizeof(AT);
-  const size_t smem = esz * (size_t)cpc;
-  const void* fn = (const void*)affine_chain_tile_kernel<MT, AT>;
+  const size_t state_smem = esz * ((size_t)((cpc + 3) & ~3) + (size_t)std::max(block, cpc));
+  // the bulk-copy ring needs 16-byte aligned column segments
+  // measured at d = 4096, S = 512: the ring is faster for float64 maps
+  // (16.9 vs 19.4 ms) and bfloat16 maps (5.0 vs 5.2 ms), the register kernel
+  // for float32 maps (6.8 vs 7.0 ms)
+  const int form = g_tune.tile_chain_form != 0 ? g_tune.tile_chain_form : (sizeof(MT) == 4 ? 1 : 2);
+  const bool ring = form == 2 && ((uintptr_t)M->data & 15) == 0 && ((size_t)n * sizeof(MT)) % 16 == 0;
+  const void* fn = ring ? (const void*)affine_chain_ring_kernel<MT, AT>
+                        : (const void*)affine_chain_tile_kernel<MT, AT>;
+  const int threads = ring ? kTileConsumers + 32 : block;
+  const size_t smem = ring ? (size_t)kTileStages * kTileStageBytes + 2 * kTileStages * sizeof(uint64_t) + state_smem
+                           : state_smem;
   nv_status st;
+  if (ring && (st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                  "ring chain smem attribute")) != NV_OK)
+    return st;
   int per_sm = 0;
-  if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem),
+  if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem),
                           "chain occupancy")) != NV_OK)
     return st;
   if ((int64_t)per_sm * sms < G)
     return nv_fail(NV_ENOTSUP, "chain needs %d resident CTAs, device holds %d", G, per_sm * sms);
-  // state triple buffer in the maps workspace tail: 3 * n values
-  if (M->ws_bytes < 256 + sizeof(double) * 2 * (size_t)n + esz * 3 * (size_t)n)
+  // the partial sums after the float64 chain vectors: two buffers of ncb x n
+  // values (register kernel) or three of tagged 64-bit words (ring kernel)
+  const size_t part_bytes = ring ? tile_chain_ring_scratch(n, ncb, (int)esz) : esz * 2 * (size_t)ncb * (size_t)n;
+  if (M->ws_bytes < 256 + sizeof(double) * 2 * (size_t)n + 16 + part_bytes)
     return nv_fail(NV_ENOTSUP, "workspace too small for the tiled chain");
   void* xb = reinterpret_cast<char*>(M->xbuf) + sizeof(double) * 2 * (size_t)n;
   xb = reinterpret_cast<void*>(((uintptr_t)xb + 15) & ~(uintptr_t)15);
-  if ((st = nv_cuda_check(cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s), "barrier reset")) != NV_OK ||
-      (st = nv_cuda_check(cudaMemsetAsync(xb, 0, esz * (size_t)n, s), "chain state reset")) != NV_OK)
+  if ((st = nv_cuda_check(cudaMemsetAsync(M->bar, 0, sizeof(unsigned), s), "barrier reset")) != NV_OK)
     return st;
+  if (ring && (st = nv_cuda_check(cudaMemsetAsync(xb, 0, part_bytes, s), "tag reset")) != NV_OK) return st;
   AffineChainArgs a{};
   a.maps = M->data;
   a.n = n;
@@ -749,8 +1139,8 @@ static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, doub
   }
   int nrb_arg = nrb, cpc_arg = cpc;
   void* args[] = {&a, &nrb_arg, &cpc_arg, &xb};
-  return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s),
-                       "affine_chain_tile_kernel cooperative launch");
+  return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, s),
+                       "tiled chain cooperative launch");
 }
 
 nv_status launch_tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,

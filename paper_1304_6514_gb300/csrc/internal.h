@@ -83,6 +83,9 @@ struct TileChainExtra {
   const double* base;   // added to every state written (S+1 x n), or NULL
   int col0_off;         // 1: drop column 0 (b_j) of the maps
 };
+// Bytes of the d > 512 chain's partial-sum scratch (in the maps workspace).
+size_t tile_chain_ring_scratch(int n, int ncb, int value_bytes);
+size_t tile_chain_scratch_bytes(int prec, int n, int sms);
 nv_status launch_tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                             const TileChainExtra* ex, cudaStream_t s);
 // float64 defects of the advection-diffusion maps: d_j = g^j(lam_j) - lam_{j+1}
@@ -121,5 +124,6 @@ struct nv_tunables {
   int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil
   int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
   int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
+  int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring
 };
 extern nv_tunables g_tune;

@@ -107,6 +107,10 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(7, -1) == nvp.NV_EINVAL
     assert lib.nv_tune_set(8, 3) == nvp.NV_EINVAL           # split-K is 0 or a power of two <= 16
     assert lib.nv_tune_set(8, 32) == nvp.NV_EINVAL
+    assert lib.nv_tune_set(9, 3) == nvp.NV_EINVAL           # tiled chain kernel is 0..2
+    assert lib.nv_tune_set(9, -1) == nvp.NV_EINVAL
+    assert lib.nv_tune_set(9, 1) == nvp.NV_OK
+    assert lib.nv_tune_set(9, 0) == nvp.NV_OK
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
     h = ctypes.c_void_p()
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL

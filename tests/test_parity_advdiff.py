@@ -102,3 +102,38 @@ def test_advdiff_fp32_refined_full_size():
     fine solve."""
     torch = need_gpu()
     _check(torch, workloads.advdiff2d(), "fp32_refine", [0, 511], 1e-5, 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16_refine"])
+def test_tiled_chain_ring_and_register_kernels_agree(prec):
+    """The d > 512 chain has two kernels with the same arithmetic in the same
+    order: loads into registers in batches (tunable 9 = 1) and the
+    shared-memory ring fed by bulk copies (9 = 2, the default).  Their boundary
+    states agree bit for bit, over column blocks whose last stage is ragged
+    (4097 columns over 76 or 38 blocks), and the final state is the serial fine
+    solve's within the precision's bound."""
+    torch = need_gpu()
+    w = workloads.advdiff2d(S=5, T=5 * 2e-3)
+    r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                 nvp.steps("rk4", w.dt, 0, prec))
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    out = {}
+    try:
+        for form in (1, 2):
+            nvp.tune_set(9, form)
+            yT = torch.empty_like(y0)
+            lam = torch.full((w.S + 1, w.dim), float("nan"), dtype=torch.float64, device="cuda")
+            nvp.compose(maps, y0, yT, lambdas=lam)
+            nvp.maps_check(maps)
+            out[form] = (yT.cpu(), lam.cpu())
+    finally:
+        nvp.tune_set(9, 0)
+        maps.destroy()
+    assert torch.equal(out[1][0], out[2][0])
+    assert torch.equal(out[1][1], out[2][1])
+    assert torch.equal(out[2][1][-1], out[2][0])
+    m = nv.workload_steps(w)
+    ser = nv.serial_fine(nv.workload_rhs(w, True), "rk4", w.t0, w.T, w.S, m, w.y0)
+    tol = {"fp64": 1e-11, "fp32": 1e-5, "bf16_refine": 1e-4}[prec]
+    assert rel_l2(out[2][0].numpy(), ser) <= tol
