@@ -321,7 +321,9 @@ def gpu_peak_probe(torch):
 #   Van der Pol batch build, 512 instances: 503.0 MB for 561 987 584 table bytes
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
+#   advection-diffusion FP32 chain, S = 8: 547.9 MB for 8 slice maps (537.0 MB read once)
 NCU_TRAFFIC_PER_UNIT = {
+    "affine_chain_tile_kernel<float,float>": (547.89e6 / 8, "profiles/advdiff_chains_d4096_S512.md"),
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
     "heat_poly9_kernel<double,8,0>": (206.55e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
@@ -626,7 +628,10 @@ def run_advdiff(args):
                          "flop_per_launch": FLOP_PER_ADV_COMPONENT_STEP * w.S * (w.dim + 1) * 10 * w.dim},
             "chain_roofline": {"bound": "hbm", "kernel": "affine_chain_tile_kernel<float,float>",
                                "achieved": f32["chain_hbm_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                               "frac": f32["chain_frac_of_hbm"], "traffic": None},
+                               "frac": f32["chain_frac_of_hbm"],
+                               "traffic": ncu_traffic("affine_chain_tile_kernel<float,float>", w.S)[0],
+                               "traffic_source": ncu_traffic("affine_chain_tile_kernel<float,float>", 1)[1],
+                               "algorithmic_bytes": f32["map_bytes"]},
             "gpu_launches": 2 * K, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
