@@ -104,16 +104,18 @@ def test_advdiff_fp32_refined_full_size():
     _check(torch, workloads.advdiff2d(), "fp32_refine", [0, 511], 1e-5, 1e-7)
 
 
+@pytest.mark.parametrize("S", [1, 2, 5])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16_refine"])
-def test_tiled_chain_ring_and_register_kernels_agree(prec):
+def test_tiled_chain_ring_and_register_kernels_agree(prec, S):
     """The d > 512 chain has two kernels with the same arithmetic in the same
     order: loads into registers in batches (tunable 9 = 1) and the
     shared-memory ring fed by bulk copies (9 = 2, the default).  Their boundary
     states agree bit for bit, over column blocks whose last stage is ragged
-    (4097 columns over 76 or 38 blocks), and the final state is the serial fine
-    solve's within the precision's bound."""
+    (4097 columns over 76 or 38 blocks), for chains shorter than, equal to and
+    longer than the ring kernel's three rotating exchange buffers, and the final
+    state is the serial fine solve's within the precision's bound."""
     torch = need_gpu()
-    w = workloads.advdiff2d(S=5, T=5 * 2e-3)
+    w = workloads.advdiff2d(S=S, T=S * 2e-3)
     r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
     maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
                                  nvp.steps("rk4", w.dt, 0, prec))
