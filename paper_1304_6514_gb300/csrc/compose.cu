@@ -446,6 +446,28 @@ __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_con
   cl.sync();   // no CTA leaves while another may still address its shared memory
 }
 
+// acc[0..VEC) += (the VEC map entries in t) * xc, for one column of a tile:
+// VEC consecutive rows of MT (bfloat16 as the high halves of float32 words).
+template <typename MT, typename AT, int VEC, typename V>
+__device__ __forceinline__ void tile_madd(AT* acc, const V& t, AT xc) {
+  if constexpr (sizeof(MT) == 2) {
+    const uint32_t w[2] = {t.x, t.y};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
+      acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
+    }
+  } else if constexpr (VEC == 4) {
+    acc[0] = fma((AT)t.x, xc, acc[0]);
+    acc[1] = fma((AT)t.y, xc, acc[1]);
+    acc[2] = fma((AT)t.z, xc, acc[2]);
+    acc[3] = fma((AT)t.w, xc, acc[3]);
+  } else {
+    acc[0] = fma((AT)t.x, xc, acc[0]);
+    acc[1] = fma((AT)t.y, xc, acc[1]);
+  }
+}
+
 // Grid-wide chain for large d (d > 512, d a multiple of 4).  CTA (rb, cb)
 // owns a tile of the slice map: rows [rb*RB, rb*RB + RB) of the column block
 // [cb*cpc, (cb+1)*cpc) of [b_j | A_j].  A column of the tile is RB contiguous
@@ -550,29 +572,11 @@ __global__ void __launch_bounds__(512, 1) affine_chain_tile_kernel(AffineChainAr
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[v] = 0;
       const MT* A = maps + (int64_t)k * slice_elems + row0;
-      auto madd = [&](const V& t, AT xc) {
-        if constexpr (sizeof(MT) == 2) {    // bfloat16: the high half of a float32
-          const uint32_t w[2] = {t.x, t.y};
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
-            acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
-          }
-        } else if constexpr (VEC == 4) {
-          acc[0] = fma((AT)t.x, xc, acc[0]);
-          acc[1] = fma((AT)t.y, xc, acc[1]);
-          acc[2] = fma((AT)t.z, xc, acc[2]);
-          acc[3] = fma((AT)t.w, xc, acc[3]);
-        } else {
-          acc[0] = fma((AT)t.x, xc, acc[0]);
-          acc[1] = fma((AT)t.y, xc, acc[1]);
-        }
-      };
       for (int c = c0; c < c1; c += kBatch) {
         if (c != c0) load_batch(A, c);
 #pragma unroll
         for (int q = 0; q < kBatch; ++q)
-          if (c + q < c1) madd(t[q], sx[c + q - c0]);
+          if (c + q < c1) tile_madd<MT, AT, VEC>(acc, t[q], sx[c + q - c0]);
       }
       if (a.vadd && cb == 0) {
 #pragma unroll
@@ -861,26 +865,8 @@ __global__ void __launch_bounds__(kTileConsumers + 32, 1)
         const MT* seg = ring + (size_t)slot * CPS * RB + tid * VEC;
 #pragma unroll
         for (int q = 0; q < CPS; ++q) {
-          if (st * CPS + q < ncols) {
-            const V t = *reinterpret_cast<const V*>(seg + q * RB);
-            const AT xc = sx[st * CPS + q];
-            if constexpr (sizeof(MT) == 2) {   // bfloat16: the high half of a float32
-              const uint32_t w[2] = {t.x, t.y};
-#pragma unroll
-              for (int i = 0; i < 2; ++i) {
-                acc[2 * i] = fma((AT)__uint_as_float(w[i] << 16), xc, acc[2 * i]);
-                acc[2 * i + 1] = fma((AT)__uint_as_float(w[i] & 0xffff0000u), xc, acc[2 * i + 1]);
-              }
-            } else if constexpr (VEC == 4) {
-              acc[0] = fma((AT)t.x, xc, acc[0]);
-              acc[1] = fma((AT)t.y, xc, acc[1]);
-              acc[2] = fma((AT)t.z, xc, acc[2]);
-              acc[3] = fma((AT)t.w, xc, acc[3]);
-            } else {
-              acc[0] = fma((AT)t.x, xc, acc[0]);
-              acc[1] = fma((AT)t.y, xc, acc[1]);
-            }
-          }
+          if (st * CPS + q < ncols)
+            tile_madd<MT, AT, VEC>(acc, *reinterpret_cast<const V*>(seg + q * RB), sx[st * CPS + q]);
         }
       }
       __syncwarp();
