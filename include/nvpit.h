@@ -402,8 +402,14 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          asynchronous copies with a barrier-free tagged exchange of the
  *          partial sums.  Same arithmetic in the same order: the results are
  *          identical.
+ *   key 10: schedule of the float64 correction passes of NV_FP32_REFINE on the
+ *          heat equations: 0 auto (pipelined: the approximate chain, every
+ *          pass's defects and correction chain run concurrently in one
+ *          cooperative launch, each a few slices behind the one it corrects,
+ *          where 64 <= d <= 256, d % 16 == 0 and at most 3 passes), 1 the
+ *          passes one after another.  Same arithmetic: identical results.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8 and 9. */
+ * or an out-of-range value of keys 6, 7, 8, 9 and 10. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

@@ -17,6 +17,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "chain.cuh"
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -191,259 +192,11 @@ __global__ void __launch_bounds__(256) affine_chains_kernel(ChainsArgs a) {
   }
 }
 
-// TMA-fed variant (64 <= d <= 256, d % 16 == 0; 16 CTAs x 16 rows): each
-// CTA's rows of A_j (16 x d, one 3-D box) are copied by the tensor memory
-// accelerator into a ring of kRing shared-memory stages, kRing - 1 slices
-// ahead, completing on an mbarrier; the copies run in the async proxy, so no
-// load sits on the dependency chain.  Stage layout: element (row r, column c)
-// at c*16 + r.
-//
-// The new state is exchanged without a cluster barrier: the lane that owns a
-// row stores it into the matching state buffer of every CTA of the cluster
-// with st.async, which completes bytes on that CTA's state mbarrier, and a CTA
-// starts step k+1 as soon as its own barrier has counted all d values of
-// x_{k+1}.  Two state buffers alternate; buffer (k+2) & 1 is rewritten only
-// by senders that already hold x_{k+1}, which every CTA sends after it has
-// read x_k, so no CTA overwrites a state another is still reading.  The
-// final state x_len is written to global memory only.  Every wait is bounded
-// (1 s of globaltimer); a CTA that gives up records NV_ETIMEOUT, stops
-// sending and leaves the loop, so the others give up at their next wait.
-constexpr int kRing = 3;
-constexpr int kChainRpc = 16;   // rows per CTA of the TMA chain
-
-__device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool ring_wait(uint64_t* bar, uint32_t parity) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.b32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(cta_smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 1000000000ull) return false;
-  }
-}
-
-// Wait for a phase completed by other CTAs' st.async: acquire at cluster scope.
-__device__ __forceinline__ bool state_wait(uint64_t* bar, uint32_t parity) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
-        "selp.b32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(cta_smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 1000000000ull) return false;
-  }
-}
-
-__device__ __forceinline__ void arm_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cta_smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, unsigned rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-  return r;
-}
-
-// 16 bytes to another CTA's shared memory, completing on its mbarrier.
-__device__ __forceinline__ void st_async16(uint32_t addr, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                           uint32_t bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-                   addr),
-               "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(bar)
-               : "memory");
-}
-
-// Eight consecutive row values (this lane's half of the CTA's 16 rows) as
-// 32 (float) or 64 (double) bytes of 16-byte stores.
-__device__ __forceinline__ void send_rows(const float* v, uint32_t addr, uint32_t bar) {
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-    st_async16(addr + 16 * q, __float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
-               __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]), bar);
-}
-__device__ __forceinline__ void send_rows(const double* v, uint32_t addr, uint32_t bar) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const unsigned long long u0 = __double_as_longlong(v[2 * q]), u1 = __double_as_longlong(v[2 * q + 1]);
-    st_async16(addr + 16 * q, (uint32_t)u0, (uint32_t)(u0 >> 32), (uint32_t)u1, (uint32_t)(u1 >> 32), bar);
-  }
-}
-
 template <typename MT, typename AT>
 __global__ void __launch_bounds__(256) affine_chains_tma_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 ChainsArgs a, int* status) {
-  constexpr int rpc = kChainRpc;
-  cg::cluster_group cl = cg::this_cluster();
-  const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
-  const int q = (int)(blockIdx.x / csize);
-  extern __shared__ __align__(128) unsigned char ring_smem[];
-  const int n = a.n;
-  const int stage_elems = rpc * n;
-  MT* ring = reinterpret_cast<MT*>(ring_smem);                          // kRing stages
-  // per stage also rpc values of v_j and of add_{j+1}, as doubles (16-byte slots)
-  double* vring = reinterpret_cast<double*>(ring + kRing * stage_elems);
-  double* aring = vring + kRing * rpc;
-  AT* xs = reinterpret_cast<AT*>(aring + kRing * rpc);                 // two state buffers
-  AT* red = xs + 2 * n;                                                // per-warp row partials
-  uint64_t* full = reinterpret_cast<uint64_t*>(
-      ((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);
-  uint64_t* xbar = full + kRing;                                       // state buffers 0, 1
-  __shared__ int abort_flag;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int r = tid % rpc, cgi = tid / rpc, ncg = blockDim.x / rpc;
-  const int my_row = (int)rank * rpc + (lane & (rpc - 1));              // row of a lane in warp 0
-  const bool active = (int)rank * rpc + r < n;
-  // CTAs past row n - 1 (d < 256) own no rows: they neither read nor send a
-  // state and take no part in the exchange
-  const unsigned owners = (unsigned)(n / rpc);
-  const bool has_rows = rank < owners;
-  const int j0 = q * a.len;
-  const int len = min(a.len, a.S - j0);
-  const int vsz = a.v_double ? 8 : (int)sizeof(MT);
-  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT)) + (uint32_t)(rpc * vsz) +
-                               (a.add ? (uint32_t)(rpc * 8) : 0u);
-  const uint32_t state_bytes = (uint32_t)(n * sizeof(AT));
-
-  if (tid == 0) {
-    for (int i = 0; i < kRing + 2; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cta_smem_u32(&full[i])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (has_rows && len >= 2) arm_tx(&xbar[1], state_bytes);   // x_1, sent during step 0
-    if (has_rows && len >= 3) arm_tx(&xbar[0], state_bytes);   // x_2, sent during step 1
-    abort_flag = 0;
-  }
-  __syncthreads();
-  auto issue = [&](int k) {   // thread 0: copy this CTA's rows of A_{j0+k}
-    const int st = k % kRing;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cta_smem_u32(&full[st])),
-                 "r"(stage_bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(cta_smem_u32(ring + st * stage_elems)),
-        "l"(&tmA), "r"((int)rank * rpc), "r"(0), "r"(j0 + k), "r"(cta_smem_u32(&full[st]))
-        : "memory");
-    const char* vsrc = reinterpret_cast<const char*>(a.v) +
-                       ((int64_t)(j0 + k) * a.v_stride + (int64_t)rank * rpc) * vsz;
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            cta_smem_u32(vring + st * rpc)),
-        "l"(vsrc), "r"(rpc * vsz), "r"(cta_smem_u32(&full[st]))
-        : "memory");
-    if (a.add) {
-      const double* asrc = a.add + (int64_t)(j0 + k + 1) * n + (int64_t)rank * rpc;
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              cta_smem_u32(aring + st * rpc)),
-          "l"(asrc), "r"(rpc * 8), "r"(cta_smem_u32(&full[st]))
-          : "memory");
-    }
-  };
-  int issued = 0;   // copies issued so far (thread 0)
-  if (tid == 0 && has_rows)
-    for (; issued < min(kRing - 1, len); ++issued) issue(issued);
-
-  const double* x0 = a.x0 ? a.x0 + (int64_t)q * a.x0_stride : nullptr;
-  for (int i = tid; i < n; i += blockDim.x) xs[i] = x0 ? (AT)x0[i] : (AT)0;
-  if (q == 0 && rank == 0 && a.write_state0 && a.states)
-    for (int i = tid; i < n; i += blockDim.x)
-      a.states[i] = (x0 ? x0[i] : 0.0) + (a.add ? a.add[i] : 0.0);
-  cl.sync();   // barriers initialised and armed, x_0 in place, before any st.async
-
-  // Sending: lane l of warp 0 stores rows 8 (l / 16) .. +7 of this CTA into
-  // CTA p = l % 16; its remote addresses of both state buffers and barriers.
-  const unsigned peer = (unsigned)(lane & 15);
-  const int half_rows = (lane >> 4) * 8;
-  const bool sender = warp == 0 && peer < owners;
-  uint32_t rx0 = 0u, rx1 = 0u, rb0 = 0u, rb1 = 0u;
-  if (sender) {
-    const uint32_t off = (uint32_t)(((int)rank * rpc + half_rows) * sizeof(AT));
-    rx0 = cluster_addr(cta_smem_u32(xs), peer) + off;
-    rx1 = cluster_addr(cta_smem_u32(xs + n), peer) + off;
-    rb0 = cluster_addr(cta_smem_u32(&xbar[0]), peer);
-    rb1 = cluster_addr(cta_smem_u32(&xbar[1]), peer);
-  }
-
-  int consumed = len;
-  for (int k = 0; has_rows && k < len; ++k) {
-    const int j = j0 + k;
-    const int st = k % kRing;
-    bool ok = true;
-    if (k >= 1) ok = state_wait(&xbar[k & 1], (uint32_t)(((k - 1) >> 1) & 1));
-    if (ok) ok = ring_wait(&full[st], (uint32_t)((k / kRing) & 1));
-    if (!ok) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) {
-      consumed = k;
-      break;
-    }
-    if (tid == 0) {
-      if (k >= 1 && k + 2 <= len - 1) arm_tx(&xbar[k & 1], state_bytes);   // x_{k+2}
-      if (issued < len) issue(issued++);   // stage (k-1) % kRing, read during step k-1
-    }
-    const AT* x = xs + (k & 1) * n;
-    const MT* Aj = ring + st * stage_elems;
-    AT acc = 0;
-    if (active)
-      for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
-    // lanes l and l ^ 16 hold the same row (rpc = 16)
-    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-    if (lane < rpc) red[warp * rpc + lane] = acc;
-    __syncthreads();
-    if (warp == 0) {
-      const int rr = lane & (rpc - 1), half = lane >> 4;
-      AT s = 0;
-      for (int w = half * (nw >> 1); w < (half + 1) * (nw >> 1); ++w) s += red[w * rpc + rr];
-      s += __shfl_xor_sync(0xffffffffu, s, 16);
-      const bool own = lane < rpc && my_row < n;
-      if (own) {
-        const AT vj = a.v_double ? (AT)vring[st * rpc + rr]
-                                 : (AT)reinterpret_cast<const MT*>(vring + st * rpc)[rr];
-        s += vj;
-      }
-      // x_{k+1} to every CTA that owns rows (not sent after the last step)
-      if (k + 1 < len) {
-        AT v8[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v8[i] = __shfl_sync(0xffffffffu, s, half_rows + i);
-        const bool odd = (k + 1) & 1;
-        if (sender) send_rows(v8, odd ? rx1 : rx0, odd ? rb1 : rb0);
-      }
-      if (own) {
-        const int64_t o = (int64_t)(j + 1) * n + my_row;
-        const double out = (double)s + (a.add ? aring[st * rpc + rr] : 0.0);
-        if (a.states) a.states[o] = out;
-        if (a.yT && j == a.S - 1) a.yT[my_row] = out;
-        if (a.finals && k == len - 1) a.finals[(int64_t)q * n + my_row] = (double)s;
-      }
-    }
-    // red and the stage slots are next written after the barrier that opens
-    // the next step, which warp 0 reaches only when it is done with them
-  }
-  if (abort_flag && tid == 0) {
-    record_status(status, NV_ETIMEOUT);
-    for (int kk = min(consumed, issued); kk < issued; ++kk)   // copies in flight (bounded waits)
-      ring_wait(&full[kk % kRing], (uint32_t)((kk / kRing) & 1));
-  }
-  cl.sync();   // no CTA leaves while another may still address its shared memory
+  cluster_chain_run<MT, AT>(&tmA, a, status, (int)(blockIdx.x / cg::this_cluster().num_blocks()),
+                            ChainNoHooks{});
 }
 
 // acc[0..VEC) += (the VEC map entries in t) * xc, for one column of a tile:
@@ -923,9 +676,9 @@ static nv_status chain_encode_fn(EncodeTiledFnC* out) {
 // TMA-fed chains: 16-CTA clusters, 16 rows per CTA (d <= 256, d % 4 == 0,
 // 16-byte aligned matrices and strides).  NV_ENOTSUP if the shape or device
 // does not allow it (the caller then takes the register-prefetch kernel).
-static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStream_t s, int* status) {
+nv_status chain_tma_prepare(const ChainsArgs& args_in, bool f64, CUtensorMap* tmap, size_t* smem) {
   const int n = args_in.n;
-  const int block = 256, csize = 16, rpc = kChainRpc;
+  const int block = 256, rpc = kChainRpc;
   const size_t esz = f64 ? 8 : 4;
   if (n > 256 || n < 64 || n % 16 != 0) return NV_ENOTSUP;
   if (((uintptr_t)args_in.A % 16) || ((args_in.a_stride * esz) % 16)) return NV_ENOTSUP;
@@ -935,20 +688,28 @@ static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStre
   EncodeTiledFnC enc = nullptr;
   nv_status st = chain_encode_fn(&enc);
   if (st != NV_OK) return st;
-  CUtensorMap tmap;
   const cuuint64_t gdim[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)args_in.S};
   const cuuint64_t gstride[2] = {(cuuint64_t)n * esz, (cuuint64_t)args_in.a_stride * esz};
   const cuuint32_t box[3] = {(cuuint32_t)rpc, (cuuint32_t)n, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult cr = enc(&tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+  CUresult cr = enc(tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                     const_cast<void*>(args_in.A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return NV_ENOTSUP;
+  *smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc + esz * (2 * (size_t)n + block) +
+          8 * (kRing + 2) + 16;
+  return NV_OK;
+}
+
+static nv_status launch_chains_tma(const ChainsArgs& args_in, bool f64, cudaStream_t s, int* status) {
+  const int block = 256, csize = 16, rpc = kChainRpc;
+  CUtensorMap tmap;
+  size_t smem = 0;
+  nv_status st = chain_tma_prepare(args_in, f64, &tmap, &smem);
+  if (st != NV_OK) return st;
   const void* fn = f64 ? (const void*)affine_chains_tma_kernel<double, double>
                        : (const void*)affine_chains_tma_kernel<float, float>;
-  const size_t smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc +
-                      esz * (2 * (size_t)n + block) + 8 * (kRing + 2) + 16;
   if ((st = nv_cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                           "cluster size attribute")) != NV_OK)
     return st;

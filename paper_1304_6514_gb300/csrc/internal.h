@@ -86,6 +86,12 @@ struct TileChainExtra {
 // Bytes of the d > 512 chain's partial-sum scratch (in the maps workspace).
 size_t tile_chain_ring_scratch(int n, int ncb, int value_bytes);
 size_t tile_chain_scratch_bytes(int prec, int n, int sms);
+// Pipelined refinement of the heat equations over float32 maps (wavefront.cu):
+// chains and defects of all passes in one cooperative launch; NV_ENOTSUP when
+// the shape or device does not fit it.  scratch: heat_wavefront_scratch_bytes.
+size_t heat_wavefront_scratch_bytes(int n, int S, int passes);
+nv_status launch_heat_wavefront(nv_maps* M, const double* y0, double* yT, double* lambdas, int passes,
+                                void* scratch, cudaStream_t s);
 nv_status launch_tile_chain(const nv_maps* M, const double* y0, double* yT, double* lambdas,
                             const TileChainExtra* ex, cudaStream_t s);
 // float64 defects of the advection-diffusion maps: d_j = g^j(lam_j) - lam_{j+1}
@@ -125,5 +131,6 @@ struct nv_tunables {
   int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
   int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
   int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring
+  int refine_schedule;     // heat NV_FP32_REFINE: 0 auto (pipelined), 1 sequential passes
 };
 extern nv_tunables g_tune;

@@ -83,20 +83,25 @@ nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* 
   if (M->rhs_kind != NV_RHS_ADVDIFF2D && !heat)
     return nv_fail(NV_ENOTSUP, "chain refinement is built for the heat equations and advection-diffusion");
   const int n = M->dim, S = M->S;
+  const int dflt = M->prec == NV_BF16_REFINE ? 2 : 1;
+  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : dflt);
+  const bool pipelined = heat && passes >= 1 && g_tune.refine_schedule != 1;
   const size_t states = (size_t)(S + 1) * n;
-  // two state sets, the defects, one zero vector
-  const size_t need = sizeof(double) * (2 * states + (size_t)S * n + (size_t)n);
+  // two state sets, the defects, one zero vector (or the pipelined passes' scratch)
+  size_t need = sizeof(double) * (2 * states + (size_t)S * n + (size_t)n);
+  if (pipelined) need = std::max(need, heat_wavefront_scratch_bytes(n, S, passes));
   nv_status st = ensure_scratch(M, need, s);
   if (st != NV_OK) return st;
+  if (pipelined) {   // all passes in one launch where they fit, else one after another
+    st = launch_heat_wavefront(M, y0, yT, lambdas, passes, M->scan_ws, s);
+    if (st != NV_ENOTSUP) return st;
+  }
   double* lt = static_cast<double*>(M->scan_ws);
   double* lt2 = lt + states;
   double* d = lt2 + states;
+  if (heat) return heat_chain_refine(M, y0, yT, lambdas, lt, lt2, d, passes, s);
   double* zero = d + (size_t)S * n;
   if ((st = nv_cuda_check(cudaMemsetAsync(zero, 0, sizeof(double) * n, s), "zero state")) != NV_OK) return st;
-
-  const int dflt = M->prec == NV_BF16_REFINE ? 2 : 1;
-  const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : dflt);
-  if (heat) return heat_chain_refine(M, y0, yT, lambdas, lt, lt2, d, passes, s);
   // approximate boundary states over the bfloat16 maps
   double* cur = lt;
   if ((st = launch_tile_chain(M, y0, passes == 0 ? yT : nullptr, passes == 0 && lambdas ? lambdas : cur,

@@ -176,6 +176,71 @@ def test_heat_fp32_refined_small(n, S):
     assert rel_l2(lam, olam) <= 1e-9
 
 
+def _refine_both_schedules(torch, w, passes, rhs_name="heat1d"):
+    """Boundary states and final state of NV_FP32_REFINE with `passes` passes,
+    pipelined (tunable 10 = 0) and one pass after another (10 = 1)."""
+    r = nvp.rhs(rhs_name, w.dim, w.params if rhs_name == "heat1d" else ())
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                 nvp.steps("rk4", w.dt, w.steps_per_slice, "fp32_refine"))
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    out = {}
+    try:
+        nvp.tune_set(5, passes)
+        for sched in (1, 0):
+            nvp.tune_set(10, sched)
+            yT = torch.empty_like(y0)
+            lam = torch.full((w.S + 1, w.dim), float("nan"), dtype=torch.float64, device="cuda")
+            nvp.compose(maps, y0, yT, lambdas=lam)
+            nvp.maps_check(maps)
+            out[sched] = (yT.cpu(), lam.cpu())
+    finally:
+        nvp.tune_set(5, 0)
+        nvp.tune_set(10, 0)
+        maps.destroy()
+    return out
+
+
+@pytest.mark.parametrize("passes", [1, 2, 3])
+def test_heat_fp32_refine_pipelined_matches_sequential_full_size(passes):
+    """n = 256, S = 1024: the pipelined schedule (approximate chain, defects
+    and every correction chain concurrently in one cooperative launch) gives
+    the sequential passes' boundary states and final state bit for bit, and
+    two or more passes reach the float64 method's error level."""
+    torch = need_gpu()
+    o = _full_oracle()
+    out = _refine_both_schedules(torch, o["w"], passes)
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    err = rel_l2(out[0][0].numpy(), o["serial"])
+    print(passes, "passes, pipelined, final state relative error", err)
+    assert err <= (1e-7 if passes == 1 else 5e-13)
+
+
+@pytest.mark.parametrize("n,S,passes,rhs_name", [(64, 7, 2, "heat1d"), (96, 2, 1, "heat1d"),
+                                                 (128, 1, 3, "heat1d"), (256, 9, 2, "heat1d"),
+                                                 (64, 33, 1, "heat1d_varcoef")])
+def test_heat_fp32_refine_pipelined_small(n, S, passes, rhs_name):
+    """Shapes of the pipelined schedule: two, four and eight rows per lane in
+    the defect warps, chains shorter than the number of passes, the
+    variable-coefficient equation.  Bit-identical to the sequential passes and
+    within 1e-9 of the oracle's composition of its own maps."""
+    torch = need_gpu()
+    dt = 2.0 / (4.0 * 1.25 * (n + 1) ** 2)       # stable for diffusion coefficients up to 1.25
+    if rhs_name == "heat1d":
+        w = workloads.heat1d(n=n, S=S, T=S * 3 * dt, dt=dt)
+    else:
+        w = workloads.Workload("v", "heat1d_varcoef", n, 0.0, S * 3 * dt, S, "rk4", dt, 0, "affine",
+                               y0=np.sin(np.pi * nv.heat1d_grid(n)))
+    out = _refine_both_schedules(torch, w, passes, rhs_name)
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    m = nv.workload_steps(w)
+    fi, fh = nv.workload_rhs(w, True), nv.workload_rhs(w, False)
+    oA, ob = nv.build_affine(fi, fh, "rk4", w.t0, w.T, w.S, m, n)
+    olam = nv.compose_affine(oA, ob, w.y0)
+    assert rel_l2(out[0][1].numpy(), olam) <= 1e-9
+
+
 def test_heat_serial_fine_gpu():
     torch = need_gpu()
     w = workloads.heat1d(n=40, S=7, T=0.003, dt=1e-4)
