@@ -29,6 +29,17 @@ __device__ __forceinline__ void halos(const T* v, int lane, int n, T& left, T& r
   if (lane == 31 || (lane + 1) * R >= n) right = (T)0;
 }
 
+// Halo policy of the literal RK4 step: one warp holds the whole vector (lane
+// l: rows l*R .. l*R+R-1).
+struct WarpHalo {
+  int lane;
+  __device__ int gl() const { return lane; }   // lane index within the whole vector
+  template <int R, typename T>
+  __device__ __forceinline__ void operator()(const T* v, int n, T& left, T& right) {
+    halos<R>(v, lane, n, left, right);
+  }
+};
+
 // One Horner-form RK4 step of y' = cdx * lap(y), lap the [1,-2,1] stencil.
 template <int R, typename T>
 __device__ __forceinline__ void heat_horner_step(T* y, T* v, T cdx, T h, int lane, int n) {
@@ -60,12 +71,13 @@ __device__ __forceinline__ void heat_horner_step(T* y, T* v, T cdx, T h, int lan
 
 // Right-hand side f(t, z) = a(t) cdx lap(z) + g(t) sx at one stage, folded into
 // the stage updates of the literal RK4 step.
-template <int R, typename T>
+template <int R, typename T, typename H>
 __device__ __forceinline__ void heat_stage(const T* y, T* z, T* acc, T a_cdx, T g, const T* sx,
-                                           bool forced, T zc, T accw, bool first, int lane,
+                                           bool forced, T zc, T accw, bool first, H& halo,
                                            int n) {
+  const int lane = halo.gl();
   T prev, right;
-  halos<R>(z, lane, n, prev, right);
+  halo.template operator()<R>(z, n, prev, right);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const T cur = z[i];
@@ -137,21 +149,22 @@ __device__ __forceinline__ StageCoefs<T> step_coefs(const HalfStepCoefs& hc, int
 }
 
 // Literal RK4 step (stage times t, t+h/2, t+h) for the heat right-hand side.
-template <int R, typename T>
+template <int R, typename T, typename H>
 __device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double h, const StageCoefs<T>& c,
-                                              const T* sx, bool forced, int lane, int n) {
+                                              const T* sx, bool forced, H& halo, int n) {
+  const int lane = halo.gl();
   const T hh = (T)(0.5 * h), hT = (T)h;
   const T g0 = forced ? c.g0 : (T)0, gh = forced ? c.gh : (T)0, g1 = forced ? c.g1 : (T)0;
   const T a0 = c.a0, ah = c.ah, a1 = c.a1;
 #pragma unroll
   for (int i = 0; i < R; ++i) z[i] = y[i];
-  heat_stage<R>(y, z, acc, a0, g0, sx, forced, hh, (T)0, true, lane, n);
-  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hh, (T)2, false, lane, n);
-  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hT, (T)2, false, lane, n);
+  heat_stage<R>(y, z, acc, a0, g0, sx, forced, hh, (T)0, true, halo, n);
+  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hh, (T)2, false, halo, n);
+  heat_stage<R>(y, z, acc, ah, gh, sx, forced, hT, (T)2, false, halo, n);
   // stage 4: k4 = f(t+h, z); y <- y + h/6 (acc + k4)
   {
     T prev, right;
-    halos<R>(z, lane, n, prev, right);
+    halo.template operator()<R>(z, n, prev, right);
     const T h6 = (T)(h / 6.0);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -172,10 +185,63 @@ __device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double h, cons
   }
 }
 
+template <int R, typename T>
+__device__ __forceinline__ void heat_rk4_step(T* y, T* z, T* acc, double h, const StageCoefs<T>& c,
+                                              const T* sx, bool forced, int lane, int n) {
+  WarpHalo halo{lane};
+  heat_rk4_step<R>(y, z, acc, h, c, sx, forced, halo, n);
+}
+
+// One RK4 step of u' = a(t) cdx T u + g(t) s in nine-point form.  T (the
+// [1,-2,1] stencil with zero ends) has s = sin(pi x) as an eigenvector, T s =
+// lam s with lam = -4 sin^2(pi/(2(n+1))), and the step's operators a(.) cdx T
+// all commute, so the classical RK4 step is exactly Q(T) u + phi s: Q the
+// degree-4 polynomial of the four stages in T, with the stage multipliers u0,
+// uh, u1 = h a(t) cdx at t, t+h/2, t+h, written as the weights c0..c4 of a
+// symmetric nine-point stencil; phi the same four stages run on the forcing's
+// coefficient along s.  (With a constant, Q is the Taylor polynomial of
+// degree 4 of the build's nine-point form.)  The stencil is applied in
+// difference form, y + sum_k c_k (y_{i-k} + y_{i+k} - 2 y_i): the weights
+// c_1..c_4 act on second differences, as the literal stages do, so that
+// rounding the weights cannot change the step's action on smooth vectors.
+// (With c_0 = 1 - 2 (c_1 + .. + c_4) stored as a rounded weight of its own,
+// the smooth mode's factor per step differs from the exact one by about an
+// ulp, and over the 10 240 steps of the heat workload the fine solve drifts
+// by 7e-13 from the literal stages; in difference form the two agree to
+// 4e-16.)
+struct Rk4Poly9 {
+  double c1, c2, c3, c4, phi;
+};
+
+__device__ __forceinline__ Rk4Poly9 rk4_poly9(double h, double u0, double uh, double u1, double g0, double gh,
+                                              double g1, double lam) {
+  const double q1 = (u0 + 4.0 * uh + u1) / 6.0;
+  const double q2 = uh * (u0 + uh + u1) / 6.0;
+  const double q3 = uh * uh * (u0 + u1) / 12.0;
+  const double q4 = u0 * uh * uh * u1 / 24.0;
+  Rk4Poly9 p;
+  p.c1 = q1 - 4.0 * q2 + 15.0 * q3 - 56.0 * q4;
+  p.c2 = q2 - 6.0 * q3 + 28.0 * q4;
+  p.c3 = q3 - 8.0 * q4;
+  p.c4 = q4;
+  const double k1 = g0;
+  const double k2 = gh + 0.5 * uh * lam * k1;
+  const double k3 = gh + 0.5 * uh * lam * k2;
+  const double k4 = g1 + u1 * lam * k3;
+  p.phi = h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+  return p;
+}
+
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
 // Float64 defect of slice j (the residual correction the Conclusion
-// proposes): d_j = g^j(lt_j) - lt_{j+1}, one literal RK4 fine solve of the
-// forced equation from lt_j over the slice.  One warp; lane l holds rows
-// l*R .. l*R+R-1.
+// proposes): d_j = g^j(lt_j) - lt_{j+1}, one RK4 fine solve of the forced
+// equation from lt_j over the slice.  One warp; lane l holds rows
+// l*R .. l*R+R-1.  Where every lane holds 4 to 8 whole rows (4 <= R <= 8,
+// n % R == 0) the steps take the nine-point form (13 instead of 24 float64
+// operations per row and step: the stencil's weights and phi for steps
+// i0 .. i0+14 are computed one step per lane and broadcast by shuffle);
+// otherwise the literal stages.
 template <int R>
 __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const double* lt, double* d, int64_t j,
                                                   int lane) {
@@ -183,7 +249,7 @@ __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const doubl
   const double dx = 1.0 / (double)(n + 1);
   const double cdx = a.kappa / (dx * dx);
   const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
-  double y[R], z[R], acc[R], sx[R];
+  double y[R], sx[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = lane * R + i;
@@ -191,10 +257,67 @@ __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const doubl
     sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
   }
   HalfStepCoefs hc{};
-  for (int64_t i = 0; i < a.m; ++i) {
-    const int64_t i0 = i - (i % 15);
-    if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
-    heat_rk4_step<R>(y, z, acc, a.h, step_coefs<double>(hc, i, i0, cdx), sx, true, lane, n);
+  // (R = 16, d > 256: the nine-point halo would not fit the registers)
+  if (R >= 4 && R <= 8 && n % R == 0) {
+    const int last = n / R - 1;                   // lane holding row n-1
+    // 2 cos(pi/(n+1)) - 2 = -4 sin^2(pi/(2(n+1))), the second form without
+    // the cancellation that would cost the first one ~1e-12 relative accuracy
+    const double sh = sin(M_PI / (2.0 * (double)(n + 1)));
+    const double lam = -4.0 * sh * sh;
+    Rk4Poly9 pl{};
+    for (int64_t i = 0; i < a.m; ++i) {
+      const int64_t i0 = i - (i % 15);
+      if (i == i0) {                              // lane l: step i0 + l (l < 15)
+        hc = half_step_coefs(a, Tj, i0, lane);
+        const int l2 = min(2 * lane, 28);
+        const double g0 = shfl_d(hc.g, l2), gh = shfl_d(hc.g, l2 + 1), g1 = shfl_d(hc.g, l2 + 2);
+        const double a0 = shfl_d(hc.a, l2), ah = shfl_d(hc.a, l2 + 1), a1 = shfl_d(hc.a, l2 + 2);
+        pl = rk4_poly9(a.h, a.h * (a0 * cdx), a.h * (ah * cdx), a.h * (a1 * cdx), g0, gh, g1, lam);
+      }
+      const int src = (int)(i - i0);
+      const double c1 = shfl_d(pl.c1, src), c2 = shfl_d(pl.c2, src);
+      const double c3 = shfl_d(pl.c3, src), c4 = shfl_d(pl.c4, src), phi = shfl_d(pl.phi, src);
+      double e[R + 8];                            // rows lane*R-4 .. lane*R+R+3
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        e[q] = __shfl_up_sync(0xffffffffu, y[R - 4 + q], 1);
+        e[R + 4 + q] = __shfl_down_sync(0xffffffffu, y[q], 1);
+      }
+      if (lane == 0) {                            // rows -4..-1 = -y2, -y1, -y0, 0 (odd reflection)
+        e[0] = -y[2];
+        e[1] = -y[1];
+        e[2] = -y[0];
+        e[3] = 0.0;
+      }
+      if (lane == last) {                         // rows n..n+3 = 0, -y_{n-1}, -y_{n-2}, -y_{n-3}
+        e[R + 4] = 0.0;
+        e[R + 5] = -y[R - 1];
+        e[R + 6] = -y[R - 2];
+        e[R + 7] = -y[R - 3];
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < R; ++i2) e[i2 + 4] = y[i2];
+#pragma unroll
+      for (int i2 = 0; i2 < R; ++i2) {
+        const double yc = e[i2 + 4];
+        double acc = fma(phi, sx[i2], yc);
+        acc = fma(c4, fma(-2.0, yc, e[i2] + e[i2 + 8]), acc);
+        acc = fma(c3, fma(-2.0, yc, e[i2 + 1] + e[i2 + 7]), acc);
+        acc = fma(c2, fma(-2.0, yc, e[i2 + 2] + e[i2 + 6]), acc);
+        y[i2] = fma(c1, fma(-2.0, yc, e[i2 + 3] + e[i2 + 5]), acc);
+      }
+      if (lane > last) {
+#pragma unroll
+        for (int i2 = 0; i2 < R; ++i2) y[i2] = 0.0;
+      }
+    }
+  } else {
+    double z[R], acc[R];
+    for (int64_t i = 0; i < a.m; ++i) {
+      const int64_t i0 = i - (i % 15);
+      if (i == i0) hc = half_step_coefs(a, Tj, i0, lane);
+      heat_rk4_step<R>(y, z, acc, a.h, step_coefs<double>(hc, i, i0, cdx), sx, true, lane, n);
+    }
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256, 1) heat_wavefront_kernel(const __grid_con
                                     WaveHooks{&w, cluster, &ready});
     return;
   }
+  // defect workers: kWaveWorkerWarps independent warps per CTA, one slice each
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp >= kWaveWorkerWarps) return;
   const int P = w.nchains - 1;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256, 1) heat_wavefront_kernel(const __grid_con
     const int c = 1 + (int)(it % P);
     const int64_t j = it / P;
     const unsigned* cprev = w.cnt + (size_t)(c - 1) * (w.S + 1);
-    bool ok = wave_wait(cprev + j, (unsigned)w.owners, w) && wave_wait(cprev + j + 1, (unsigned)w.owners, w);
+    const bool ok = wave_wait(cprev + j, (unsigned)w.owners, w) && wave_wait(cprev + j + 1, (unsigned)w.owners, w);
     if (!__all_sync(0xffffffffu, ok)) break;
     heat_defect_slice<R>(w.heat, w.lt[c - 1], w.d[c], j, lane);
     __syncwarp();
@@ -171,7 +172,7 @@ nv_status launch_heat_wavefront(nv_maps* M, const double* y0, double* yT, double
   const int n = M->dim, S = M->S;
   if (passes < 1 || passes >= kWaveMaxChains || M->prec != NV_FP32_REFINE) return NV_ENOTSUP;
   if (M->rhs_kind != NV_RHS_HEAT1D && M->rhs_kind != NV_RHS_HEAT1D_VARCOEF) return NV_ENOTSUP;
-  const int R = n <= 64 ? 2 : (n <= 128 ? 4 : 8);
+  const int R = n <= 64 ? 2 : (n <= 128 ? 4 : 8);   // rows per lane of a defect warp
   if (R * 32 < n) return NV_ENOTSUP;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char* p = static_cast<char*>(scratch);
@@ -223,6 +224,9 @@ nv_status launch_heat_wavefront(nv_maps* M, const double* y0, double* yT, double
   size_t smem = 0;
   nv_status st = chain_tma_prepare(w.chain[passes > 0 ? 1 : 0], false, &tmap, &smem);
   if (st != NV_OK) return st;
+  // more than half an SM's shared memory: one CTA per SM, so no defect team
+  // shares an SM with a chain's CTA
+  smem = std::max(smem, (size_t)116 * 1024);
   const void* fn = R == 2 ? (const void*)heat_wavefront_kernel<2>
                  : R == 4 ? (const void*)heat_wavefront_kernel<4>
                           : (const void*)heat_wavefront_kernel<8>;
