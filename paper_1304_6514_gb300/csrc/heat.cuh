@@ -17,7 +17,15 @@ struct HeatArgs {
   double kappa, amp;     // NV_RHS_HEAT1D parameters
   int varcoef;           // NV_RHS_HEAT1D_VARCOEF
   double poly9[5];       // nine-point form of the RK4 step: weights c_0..c_4
+  float poly9f[5];       // the same rounded to float32, with c_0 + 2 (c_1 + .. + c_4) = 1
 };
+
+template <typename T>
+__device__ __forceinline__ T poly9_weight(const HeatArgs& a, int k);
+template <>
+__device__ __forceinline__ double poly9_weight<double>(const HeatArgs& a, int k) { return a.poly9[k]; }
+template <>
+__device__ __forceinline__ float poly9_weight<float>(const HeatArgs& a, int k) { return a.poly9f[k]; }
 
 // Neighbour values of a lane-blocked vector: left of row lane*R, right of row
 // lane*R+R-1 (zero at the Dirichlet boundary and past the last row).
