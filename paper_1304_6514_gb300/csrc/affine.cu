@@ -706,11 +706,35 @@ static AdvArgs adv_args(const nv_maps* M) {
   a.w_yp = nu / (dx * dx);
   a.w_0 = -4.0 * nu / (dx * dx) - ax / dx - ay / dx;
   const double w[5] = {a.w_xm, a.w_xp, a.w_ym, a.w_yp, a.w_0};
-  for (int st = 0; st < 4; ++st)
+  for (int st = 0; st < 4; ++st) {
     for (int q = 0; q < 5; ++q) {
       a.cw64[st][q] = (a.h / (4 - st)) * w[q];
       a.cw32[st][q] = (float)a.cw64[st][q];
     }
+    // The periodic operator maps constants to zero (its weights sum to 0), so
+    // the mean is conserved; the float32 stage weights rounded one by one sum
+    // to about 1e-9 instead, and every stage then scales the mean by that (a
+    // float32 fine integration of the 5 120 steps drifts by 1.4e-5 from the
+    // float64 one that way, by 5e-7 without).  So the centre weight is minus
+    // the exact sum of the other four, which must itself be a float32: the
+    // sum of four float32 values is exact in double, and the last neighbour
+    // weight moves by single ulps (at most a few) until that sum rounds to
+    // float32 exactly.  (The composed float32 maps err by 8.6e-5 either way:
+    // there the maps' own float32 entries and the chain's sums dominate.)
+    float* c = a.cw32[st];
+    const float base = c[3];
+    for (int k = 0; k < 64; ++k) {
+      const int d = (k + 1) / 2 * ((k & 1) ? 1 : -1);   // 0, +1, -1, +2, -2, ... ulps
+      float c3 = base;
+      for (int i = 0; i < (d > 0 ? d : -d); ++i) c3 = nextafterf(c3, d > 0 ? INFINITY : -INFINITY);
+      const double s4 = (double)c[0] + (double)c[1] + (double)c[2] + (double)c3;
+      if ((double)(float)s4 == s4) {
+        c[3] = c3;
+        c[4] = -(float)s4;
+        break;
+      }
+    }
+  }
   return a;
 }
 
