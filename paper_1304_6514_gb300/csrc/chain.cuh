@@ -127,6 +127,13 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
                                                   int q, const Hooks& hooks) {
   constexpr int rpc = kChainRpc;
   cg::cluster_group cl = cg::this_cluster();
+  // The exchange addresses 16 peer CTAs of the cluster: a launch that is not
+  // in 16-CTA clusters (whatever the cause) records an error and touches no
+  // cluster address.  Uniform over the cluster, so no CTA waits for another.
+  if (cl.num_blocks() != 16 || blockDim.x != 256) {
+    if (threadIdx.x == 0) record_status(status, NV_ECUDA);
+    return;
+  }
   const unsigned rank = cl.block_rank();
   extern __shared__ __align__(128) unsigned char ring_smem[];
   const int n = a.n;

@@ -128,6 +128,16 @@ struct WaveHooks {
 template <int R>
 __global__ void __launch_bounds__(256, 1) heat_wavefront_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ WavefrontArgs w) {
+  // the roles need 16-CTA clusters and at least one worker cluster; any
+  // other launch shape records an error and returns at once (uniformly)
+  if (cg::this_cluster().num_blocks() != 16 || gridDim.x % 16 != 0 || gridDim.x < 16u * (w.nchains + 1) ||
+      blockDim.x != 256) {
+    if (threadIdx.x == 0) {
+      record_status(w.chain[0].status, NV_ECUDA);
+      atomicExch(w.abort, 1u);
+    }
+    return;
+  }
   const int cluster = (int)(blockIdx.x / 16);
   if (cluster < w.nchains) {
     __shared__ int ready;
