@@ -316,7 +316,7 @@ def gpu_peak_probe(torch):
 # DRAM bytes (read + write) per unit of output from one ncu capture of each
 # dominant kernel, scaled to the bench's launch by the units it writes (the
 # captures ran smaller cases of the same kernels; see profiles/):
-#   heat FP64 build (nine-point form), S = 512 capture: 206.55 MB for 131 072 columns
+#   heat FP64 build (nine-point form), S = 512 capture: 207.06 MB for 131 072 columns
 #   advection-diffusion FP32 build, S = 8 capture: 475.04 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 503.0 MB for 561 987 584 table bytes
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
@@ -325,7 +325,7 @@ def gpu_peak_probe(torch):
 NCU_TRAFFIC_PER_UNIT = {
     "affine_chain_tile_kernel<float,float>": (547.89e6 / 8, "profiles/advdiff_chains_d4096_S512.md"),
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
-    "heat_poly9_kernel<double,8,0>": (206.55e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
+    "heat_poly9_kernel<double,8,0>": (207.06e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
