@@ -116,6 +116,7 @@ __device__ __forceinline__ void send_rows(const double* v, uint32_t addr, uint32
 // it by a CTA barrier; before_state0 / after_state0: thread 0 of the CTA that
 // writes states[0], around that write.
 struct ChainNoHooks {
+  static constexpr bool kTopBarrierFree = true;   // the step needs no barrier before its product
   __device__ bool before_issue(int) const { return true; }
   __device__ void stored(int) const {}
   __device__ bool before_state0() const { return true; }
@@ -143,9 +144,9 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
   double* vring = reinterpret_cast<double*>(ring + kRing * stage_elems);
   double* aring = vring + kRing * rpc;
   AT* xs = reinterpret_cast<AT*>(aring + kRing * rpc);                 // two state buffers
-  AT* red = xs + 2 * n;                                                // per-warp row partials
+  AT* red = xs + 2 * n;                                                // per-warp row partials, x2
   uint64_t* full = reinterpret_cast<uint64_t*>(
-      ((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);
+      ((uintptr_t)(red + 2 * blockDim.x) + 7) & ~(uintptr_t)7);
   uint64_t* xbar = full + kRing;                                       // state buffers 0, 1
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -247,12 +248,18 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     bool ok = true;
     if (k >= 1) ok = state_wait(&xbar[k & 1], (uint32_t)(((k - 1) >> 1) & 1));
     if (ok) ok = ring_wait(&full[st], (uint32_t)((k / kRing) & 1));
+    // No block barrier is needed here: every thread waits on the barriers of
+    // what it reads itself.  (The reduction buffer alternates by step; a ring
+    // slot is refilled only after the reduction barrier of the following step;
+    // and state buffer k & 1 cannot receive x_{k+2} before this CTA has sent
+    // its rows of x_{k+1}, which warp 0 does after that barrier, when every
+    // warp here has read x_k.)  A failed wait is acted on at the reduction
+    // barrier.  Measured on one GB300: without it a float32 step is 7 % faster,
+    // a float64 step 1 % slower, and the pipelined refinement's chains, whose
+    // issuer runs hooks after the reduction barrier, 4 % slower: so it stays
+    // except for float32 chains without hooks.
     if (!ok) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) {
-      consumed = k;
-      break;
-    }
+    if constexpr (!(Hooks::kTopBarrierFree && sizeof(AT) == 4)) __syncthreads();
     if (tid == 0 && k >= 1 && k + 2 <= len - 1) arm_tx(&xbar[k & 1], state_bytes);   // x_{k+2}
     const AT* x = xs + (k & 1) * n;
     const MT* Aj = ring + st * stage_elems;
@@ -261,21 +268,26 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
       for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
     // lanes l and l ^ 16 hold the same row (rpc = 16)
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-    if (lane < rpc) red[warp * rpc + lane] = acc;
+    AT* redk = red + (k & 1) * blockDim.x;
+    if (lane < rpc) redk[warp * rpc + lane] = acc;
     __syncthreads();
+    if (abort_flag) {
+      consumed = k;
+      break;
+    }
     // stage k+2 into slot (k-1) % kRing, which every thread finished with in
     // step k-1
     if (issuer && issued < len) {
       if (issue(issued)) ++issued;
       else abort_flag = 1;                 // seen at the next step's barrier
     }
-    // warp 0 stored its rows of states[j0 + k] in step k - 1, before the
-    // barrier that opened this step
+    // warp 0 stored its rows of states[j0 + k] in step k - 1, before this
+    // step's reduction barrier
     if (issuer && k >= 1) hooks.stored(j0 + k);
     if (warp == 0) {
       const int rr = lane & (rpc - 1), half = lane >> 4;
       AT s = 0;
-      for (int w = half * (nw >> 1); w < (half + 1) * (nw >> 1); ++w) s += red[w * rpc + rr];
+      for (int w = half * (nw >> 1); w < (half + 1) * (nw >> 1); ++w) s += redk[w * rpc + rr];
       s += __shfl_xor_sync(0xffffffffu, s, 16);
       const bool own = lane < rpc && my_row < n;
       if (own) {
@@ -299,8 +311,8 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
         if (a.finals && k == len - 1) a.finals[(int64_t)q * n + my_row] = (double)s;
       }
     }
-    // red is next written after the barrier that opens the next step, which
-    // warp 0 reaches only when it is done with it
+    // this step's reduction buffer is next written two steps on, after the
+    // next reduction barrier, which warp 0 reaches only when it is done with it
   }
   __syncthreads();
   if (has_rows && !abort_flag && issuer && len >= 1) hooks.stored(j0 + len);

@@ -697,7 +697,7 @@ nv_status chain_tma_prepare(const ChainsArgs& args_in, bool f64, CUtensorMap* tm
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return NV_ENOTSUP;
-  *smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc + esz * (2 * (size_t)n + block) +
+  *smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc + esz * (2 * (size_t)n + 2 * block) +
           8 * (kRing + 2) + 16;
   return NV_OK;
 }

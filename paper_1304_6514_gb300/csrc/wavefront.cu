@@ -85,6 +85,7 @@ __device__ __forceinline__ bool wave_wait(const unsigned* p, unsigned target, co
 constexpr int kWaveBatch = 32;
 
 struct WaveHooks {
+  static constexpr bool kTopBarrierFree = false;   // keep the step's first barrier (see chain.cuh)
   const WavefrontArgs* w;
   int c;
   int* ready;   // shared: defects of slices < *ready are known to be stored (the issuer)
