@@ -408,8 +408,14 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          cooperative launch, each a few slices behind the one it corrects,
  *          where 64 <= d <= 256, d % 16 == 0 and at most 3 passes), 1 the
  *          passes one after another.  Same arithmetic: identical results.
+ *   key 12: test hook, >= 0 (default 0): in the pipelined refinement the
+ *          defect of slice value - 1 of the first pass is computed but its
+ *          flag is never set, so the correction chain's bounded wait for it
+ *          runs out (~1 s): NV_ETIMEOUT is recorded in the maps' status word
+ *          (read by nv_maps_check), every role of the launch gives up, and
+ *          the context stays usable.  The paper has no counterpart.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9 and 10. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10 and 12. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

@@ -132,5 +132,6 @@ struct nv_tunables {
   int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
   int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring
   int refine_schedule;     // heat NV_FP32_REFINE: 0 auto (pipelined), 1 sequential passes
+  int test_withhold_defect;  // test hook: pipelined refinement never flags pass 1's defect of this slice + 1
 };
 extern nv_tunables g_tune;

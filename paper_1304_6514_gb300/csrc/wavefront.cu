@@ -49,6 +49,7 @@ struct WavefrontArgs {
   unsigned* dflag;                     // nchains x S: defect of pass c, slice j, stored
   unsigned* abort;                     // nonzero once any waiter gave up
   int nchains, S, owners;
+  int withhold;                        // test hook: the flag of pass 1, slice withhold - 1 is never set (0: off)
   HeatArgs heat;
 };
 
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(256, 1) heat_wavefront_kernel(const __grid_con
     if (!__all_sync(0xffffffffu, ok)) break;
     heat_defect_slice<R>(w.heat, w.lt[c - 1], w.d[c], j, lane);
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && !(c == 1 && j + 1 == w.withhold)) {
       __threadfence();
       atomicExch(w.dflag + (size_t)c * w.S + j, 1u);
     }
@@ -196,6 +197,7 @@ nv_status launch_heat_wavefront(nv_maps* M, const double* y0, double* yT, double
 
   WavefrontArgs w{};
   w.nchains = passes + 1;
+  w.withhold = g_tune.test_withhold_defect;
   w.S = S;
   w.owners = n / kChainRpc;
   w.heat = heat_args(M);

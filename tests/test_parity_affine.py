@@ -249,6 +249,49 @@ def test_heat_fp32_refine_pipelined_small(n, S, passes, rhs_name):
     assert rel_l2(out[0][1].numpy(), olam) <= 1e-9
 
 
+def test_pipelined_refinement_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection of the pipelined refinement without a GPU fault: a
+    test hook (tunable 12) keeps one defect's flag unset, so the correction
+    chain's bounded wait for it runs out; the launch records NV_ETIMEOUT, which
+    nv_maps_check reports, and every role gives up (the launch ends in about
+    a second).  The next composition on the same maps and context matches the
+    sequential passes bit for bit."""
+    torch = need_gpu()
+    import time
+    n, S = 128, 40
+    dt = 2.0 / (4.0 * 1.25 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=S * 3 * dt, dt=dt)
+    r = nvp.rhs("heat1d", w.dim, w.params)
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                 nvp.steps("rk4", w.dt, w.steps_per_slice, "fp32_refine"))
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    yT = torch.empty_like(y0)
+    try:
+        nvp.tune_set(5, 2)
+        nvp.tune_set(12, 6)                       # withhold pass 1's defect of slice 5
+        t0 = time.time()
+        nvp.compose(maps, y0, yT)
+        with pytest.raises(nvp.NvError) as exc:
+            nvp.maps_check(maps)
+        elapsed = time.time() - t0
+        assert exc.value.status == nvp.NV_ETIMEOUT
+        assert elapsed < 10.0
+        nvp.tune_set(12, 0)
+        out = {}
+        for sched in (0, 1):
+            nvp.tune_set(10, sched)
+            y = torch.empty_like(y0)
+            nvp.compose(maps, y0, y)
+            nvp.maps_check(maps)
+            out[sched] = y.cpu()
+        assert torch.equal(out[0], out[1])
+    finally:
+        nvp.tune_set(12, 0)
+        nvp.tune_set(10, 0)
+        nvp.tune_set(5, 0)
+        maps.destroy()
+
+
 def test_heat_serial_fine_gpu():
     torch = need_gpu()
     w = workloads.heat1d(n=40, S=7, T=0.003, dt=1e-4)
