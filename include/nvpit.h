@@ -414,8 +414,13 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          runs out (~1 s): NV_ETIMEOUT is recorded in the maps' status word
  *          (read by nv_maps_check), every role of the launch gives up, and
  *          the context stays usable.  The paper has no counterpart.
+ *   key 13: test hook, >= 0 (default 0): the d > 512 ring chain's first CTA
+ *          never stores its partial sums of step value - 1, so the CTAs that
+ *          need them give up after their bounded wait (~1 s) and record
+ *          NV_ETIMEOUT; the others run out their loops; the context stays
+ *          usable.  The paper has no counterpart.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10 and 12. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12 and 13. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

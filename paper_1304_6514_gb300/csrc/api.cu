@@ -19,7 +19,7 @@ nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, 
 nv_status launch_serial_wave(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 int64_t wave_aux_elems(int d);
 
-nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
 static thread_local char g_err[512] = "";
 
@@ -456,6 +456,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 12:
       if (value < 0) return nv_fail(NV_EINVAL, "withheld slice is 0 (off) or slice + 1");
       g_tune.test_withhold_defect = value;
+      break;
+    case 13:
+      if (value < 0) return nv_fail(NV_EINVAL, "skipped step is 0 (off) or step + 1");
+      g_tune.test_skip_partials = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }

@@ -38,6 +38,7 @@ struct AffineChainArgs {
   const double* vadd;   // optional: v_j added to slice j's product (S x n)
   const double* base;   // optional: added to every state written (S+1 x n)
   int col0_off;         // 1: drop column 0 (b_j) of the maps
+  int test_skip;        // ring chain test hook: CTA 0 never stores the partials of step test_skip - 1
 };
 
 // Loads issued ahead of the barrier: up to kPre columns per thread.
@@ -631,6 +632,7 @@ __global__ void __launch_bounds__(kTileConsumers + 32, 1)
         for (int v = 0; v < VEC; ++v) acc[v] += (AT)a.vadd[(int64_t)k * n + row0 + v];
       }
       unsigned long long* dst = part + (size_t)(k % kTagBuffers) * buf_words + ((size_t)cb * n + row0) * W;
+      if (!(a.test_skip == k + 1 && blockIdx.x == 0))
 #pragma unroll
       for (int v = 0; v < VEC; ++v) {
         unsigned long long w[W];
@@ -884,6 +886,7 @@ static nv_status tile_chain(const nv_maps* M, const double* y0, double* yT, doub
     a.base = ex->base;
     a.col0_off = ex->col0_off;
   }
+  a.test_skip = g_tune.test_skip_partials;
   int nrb_arg = nrb, cpc_arg = cpc;
   void* args[] = {&a, &nrb_arg, &cpc_arg, &xb};
   return nv_cuda_check(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, s),

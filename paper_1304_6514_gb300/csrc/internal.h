@@ -133,5 +133,6 @@ struct nv_tunables {
   int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring
   int refine_schedule;     // heat NV_FP32_REFINE: 0 auto (pipelined), 1 sequential passes
   int test_withhold_defect;  // test hook: pipelined refinement never flags pass 1's defect of this slice + 1
+  int test_skip_partials;    // test hook: the d > 512 ring chain's CTA 0 never stores step value - 1's partials
 };
 extern nv_tunables g_tune;

@@ -139,3 +139,42 @@ def test_tiled_chain_ring_and_register_kernels_agree(prec, S):
     ser = nv.serial_fine(nv.workload_rhs(w, True), "rk4", w.t0, w.T, w.S, m, w.y0)
     tol = {"fp64": 1e-11, "fp32": 1e-5, "bf16_refine": 1e-4}[prec]
     assert rel_l2(out[2][0].numpy(), ser) <= tol
+
+
+def test_ring_chain_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection of the d > 512 ring chain (tagged exchange, no grid
+    barrier) without a GPU fault: a test hook (tunable 13) keeps the first
+    CTA from storing its partials of step 1, so the CTAs that need them give
+    up after their bounded wait; NV_ETIMEOUT is reported and the launch ends
+    within seconds.  The next composition on the same maps and context matches
+    the register kernel bit for bit."""
+    torch = need_gpu()
+    import time
+    w = workloads.advdiff2d(S=3, T=3 * 2e-3)
+    r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
+    maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                 nvp.steps("rk4", w.dt, 0, "fp64"))
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    yT = torch.empty_like(y0)
+    try:
+        nvp.tune_set(9, 2)                        # the ring kernel
+        nvp.tune_set(13, 2)                       # CTA 0 skips step 1's partials
+        t0 = time.time()
+        nvp.compose(maps, y0, yT)
+        with pytest.raises(nvp.NvError) as exc:
+            nvp.maps_check(maps)
+        assert exc.value.status == nvp.NV_ETIMEOUT
+        assert time.time() - t0 < 10.0
+        nvp.tune_set(13, 0)
+        out = {}
+        for form in (2, 1):
+            nvp.tune_set(9, form)
+            y = torch.empty_like(y0)
+            nvp.compose(maps, y0, y)
+            nvp.maps_check(maps)
+            out[form] = y.cpu()
+        assert torch.equal(out[1], out[2])
+    finally:
+        nvp.tune_set(13, 0)
+        nvp.tune_set(9, 0)
+        maps.destroy()
