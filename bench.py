@@ -809,6 +809,17 @@ def run_square(args):
                      "paper_us_tesla_c2075": paper_us,
                      "paper_traj_steps_per_s": M * round(w.T / w.dt) / (paper_us * 1e-6)})
     big = rows[-1]
+    # the paper's cost model (eq. gpucostmodel) fitted to these times, beside
+    # its own fit on the Tesla C2075 (Table tauparameters)
+    from paper_1304_6514_gb300 import costmodel
+    shapes = [(0.5 * 2 ** e, S, M) for e, S, M, _ in PAPER_GPU_TABLE]
+    fits = {}
+    for key in ("e2e_us", "device_us"):
+        tf, tn, tk = costmodel.fit_gpu_cost([(n, S, M, row[key]) for (n, S, M), row in zip(shapes, rows)])
+        fits[key] = {"tau_F_us": tf, "tau_N_us": tn, "tau_K_us": tk}
+    cost_model = {"model": "C_G = (M n / N) tau_F + N tau_N + tau_K, n = T / dt (eq. gpucostmodel)",
+                  "fit_e2e": fits["e2e_us"], "fit_device": fits["device_us"],
+                  "paper_tesla_c2075": {"tau_F_us": 0.040, "tau_N_us": 0.701, "tau_K_us": 137.0}}
     line = {"metric": METRIC, "value": big["traj_steps_per_s_e2e"], "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": big["e2e_us"] * 1e-3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 build, f64 composition", "data": "synthetic",
@@ -816,7 +827,7 @@ def run_square(args):
                        "l2": "not flushed: the whole problem (3.6 KB of tables) lives in L2 as in the paper's runs"},
             "e2e": {"value": big["traj_steps_per_s_e2e"], "unit": UNIT, "h2d_bytes_per_step": 8,
                     "d2h_bytes_per_step": 8, "api": "nv_solve (allocates, builds, composes, frees)"},
-            "sweep": rows,
+            "sweep": rows, "cost_model": cost_model,
             "paper_context": "Tesla C2075 (Fermi), backward Euler + Chebyshev interpolation, single precision; "
                              "times include allocation, transfers and CPU interpolation",
             "gpu_launches": 2 * K}
