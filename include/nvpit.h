@@ -385,10 +385,18 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          NV_FP32_REFINE (default 0 = three / two / one; a negative value
  *          returns the unrefined reduced-precision states)
  *   key 6: form of the RK4 step for the homogeneous heat columns: 0 auto (the
- *          nine-point stencil where every lane holds >= 4 whole rows, else
- *          Horner stages), 1 Horner stages, 2 nine-point stencil where it
- *          applies.  Both are the classical RK4 step of y' = Ly exactly; they
- *          differ in rounding only.
+ *          windowed nine-point stencil where a built window fits, else the
+ *          full-width nine-point stencil where every lane holds >= 4 whole
+ *          rows, else Horner stages), 1 Horner stages, 2 full-width nine-point
+ *          stencil where it applies, 3 one window per column, 4 two windows
+ *          per column (a narrow one for the first steps, a wide one for the
+ *          rest).  Forms 3 and 4 make the build return NV_ENOTSUP when no
+ *          built window of that kind holds the 8m+1 rows within n.  All are
+ *          the classical RK4 step of y' = Ly exactly; Horner and nine-point
+ *          differ in rounding only, and a windowed stencil integrates each
+ *          column only over the rows its steps can reach (they are exactly
+ *          zero elsewhere), with the same nonzero entries as the full-width
+ *          stencil bit for bit.
  *   key 7: test hook, 0..4 (default 0): participants that never arrive, added to the
  *          grid barrier of the cooperative row chain (selected by key 3 < 0).  Every
  *          CTA then gives up at its first bounded wait (~0.4 s), records NV_ETIMEOUT
@@ -419,8 +427,12 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          need them give up after their bounded wait (~1 s) and record
  *          NV_ETIMEOUT; the others run out their loops; the context stays
  *          usable.  The paper has no counterpart.
+ *   key 14: 0 (default) or 1: with 1 the d <= 256 cluster chains read every
+ *          column of banded maps (those of the heat equations, zero off
+ *          |r - c| <= 4m) instead of the band around each CTA's rows; the
+ *          results are the same bit for bit.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12 and 13. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13 and 14. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

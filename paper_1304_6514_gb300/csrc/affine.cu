@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <stdint.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -142,6 +144,198 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64 && R <= 8) ? 4 : 1) 
       }
     }
     store_column<R, TF32OUT>(y, column_stage<R, T>(), out + ((int64_t)j * cols + c) * n, lane, n);
+  }
+}
+
+// One nine-point step of a window of G*R rows held by G lanes (R rows each):
+// the halo comes from the neighbouring lanes of the group, and at the
+// window's ends it is the odd reflection (lo_end / hi_end: the end of the
+// window is the end of the domain) or zero (the window is cut inside the
+// domain).  Same expression, operand for operand, as heat_poly9_kernel.
+template <typename T, int G, int R>
+__device__ __forceinline__ void window_step(T (&y)[R], int gl, bool lo_end, bool hi_end, T c0, T c1, T c2,
+                                            T c3, T c4) {
+  T e[R + 8];                                       // rows w0+gl*R-4 .. w0+gl*R+R+3
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    e[k] = __shfl_up_sync(0xffffffffu, y[R - 4 + k], 1, G);
+    e[R + 4 + k] = __shfl_down_sync(0xffffffffu, y[k], 1, G);
+  }
+  if (gl == 0) {                                    // rows w0-4..w0-1
+    e[0] = lo_end ? -y[2] : (T)0;
+    e[1] = lo_end ? -y[1] : (T)0;
+    e[2] = lo_end ? -y[0] : (T)0;
+    e[3] = (T)0;
+  }
+  if (gl == G - 1) {                                // rows w0+W .. w0+W+3
+    e[R + 4] = (T)0;
+    e[R + 5] = hi_end ? -y[R - 1] : (T)0;
+    e[R + 6] = hi_end ? -y[R - 2] : (T)0;
+    e[R + 7] = hi_end ? -y[R - 3] : (T)0;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) e[i + 4] = y[i];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    T acc = c4 * (e[i] + e[i + 8]);
+    acc = fma(c3, e[i + 1] + e[i + 7], acc);
+    acc = fma(c2, e[i + 2] + e[i + 6], acc);
+    acc = fma(c1, e[i + 3] + e[i + 5], acc);
+    y[i] = fma(c0, e[i + 4], acc);
+  }
+}
+
+// Window origin of column c (1-based) for a window of W rows and reach 4m.
+__device__ __forceinline__ int window_origin(int c, int reach, int n, int W) {
+  return min(max(c - 1 - reach, 0), n - W);
+}
+
+// Write the windows of 32/G columns (w*CPW .. w*CPW+CPW-1 of the flattened
+// (slice, column) order), staged in buf as lane*(R+1)+i, as full columns of n
+// rows with zeros outside the windows; consecutive rows in consecutive lanes.
+template <typename T, int G, int R, bool TF32OUT>
+__device__ __forceinline__ void store_windows(const T* buf, T* out, int64_t first, int64_t total, int n,
+                                              int reach, int lane) {
+  constexpr int W = G * R, CPW = 32 / G;
+  const int cols = n + 1;
+#pragma unroll 1
+  for (int g = 0; g < CPW; ++g) {
+    const int64_t id = first + g;
+    if (id >= total) break;                         // warp-uniform
+    const int jg = (int)(id / n);
+    const int cg = 1 + (int)(id - (int64_t)jg * n);
+    const int v0 = window_origin(cg, reach, n, W);
+    T* col = out + ((int64_t)jg * cols + cg) * n;
+    for (int r = lane; r < n; r += 32) {
+      const int o = r - v0;
+      T v = (T)0;
+      if (o >= 0 && o < W) {
+        const int src = o / R;
+        v = buf[(g * G + src) * (R + 1) + (o - src * R)];
+      }
+      if constexpr (TF32OUT) col[r] = round_tf32(v);
+      else col[r] = v;
+    }
+  }
+}
+
+// The homogeneous columns again, each integrated over its domain of
+// dependence only.  A nine-point step carries information four rows, so the
+// column started from e_c is exactly zero outside rows c-1-4k .. c-1+4k after
+// k steps.  A group of G lanes (R rows each, 32/G columns per warp) holds a
+// window of W = G*R >= 8m+1 rows placed so that those rows of the last step
+// lie inside it: w0 = clamp(c-1-4m, 0, n-W).  Where the window is cut inside
+// the domain its halo reads zeros, the exact values there at every step that
+// reads them (the column's reach before the last step is 4(m-1), the cut is
+// 4m+1 rows away); where it meets an end of the domain the odd reflection
+// applies as above.  Each entry in the window is the same floating-point
+// expression as in heat_poly9_kernel (the inputs differ at most in the sign of
+// a zero), so the maps agree bit for bit up to the sign of zero entries; the
+// rows outside the window are written as zeros.  The work per column falls
+// from n to W rows.
+template <typename T, int G, int R, bool TF32OUT>
+__global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_window_kernel(HeatArgs a) {
+  static_assert(R >= 4 && G >= 2 && 32 % G == 0, "R >= 4 rows per lane, G lanes dividing the warp");
+  constexpr int W = G * R, CPW = 32 / G;
+  const int lane = threadIdx.x & 31, gl = lane % G, q = lane / G;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  const int reach = (int)(4 * a.m);                 // launcher: 8m+1 <= W <= n
+  const int64_t total = (int64_t)a.S * n;
+  const T c0 = poly9_weight<T>(a, 0), c1 = poly9_weight<T>(a, 1), c2 = poly9_weight<T>(a, 2),
+          c3 = poly9_weight<T>(a, 3), c4 = poly9_weight<T>(a, 4);
+  T* out = reinterpret_cast<T*>(a.out);
+  T* buf = column_stage<R, T>();
+  for (int64_t w = warp0; w * CPW < total; w += nwarps) {
+    const int64_t idx = w * CPW + q;                // this group's column; past the end: a dummy
+    const int j = idx < total ? (int)(idx / n) : 0;
+    const int c = idx < total ? 1 + (int)(idx - (int64_t)j * n) : 1;
+    const int w0 = window_origin(c, reach, n, W);
+    const bool lo_end = w0 == 0, hi_end = w0 + W == n;
+    T y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = (w0 + gl * R + i == c - 1) ? (T)1 : (T)0;
+    for (int64_t step = 0; step < a.m; ++step) window_step<T, G, R>(y, gl, lo_end, hi_end, c0, c1, c2, c3, c4);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < R; ++i) buf[lane * (R + 1) + i] = y[i];
+    __syncwarp();
+    store_windows<T, G, R, TF32OUT>(buf, out, w * CPW, total, n, reach, lane);
+    __syncwarp();
+  }
+}
+
+// Two windows per column: the column's reach grows by four rows a step, so
+// the first m1 steps (8*m1+1 <= GA*R rows) run on windows of GA lanes, 32/GA
+// columns per warp, and the remaining m - m1 steps on windows of GB = 2*GA
+// lanes (8m+1 <= GB*R rows), the warp's columns in two rounds of 32/GB.  Between
+// the phases each column's narrow window is staged in shared memory and read
+// back into the wide one by row (the narrow window lies inside the wide one:
+// both are clamped to the domain around the same row).  The steps are the
+// same expressions as in heat_window_kernel, so the maps are the same.
+template <typename T, int GA, int R, bool TF32OUT>
+__global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_window2_kernel(HeatArgs a, int m1) {
+  constexpr int GB = 2 * GA, WA = GA * R, WB = GB * R, CPW = 32 / GA, CPB = 32 / GB;
+  static_assert(R >= 4 && GA >= 2 && 32 % GB == 0, "R >= 4 rows per lane, 2*GA lanes dividing the warp");
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  const int reach1 = 4 * m1, reach = (int)(4 * a.m);   // launcher: 8*m1+1 <= WA, 8m+1 <= WB <= n
+  const int64_t total = (int64_t)a.S * n;
+  const T c0 = poly9_weight<T>(a, 0), c1 = poly9_weight<T>(a, 1), c2 = poly9_weight<T>(a, 2),
+          c3 = poly9_weight<T>(a, 3), c4 = poly9_weight<T>(a, 4);
+  T* out = reinterpret_cast<T*>(a.out);
+  __shared__ T narrow_all[8 * 32 * (R + 1)];         // the narrow windows, lane*(R+1)+i
+  T* narrow = narrow_all + (threadIdx.x >> 5) * 32 * (R + 1);
+  T* buf = column_stage<R, T>();
+  for (int64_t w = warp0; w * CPW < total; w += nwarps) {
+    {                                               // phase 1: CPW columns, GA lanes each
+      const int gl = lane % GA;
+      const int64_t idx = w * CPW + lane / GA;
+      const int j = idx < total ? (int)(idx / n) : 0;
+      const int c = idx < total ? 1 + (int)(idx - (int64_t)j * n) : 1;
+      const int w0 = window_origin(c, reach1, n, WA);
+      T y[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) y[i] = (w0 + gl * R + i == c - 1) ? (T)1 : (T)0;
+      for (int step = 0; step < m1; ++step)
+        window_step<T, GA, R>(y, gl, w0 == 0, w0 + WA == n, c0, c1, c2, c3, c4);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < R; ++i) narrow[lane * (R + 1) + i] = y[i];
+      __syncwarp();
+    }
+#pragma unroll 1
+    for (int round = 0; round < CPW / CPB; ++round) { // phase 2: CPB columns at a time, GB lanes each
+      const int gl = lane % GB, qa = round * CPB + lane / GB;   // the column's slot in phase 1
+      const int64_t first = w * CPW + round * CPB;
+      if (first >= total) break;                    // warp-uniform
+      const int64_t idx = w * CPW + qa;
+      const int j = idx < total ? (int)(idx / n) : 0;
+      const int c = idx < total ? 1 + (int)(idx - (int64_t)j * n) : 1;
+      const int wa = window_origin(c, reach1, n, WA), wb = window_origin(c, reach, n, WB);
+      T y[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int o = wb + gl * R + i - wa;         // row's offset in the narrow window
+        T v = (T)0;
+        if (o >= 0 && o < WA) {
+          const int src = o / R;
+          v = narrow[(qa * GA + src) * (R + 1) + (o - src * R)];
+        }
+        y[i] = v;
+      }
+      for (int64_t step = m1; step < a.m; ++step)
+        window_step<T, GB, R>(y, gl, wb == 0, wb + WB == n, c0, c1, c2, c3, c4);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < R; ++i) buf[lane * (R + 1) + i] = y[i];
+      __syncwarp();
+      store_windows<T, GB, R, TF32OUT>(buf, out, first, total, n, reach, lane);
+      __syncwarp();
+    }
   }
 }
 
@@ -578,6 +772,90 @@ static nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* g
   return NV_OK;
 }
 
+template <typename T, int G, int R>
+static nv_status launch_window_GR(const HeatArgs& a, int block, cudaStream_t s, bool tf32out) {
+  const int64_t warps = ((int64_t)a.S * a.n + 32 / G - 1) / (32 / G);
+  int grid = 0;
+  nv_status st;
+  if constexpr (sizeof(T) == 4) {
+    if (tf32out) {
+      st = persistent_grid(heat_window_kernel<T, G, R, true>, block, warps, &grid);
+      if (st != NV_OK) return st;
+      heat_window_kernel<T, G, R, true><<<grid, block, 0, s>>>(a);
+      return nv_cuda_check(cudaGetLastError(), "heat_window_kernel launch");
+    }
+  }
+  st = persistent_grid(heat_window_kernel<T, G, R, false>, block, warps, &grid);
+  if (st != NV_OK) return st;
+  heat_window_kernel<T, G, R, false><<<grid, block, 0, s>>>(a);
+  return nv_cuda_check(cudaGetLastError(), "heat_window_kernel launch");
+}
+
+template <typename T, int GA, int R>
+static nv_status launch_window2(const HeatArgs& a, int m1, int block, cudaStream_t s, bool tf32out) {
+  const int64_t warps = ((int64_t)a.S * a.n + 32 / GA - 1) / (32 / GA);
+  int grid = 0;
+  nv_status st;
+  if constexpr (sizeof(T) == 4) {
+    if (tf32out) {
+      st = persistent_grid(heat_window2_kernel<T, GA, R, true>, block, warps, &grid);
+      if (st != NV_OK) return st;
+      heat_window2_kernel<T, GA, R, true><<<grid, block, 0, s>>>(a, m1);
+      return nv_cuda_check(cudaGetLastError(), "heat_window2_kernel launch");
+    }
+  }
+  st = persistent_grid(heat_window2_kernel<T, GA, R, false>, block, warps, &grid);
+  if (st != NV_OK) return st;
+  heat_window2_kernel<T, GA, R, false><<<grid, block, 0, s>>>(a, m1);
+  return nv_cuda_check(cudaGetLastError(), "heat_window2_kernel launch");
+}
+
+// Built window shapes: one window of G lanes x R rows (W = G*R >= 8m+1), or
+// two (GA x R for the first m1 = (GA*R-1)/8 steps, 2*GA x R for the rest).
+// The launcher takes the built option with the fewest row-steps per column
+// (m*W, or m1*GA*R + (m-m1)*2*GA*R); a window as wide as n only when asked
+// for, since the full-width kernel does the same work.  Form 3 takes single
+// windows only, form 4 two-phase windows only, form 0 either.  NV_ENOTSUP,
+// with no launch, when nothing fits.
+static const int kWindow1[][2] = {{8, 4}, {8, 8}, {8, 11}, {16, 8}, {16, 11}, {32, 8}};
+static const int kWindow2[][2] = {{4, 11}, {8, 8}};
+
+template <typename T>
+static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form) {
+  int64_t best = INT64_MAX;
+  int pick = -1, m1 = 0;
+  if (form != 4) {
+    for (int k = 0; k < 6; ++k) {
+      const int W = kWindow1[k][0] * kWindow1[k][1];
+      if (8 * a.m + 1 > W || W > a.n || (W == a.n && form != 3)) continue;
+      if (a.m * W < best) best = a.m * W, pick = k;
+    }
+  }
+  if (form != 3) {
+    for (int k = 0; k < 2; ++k) {
+      const int WA = kWindow2[k][0] * kWindow2[k][1], WB = 2 * WA, k1 = (WA - 1) / 8;
+      if (8 * a.m + 1 > WB || WB > a.n || k1 >= a.m || (WB == a.n && form != 4)) continue;
+      const int64_t cost = k1 * WA + (a.m - k1) * WB;
+      if (cost < best) best = cost, pick = 6 + k, m1 = k1;
+    }
+  }
+  switch (pick) {
+    case 0: return launch_window_GR<T, 8, 4>(a, block, s, tf32out);
+    case 1: return launch_window_GR<T, 8, 8>(a, block, s, tf32out);
+    case 2: return launch_window_GR<T, 8, 11>(a, block, s, tf32out);
+    case 3: return launch_window_GR<T, 16, 8>(a, block, s, tf32out);
+    case 4: return launch_window_GR<T, 16, 11>(a, block, s, tf32out);
+    case 5: return launch_window_GR<T, 32, 8>(a, block, s, tf32out);
+    case 6: return launch_window2<T, 4, 11>(a, m1, block, s, tf32out);
+    case 7: return launch_window2<T, 8, 8>(a, m1, block, s, tf32out);
+    default: break;
+  }
+  if (form == 3 || form == 4)
+    return nv_fail(NV_ENOTSUP, "no built window holds 8m+1 = %lld rows within n = %d",
+                   (long long)(8 * a.m + 1), a.n);
+  return NV_ENOTSUP;
+}
+
 template <typename T, int R>
 static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) {
   const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
@@ -595,6 +873,11 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
   heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
   st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   if (st != NV_OK) return st;
+  const int form = g_tune.heat_step_form;
+  if (form == 0 || form == 3 || form == 4) {
+    st = launch_heat_window<T>(a, block, s, tf32out, form);
+    if (st != NV_ENOTSUP || form != 0) return st;
+  }
   if constexpr (R >= 4) {
     if (g_tune.heat_step_form != 1 && a.n % R == 0) {
       if constexpr (sizeof(T) == 4) {
@@ -646,6 +929,10 @@ nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
     const int R = rows_per_lane(M->dim);
     if (R == 0) return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", M->dim);
     const HeatArgs a = heat_args(M);
+    // each RK4 step of the three-point operator widens a column's support by
+    // four rows on each side (four stages), so A_j is zero off the band
+    // |r - c| <= 4m
+    M->band = M->m < (1 << 28) ? (int32_t)(4 * M->m + 1) : 0;
     if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s, false);
     return launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE);
   }

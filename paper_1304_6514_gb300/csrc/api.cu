@@ -434,7 +434,7 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 4: g_tune.scan_block = value; break;
     case 5: g_tune.refine_passes = value; break;
     case 6:
-      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "heat step form is 0, 1 or 2");
+      if (value < 0 || value > 4) return nv_fail(NV_EINVAL, "heat step form is 0..4");
       g_tune.heat_step_form = value;
       break;
     case 7:
@@ -460,6 +460,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 13:
       if (value < 0) return nv_fail(NV_EINVAL, "skipped step is 0 (off) or step + 1");
       g_tune.test_skip_partials = value;
+      break;
+    case 14:
+      if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "chain band use is 0 or 1");
+      g_tune.chain_dense = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }

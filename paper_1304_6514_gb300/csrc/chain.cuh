@@ -123,6 +123,24 @@ struct ChainNoHooks {
   __device__ void after_state0() const {}
 };
 
+// Banded maps (ChainsArgs::band > 0): the 16 rows r0 .. r0+15 of a CTA meet
+// nonzero entries only in columns r0-(band-1) .. r0+15+(band-1).  The CTA
+// reads columns r0-bw .. r0+15+bw, bw = band-1 rounded up to a multiple of 16,
+// so that each thread's columns (those congruent to its column group modulo
+// 16) keep their order and the products are the dense chain's, less terms that
+// are exactly zero.  chain_band_lo is bw, or 0 when that window is not
+// narrower than d (the CTA then reads all d columns); chain_band_cols the
+// columns read.
+__host__ __device__ inline int chain_band_lo(int n, int band) {
+  if (band <= 0) return 0;
+  const int bw = (band - 1 + 15) & ~15;
+  return kChainRpc + 2 * bw < n ? bw : 0;
+}
+__host__ __device__ inline int chain_band_cols(int n, int band) {
+  const int bw = chain_band_lo(n, band);
+  return bw > 0 ? kChainRpc + 2 * bw : n;
+}
+
 template <typename MT, typename AT, typename Hooks>
 __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const ChainsArgs& a, int* status,
                                                   int q, const Hooks& hooks) {
@@ -138,7 +156,10 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
   const unsigned rank = cl.block_rank();
   extern __shared__ __align__(128) unsigned char ring_smem[];
   const int n = a.n;
-  const int stage_elems = rpc * n;
+  const int wcols = chain_band_cols(n, a.band);                        // columns of A_j read
+  const int bw = chain_band_lo(n, a.band);
+  const int col0 = bw > 0 ? (int)rank * rpc - bw : 0;                  // the first (may be < 0)
+  const int stage_elems = rpc * wcols;
   MT* ring = reinterpret_cast<MT*>(ring_smem);                          // kRing stages
   // per stage also rpc values of v_j and of add_{j+1}, as doubles (16-byte slots)
   double* vring = reinterpret_cast<double*>(ring + kRing * stage_elems);
@@ -186,7 +207,7 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(cta_smem_u32(ring + st * stage_elems)),
-        "l"(tmA), "r"((int)rank * rpc), "r"(0), "r"(j0 + k), "r"(cta_smem_u32(&full[st]))
+        "l"(tmA), "r"((int)rank * rpc), "r"(col0), "r"(j0 + k), "r"(cta_smem_u32(&full[st]))
         : "memory");
     const char* vsrc = reinterpret_cast<const char*>(a.v) +
                        ((int64_t)(j0 + k) * a.v_stride + (int64_t)rank * rpc) * vsz;
@@ -241,6 +262,8 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     rb1 = cluster_addr(cta_smem_u32(&xbar[1]), peer);
   }
 
+  // the window's columns inside 0 .. d-1 (those outside are the copy's zero fill)
+  const int cb = max(0, -col0), ce = min(wcols, n - col0);
   int consumed = len;
   for (int k = 0; has_rows && k < len; ++k) {
     const int j = j0 + k;
@@ -265,7 +288,7 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     const MT* Aj = ring + st * stage_elems;
     AT acc = 0;
     if (active)
-      for (int c = cgi; c < n; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[c], acc);
+      for (int c = cb + cgi; c < ce; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[col0 + c], acc);
     // lanes l and l ^ 16 hold the same row (rpc = 16)
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     AT* redk = red + (k & 1) * blockDim.x;

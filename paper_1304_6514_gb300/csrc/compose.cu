@@ -692,14 +692,15 @@ nv_status chain_tma_prepare(const ChainsArgs& args_in, bool f64, CUtensorMap* tm
   if (st != NV_OK) return st;
   const cuuint64_t gdim[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)args_in.S};
   const cuuint64_t gstride[2] = {(cuuint64_t)n * esz, (cuuint64_t)args_in.a_stride * esz};
-  const cuuint32_t box[3] = {(cuuint32_t)rpc, (cuuint32_t)n, 1};
+  const int wcols = chain_band_cols(n, args_in.band);
+  const cuuint32_t box[3] = {(cuuint32_t)rpc, (cuuint32_t)wcols, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult cr = enc(tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                     const_cast<void*>(args_in.A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return NV_ENOTSUP;
-  *smem = esz * (size_t)kRing * rpc * n + 2 * 8 * (size_t)kRing * rpc + esz * (2 * (size_t)n + 2 * block) +
+  *smem = esz * (size_t)kRing * rpc * wcols + 2 * 8 * (size_t)kRing * rpc + esz * (2 * (size_t)n + 2 * block) +
           8 * (kRing + 2) + 16;
   return NV_OK;
 }
@@ -803,6 +804,7 @@ static nv_status launch_affine_chain_cluster(const nv_maps* M, const double* y0,
   a.yT = yT;
   a.write_state0 = 1;
   a.status = M->status;
+  a.band = g_tune.chain_dense ? 0 : M->band;
   return launch_chains(a, f64, s, want_csize);
 }
 

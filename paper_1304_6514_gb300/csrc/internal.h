@@ -43,6 +43,9 @@ struct nv_maps {
   int64_t coef_per_slice;
   double* aux;                 // operator storage (wave: D and D2), may be NULL
   int64_t aux_elems;
+  // 0: dense maps; > 0: every A_j[r][c] with |r - c| >= band is exactly zero
+  // (set by the build where the scheme fixes it; the chains then skip them)
+  int32_t band;
   // reduced-precision composition scratch (NV_TF32_REFINE), allocated lazily
   void* scan_ws;
   size_t scan_ws_bytes;
@@ -114,6 +117,7 @@ struct ChainsArgs {
   double* yT;             // optional: x after the last slice S-1 (+ add)
   int write_state0;       // chain 0 also writes states[0..n) = x0 (+ add)
   int* status;            // device status word (bounded waits record NV_ETIMEOUT)
+  int band;               // 0 dense; > 0: A_j[r][c] == 0 whenever |r - c| >= band
 };
 
 nv_status launch_chains(const ChainsArgs& args, bool f64, cudaStream_t s, int want_csize);
@@ -127,12 +131,13 @@ struct nv_tunables {
   int chain_cluster;       // CTAs per cluster of the d <= 512 chain (0 auto, < 0 grid-wide)
   int scan_block;          // slices per block of the tensor-core scan (0 auto)
   int refine_passes;       // float64 correction passes of NV_TF32_REFINE (0 = 1, < 0 none)
-  int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil
+  int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil, 3 / 4 one / two windows
   int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
   int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
   int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring
   int refine_schedule;     // heat NV_FP32_REFINE: 0 auto (pipelined), 1 sequential passes
   int test_withhold_defect;  // test hook: pipelined refinement never flags pass 1's defect of this slice + 1
   int test_skip_partials;    // test hook: the d > 512 ring chain's CTA 0 never stores step value - 1's partials
+  int chain_dense;           // 1: the d <= 256 cluster chains read every column even of banded maps
 };
 extern nv_tunables g_tune;

@@ -52,6 +52,7 @@ static nv_status heat_chain_refine(nv_maps* M, const double* y0, double* yT, dou
   c.a_stride = (int64_t)n * (n + 1);
   c.status = M->status;
   c.write_state0 = 1;
+  c.band = g_tune.chain_dense ? 0 : M->band;
   ChainsArgs approx = c;                 // lt: the chain over the float32 maps from y0
   approx.v = maps;                       // column 0, b_j
   approx.v_stride = (int64_t)n * (n + 1);

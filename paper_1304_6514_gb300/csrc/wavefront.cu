@@ -216,6 +216,7 @@ nv_status launch_heat_wavefront(nv_maps* M, const double* y0, double* yT, double
     a.a_stride = (int64_t)n * (n + 1);
     a.status = M->status;
     a.write_state0 = 1;
+    a.band = g_tune.chain_dense ? 0 : M->band;
     const bool last = c == passes;
     double* states = last ? lambdas : lt + (size_t)c * (S + 1) * n;
     a.states = states;

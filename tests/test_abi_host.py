@@ -102,7 +102,11 @@ def test_null_handles(lib):
     assert lib.nv_maps_info(None, None) == nvp.NV_EINVAL
     assert lib.nv_maps_destroy(None) == nvp.NV_OK
     assert lib.nv_tune_set(99, 1) == nvp.NV_EINVAL
-    assert lib.nv_tune_set(6, 3) == nvp.NV_EINVAL           # heat step form is 0..2
+    assert lib.nv_tune_set(6, 5) == nvp.NV_EINVAL           # heat step form is 0..4
+    assert lib.nv_tune_set(6, 4) == nvp.NV_OK
+    assert lib.nv_tune_set(6, -1) == nvp.NV_EINVAL
+    assert lib.nv_tune_set(6, 3) == nvp.NV_OK
+    assert lib.nv_tune_set(6, 0) == nvp.NV_OK
     assert lib.nv_tune_set(7, 5) == nvp.NV_EINVAL           # phantom barrier participants 0..4
     assert lib.nv_tune_set(7, -1) == nvp.NV_EINVAL
     assert lib.nv_tune_set(8, 3) == nvp.NV_EINVAL           # split-K is 0 or a power of two <= 16
@@ -111,6 +115,10 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(9, -1) == nvp.NV_EINVAL
     assert lib.nv_tune_set(9, 1) == nvp.NV_OK
     assert lib.nv_tune_set(9, 0) == nvp.NV_OK
+    assert lib.nv_tune_set(14, 2) == nvp.NV_EINVAL          # chain band use is 0 or 1
+    assert lib.nv_tune_set(14, -1) == nvp.NV_EINVAL
+    assert lib.nv_tune_set(14, 1) == nvp.NV_OK
+    assert lib.nv_tune_set(14, 0) == nvp.NV_OK
     assert lib.nv_tune_set(10, 2) == nvp.NV_EINVAL          # refinement schedule is 0 or 1
     assert lib.nv_tune_set(10, 1) == nvp.NV_OK
     assert lib.nv_tune_set(10, 0) == nvp.NV_OK

@@ -46,7 +46,7 @@ def test_heat_small_elementwise_fp64(n, S):
     assert rel_l2(yT, olam[-1]) <= 1e-11
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 @pytest.mark.parametrize("n,S", [(128, 3), (200, 4), (256, 3), (512, 2)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
 def test_heat_step_forms_elementwise(form, n, S, prec, tol):
@@ -70,6 +70,90 @@ def test_heat_step_forms_elementwise(form, n, S, prec, tol):
     assert rel_max(b, ob) <= tol
     olam = nv.compose_affine(oA, ob, w.y0)
     assert rel_l2(lam, olam) <= (1e-11 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("n,S,steps,form", [
+    (256, 1024, 10, 3), (256, 1024, 10, 4),      # the heat benchmark's build
+    (256, 6, 3, 3), (100, 5, 5, 3), (128, 4, 15, 3), (512, 3, 21, 3), (512, 2, 31, 3), (200, 4, 10, 3),
+    (256, 6, 8, 4), (100, 5, 6, 4), (128, 4, 15, 4), (176, 3, 12, 4), (200, 4, 10, 4)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heat_window_matches_full_width(n, S, steps, form, prec):
+    """The windowed nine-point builds (each column integrated only over the
+    rows its steps reach: form 3 one window of >= 8m+1 rows, form 4 a narrow
+    window for the first steps and a wide one for the rest) write the same
+    maps as the full-width nine-point build, entry for entry (zeros compare
+    equal whatever their sign).  n = 256, S = 1024, m = 10 is the heat
+    benchmark's build; the others take every built window shape, windows
+    against both Dirichlet ends, windows as wide as n (n = 128, m = 15) and
+    n = 100, 176, 200 (not multiples of a window's rows per lane)."""
+    torch = need_gpu()
+    T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    assert nv.workload_steps(w) == steps
+    got = {}
+    for f in (form, 2):
+        nvp.tune_set(6, f)
+        try:
+            _, A, b, yT, lam = _heat(torch, w, prec)
+        finally:
+            nvp.tune_set(6, 0)
+        got[f] = (A, b, lam)
+    assert np.array_equal(got[form][0], got[2][0])
+    assert np.array_equal(got[form][1], got[2][1])
+    assert np.array_equal(got[form][2], got[2][2])
+    # the zeros outside the reach are exact
+    A = got[form][0]
+    rows, cols = np.indices(A.shape[1:])
+    outside = np.abs(rows - cols) > 4 * steps
+    assert not np.any(A[:, outside])
+
+
+@pytest.mark.parametrize("n,S,steps", [(256, 1024, 10), (256, 7, 3), (128, 5, 2), (64, 3, 1), (192, 6, 5),
+                                       (256, 4, 40)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_refine"])
+def test_banded_chain_matches_dense(n, S, steps, prec):
+    """The heat maps are zero off the band |r - c| <= 4m, and the cluster
+    chain then reads only the columns of that band around each CTA's rows
+    (rounded out to 16 so that every thread keeps its columns and their
+    order): every boundary state equals the dense chain's (tunable 14 = 1)
+    bit for bit, for the plain float64 / float32 compositions and the
+    pipelined float64 refinement.  n = 256, S = 1024, m = 10 is the heat
+    benchmark; m = 40 at n = 256 has a band wider than the matrix (dense)."""
+    torch = need_gpu()
+    T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    assert nv.workload_steps(w) == steps
+    got = {}
+    for dense in (0, 1):
+        nvp.tune_set(14, dense)
+        try:
+            _, A, b, yT, lam = _heat(torch, w, prec)
+        finally:
+            nvp.tune_set(14, 0)
+        got[dense] = (yT, lam)
+    assert np.array_equal(got[0][0], got[1][0])
+    assert np.array_equal(got[0][1], got[1][1])
+    rows, cols = np.indices((n, n))
+    assert not np.any(A[:, np.abs(rows - cols) > 4 * steps])   # the band the chain relies on
+
+
+@pytest.mark.parametrize("form", [3, 4])
+def test_heat_window_refused_when_none_fits(form):
+    """Forms 3 and 4 with no built window holding 8m+1 rows within n are
+    refused by the build with NV_ENOTSUP (n = 96, m = 11 needs 89 rows; the
+    single windows are 32, 64, 88, 128, 176 and 256 rows, the two-phase ones
+    end at 88 and 128)."""
+    torch = need_gpu()
+    n, S, steps = 96, 2, 11
+    T = S * steps * 2.0 / (5.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    nvp.tune_set(6, form)
+    try:
+        with pytest.raises(nvp.NvError) as ei:
+            _heat(torch, w, "fp64")
+        assert ei.value.status == nvp.NV_ENOTSUP
+    finally:
+        nvp.tune_set(6, 0)
 
 
 def test_heat_small_fp32():
