@@ -183,7 +183,14 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
   const int vsz = a.v_double ? 8 : (int)sizeof(MT);
   const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(MT)) + (uint32_t)(rpc * vsz) +
                                (a.add ? (uint32_t)(rpc * 8) : 0u);
-  const uint32_t state_bytes = (uint32_t)(n * sizeof(AT));
+  // Banded maps: a CTA's columns are the rows of the CTAs within hops ranks,
+  // so it receives the state rows of those CTAs only, and sends its own rows
+  // to the same CTAs (the relation is symmetric, which keeps the ordering
+  // argument of the state buffers below).  Dense: every CTA that owns rows.
+  const int hops = bw / rpc;
+  const unsigned src_lo = bw > 0 ? (unsigned)max((int)rank - hops, 0) : 0u;
+  const unsigned src_hi = bw > 0 ? min(rank + (unsigned)hops, owners - 1u) : owners - 1u;
+  const uint32_t state_bytes = (uint32_t)((src_hi - src_lo + 1u) * rpc * sizeof(AT));
 
   if (tid == 0) {
     for (int i = 0; i < kRing + 2; ++i)
@@ -252,7 +259,7 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
   // CTA p = l % 16; its remote addresses of both state buffers and barriers.
   const unsigned peer = (unsigned)(lane & 15);
   const int half_rows = (lane >> 4) * 8;
-  const bool sender = warp == 0 && peer < owners;
+  const bool sender = warp == 0 && peer < owners && (bw == 0 || abs((int)peer - (int)rank) <= hops);
   uint32_t rx0 = 0u, rx1 = 0u, rb0 = 0u, rb1 = 0u;
   if (sender) {
     const uint32_t off = (uint32_t)(((int)rank * rpc + half_rows) * sizeof(AT));
