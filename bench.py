@@ -40,10 +40,12 @@ FLOP_PER_COMPONENT_STEP = 20         # Horner-form RK4 step of the 3-point stenc
 # Window shapes (lanes per column, rows per lane) built for the heat equation's
 # homogeneous columns: one window of W = lanes * rows >= 8m+1 (the rows that m
 # nine-point steps reach from one basis vector), or two (lanes x rows for the
-# first m1 = (W-1) // 8 steps, twice the lanes for the rest).  The build takes
+# first m1 = (W-1) // 8 steps, twice the lanes for the rest), or three (the
+# lanes doubling twice).  The build takes
 # the option with the fewest row-steps per column, windows narrower than n only.
 HEAT_WINDOWS = ((8, 4), (8, 8), (8, 11), (16, 8), (16, 11), (32, 8))
 HEAT_WINDOWS2 = ((4, 11), (8, 8))
+HEAT_WINDOWS3 = ((2, 11),)          # lanes of the first of three windows (then x2, x4), rows
 
 
 def heat_window(n, m):
@@ -58,6 +60,12 @@ def heat_window(n, m):
             cost = m1 * wa + (m - m1) * 2 * wa
             if best is None or cost < best[0]:
                 best = (cost, f"heat_window2_kernel<double,{g},{r},0>")
+    for g, r in HEAT_WINDOWS3:
+        w1, m1, m2 = g * r, (g * r - 1) // 8, (2 * g * r - 1) // 8
+        if 8 * m + 1 <= 4 * w1 < n and 1 <= m1 and m2 < m:
+            cost = m1 * w1 + (m2 - m1) * 2 * w1 + (m - m2) * 4 * w1
+            if best is None or cost < best[0]:
+                best = (cost, f"heat_window3_kernel<double,{g},{r},0>")
     if best is None:
         r = max(4, 1 << (max(1, -(-n // 32)) - 1).bit_length())
         best = (m * n, f"heat_poly9_kernel<double,{r},0>")
@@ -344,6 +352,7 @@ def gpu_peak_probe(torch):
 # captures ran smaller cases of the same kernels; see profiles/):
 #   heat FP64 build (nine-point form), S = 512 capture: 207.06 MB for 131 072 columns
 #   heat FP64 build (two-window form), full size: 475.35 MB for 262 144 columns
+#   heat FP64 build (three-window form), full size: 475.15 MB for 262 144 columns
 #   advection-diffusion FP32 build, S = 8 capture: 475.04 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 503.0 MB for 561 987 584 table bytes
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
@@ -354,6 +363,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
     "heat_poly9_kernel<double,8,0>": (207.06e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "heat_window2_kernel<double,4,11,0>": (475.35e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
+    "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),

@@ -390,8 +390,9 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          rows, else Horner stages), 1 Horner stages, 2 full-width nine-point
  *          stencil where it applies, 3 one window per column, 4 two windows
  *          per column (a narrow one for the first steps, a wide one for the
- *          rest).  Forms 3 and 4 make the build return NV_ENOTSUP when no
- *          built window of that kind holds the 8m+1 rows within n.  All are
+ *          rest), 5 three windows.  Forms 3, 4 and 5 make the build return
+ *          NV_ENOTSUP when no built window of that kind holds the 8m+1 rows
+ *          within n.  All are
  *          the classical RK4 step of y' = Ly exactly; Horner and nine-point
  *          differ in rounding only, and a windowed stencil integrates each
  *          column only over the rows its steps can reach (they are exactly

@@ -339,6 +339,107 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
   }
 }
 
+// Fill a wide window (origin wide0, G lanes of R rows, this lane's rows
+// gl*R ..) from a narrow window of slot `slot` staged by GN lanes per column
+// as lane*(R+1)+i (origin wn, WN rows); rows outside the narrow window are 0.
+template <typename T, int GN, int R>
+__device__ __forceinline__ void widen_window(T (&y)[R], const T* narrow, int slot, int wn, int WN, int wide0,
+                                             int gl) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int o = wide0 + gl * R + i - wn;
+    T v = (T)0;
+    if (o >= 0 && o < WN) {
+      const int src = o / R;
+      v = narrow[(slot * GN + src) * (R + 1) + (o - src * R)];
+    }
+    y[i] = v;
+  }
+}
+
+// Three windows per column, doubling the lanes each time: the first
+// m1 = (G1*R-1)/8 steps on G1 lanes (32/G1 columns per warp), up to step
+// m2 = (2*G1*R-1)/8 on 2*G1 lanes, the rest on 4*G1 lanes (8m+1 <= 4*G1*R).
+// The narrow windows are staged in shared memory and widened by row as in
+// heat_window2_kernel; with the column staging that is three buffers of
+// 32*(R+1) values per warp, so the CTA has at most four warps.  The steps are
+// the same expressions as in heat_window_kernel, so the maps are the same.
+template <typename T, int G1, int R, bool TF32OUT>
+__global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, int m2) {
+  constexpr int G2 = 2 * G1, G3 = 4 * G1, W1 = G1 * R, W2 = G2 * R, W3 = G3 * R;
+  constexpr int C1 = 32 / G1, C2 = 32 / G2, C3 = 32 / G3;
+  static_assert(R >= 4 && G1 >= 2 && 32 % G3 == 0, "R >= 4 rows per lane, 4*G1 lanes dividing the warp");
+  __shared__ T slots[4][3][32 * (R + 1)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* b1 = slots[warp][0];
+  T* b2 = slots[warp][1];
+  T* stage = slots[warp][2];
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  const int reach1 = 4 * m1, reach2 = 4 * m2, reach = (int)(4 * a.m);   // launcher: 8m+1 <= W3 <= n
+  const int64_t total = (int64_t)a.S * n;
+  const T c0 = poly9_weight<T>(a, 0), c1 = poly9_weight<T>(a, 1), c2 = poly9_weight<T>(a, 2),
+          c3 = poly9_weight<T>(a, 3), c4 = poly9_weight<T>(a, 4);
+  T* out = reinterpret_cast<T*>(a.out);
+  auto column = [&](int64_t idx) {              // (slice, column) of flattened index idx
+    const int j = idx < total ? (int)(idx / n) : 0;
+    return idx < total ? 1 + (int)(idx - (int64_t)j * n) : 1;
+  };
+  for (int64_t w = warp0; w * C1 < total; w += nwarps) {
+    {                                           // phase 1: C1 columns, G1 lanes each
+      const int gl = lane % G1;
+      const int c = column(w * C1 + lane / G1);
+      const int w0 = window_origin(c, reach1, n, W1);
+      T y[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) y[i] = (w0 + gl * R + i == c - 1) ? (T)1 : (T)0;
+      for (int step = 0; step < m1; ++step)
+        window_step<T, G1, R>(y, gl, w0 == 0, w0 + W1 == n, c0, c1, c2, c3, c4);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < R; ++i) b1[lane * (R + 1) + i] = y[i];
+      __syncwarp();
+    }
+#pragma unroll 1
+    for (int r2 = 0; r2 < C1 / C2; ++r2) {      // phase 2: C2 columns at a time, G2 lanes each
+      const int64_t first2 = w * C1 + r2 * C2;
+      if (first2 >= total) break;               // warp-uniform
+      {
+        const int gl = lane % G2, q = r2 * C2 + lane / G2;   // slot in phase 1
+        const int c = column(w * C1 + q);
+        const int wa = window_origin(c, reach1, n, W1), wb = window_origin(c, reach2, n, W2);
+        T y[R];
+        widen_window<T, G1, R>(y, b1, q, wa, W1, wb, gl);
+        for (int step = m1; step < m2; ++step)
+          window_step<T, G2, R>(y, gl, wb == 0, wb + W2 == n, c0, c1, c2, c3, c4);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) b2[lane * (R + 1) + i] = y[i];
+        __syncwarp();
+      }
+#pragma unroll 1
+      for (int r3 = 0; r3 < C2 / C3; ++r3) {    // phase 3: C3 columns at a time, G3 lanes each
+        const int64_t first3 = first2 + r3 * C3;
+        if (first3 >= total) break;             // warp-uniform
+        const int gl = lane % G3, q = r3 * C3 + lane / G3;   // slot in phase 2
+        const int c = column(first2 + q);
+        const int wb = window_origin(c, reach2, n, W2), wc = window_origin(c, reach, n, W3);
+        T y[R];
+        widen_window<T, G2, R>(y, b2, q, wb, W2, wc, gl);
+        for (int64_t step = m2; step < a.m; ++step)
+          window_step<T, G3, R>(y, gl, wc == 0, wc + W3 == n, c0, c1, c2, c3, c4);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) stage[lane * (R + 1) + i] = y[i];
+        __syncwarp();
+        store_windows<T, G3, R, TF32OUT>(stage, out, first3, total, n, reach, lane);
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // Columns that take the four RK4 stages literally: the forcing column c = 0
 // of every slice, and for a time-dependent operator every column.
 template <typename T, int R>
@@ -810,33 +911,66 @@ static nv_status launch_window2(const HeatArgs& a, int m1, int block, cudaStream
   return nv_cuda_check(cudaGetLastError(), "heat_window2_kernel launch");
 }
 
-// Built window shapes: one window of G lanes x R rows (W = G*R >= 8m+1), or
-// two (GA x R for the first m1 = (GA*R-1)/8 steps, 2*GA x R for the rest).
-// The launcher takes the built option with the fewest row-steps per column
-// (m*W, or m1*GA*R + (m-m1)*2*GA*R); a window as wide as n only when asked
-// for, since the full-width kernel does the same work.  Form 3 takes single
-// windows only, form 4 two-phase windows only, form 0 either.  NV_ENOTSUP,
-// with no launch, when nothing fits.
+template <typename T, int G1, int R>
+static nv_status launch_window3(const HeatArgs& a, int m1, int m2, cudaStream_t s, bool tf32out) {
+  const int block = 128;                        // the kernel's shared memory holds four warps
+  const int64_t warps = ((int64_t)a.S * a.n + 32 / G1 - 1) / (32 / G1);
+  int grid = 0;
+  nv_status st;
+  if constexpr (sizeof(T) == 4) {
+    if (tf32out) {
+      st = persistent_grid(heat_window3_kernel<T, G1, R, true>, block, warps, &grid);
+      if (st != NV_OK) return st;
+      heat_window3_kernel<T, G1, R, true><<<grid, block, 0, s>>>(a, m1, m2);
+      return nv_cuda_check(cudaGetLastError(), "heat_window3_kernel launch");
+    }
+  }
+  st = persistent_grid(heat_window3_kernel<T, G1, R, false>, block, warps, &grid);
+  if (st != NV_OK) return st;
+  heat_window3_kernel<T, G1, R, false><<<grid, block, 0, s>>>(a, m1, m2);
+  return nv_cuda_check(cudaGetLastError(), "heat_window3_kernel launch");
+}
+
+// Built window shapes: one window of G lanes x R rows (W = G*R >= 8m+1); two
+// (GA x R for the first m1 = (GA*R-1)/8 steps, 2*GA x R for the rest); or
+// three (G1, 2*G1, 4*G1 lanes of R rows, switching after m1 = (G1*R-1)/8 and
+// m2 = (2*G1*R-1)/8 steps).  The launcher takes the built option with the
+// fewest row-steps per column (m*W; m1*GA*R + (m-m1)*2*GA*R; and so on); a
+// window as wide as n only when asked for, since the full-width kernel does
+// the same work.  Form 3 takes single windows only, form 4 two-phase windows
+// only, form 5 three-phase windows only, form 0 any.  NV_ENOTSUP, with no
+// launch, when nothing fits.
 static const int kWindow1[][2] = {{8, 4}, {8, 8}, {8, 11}, {16, 8}, {16, 11}, {32, 8}};
 static const int kWindow2[][2] = {{4, 11}, {8, 8}};
+static const int kWindow3[][2] = {{2, 11}};
 
 template <typename T>
 static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form) {
   int64_t best = INT64_MAX;
   int pick = -1, m1 = 0;
-  if (form != 4) {
+  int m2 = 0;
+  if (form == 0 || form == 3) {
     for (int k = 0; k < 6; ++k) {
       const int W = kWindow1[k][0] * kWindow1[k][1];
       if (8 * a.m + 1 > W || W > a.n || (W == a.n && form != 3)) continue;
       if (a.m * W < best) best = a.m * W, pick = k;
     }
   }
-  if (form != 3) {
+  if (form == 0 || form == 4) {
     for (int k = 0; k < 2; ++k) {
       const int WA = kWindow2[k][0] * kWindow2[k][1], WB = 2 * WA, k1 = (WA - 1) / 8;
       if (8 * a.m + 1 > WB || WB > a.n || k1 >= a.m || (WB == a.n && form != 4)) continue;
       const int64_t cost = k1 * WA + (a.m - k1) * WB;
       if (cost < best) best = cost, pick = 6 + k, m1 = k1;
+    }
+  }
+  if (form == 0 || form == 5) {
+    for (int k = 0; k < 1; ++k) {
+      const int W1 = kWindow3[k][0] * kWindow3[k][1], W2 = 2 * W1, W3 = 4 * W1;
+      const int k1 = (W1 - 1) / 8, k2 = (W2 - 1) / 8;
+      if (8 * a.m + 1 > W3 || W3 > a.n || k2 >= a.m || k1 < 1 || (W3 == a.n && form != 5)) continue;
+      const int64_t cost = k1 * W1 + (k2 - k1) * W2 + (a.m - k2) * W3;
+      if (cost < best) best = cost, pick = 8 + k, m1 = k1, m2 = k2;
     }
   }
   switch (pick) {
@@ -848,9 +982,10 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
     case 5: return launch_window_GR<T, 32, 8>(a, block, s, tf32out);
     case 6: return launch_window2<T, 4, 11>(a, m1, block, s, tf32out);
     case 7: return launch_window2<T, 8, 8>(a, m1, block, s, tf32out);
+    case 8: return launch_window3<T, 2, 11>(a, m1, m2, s, tf32out);
     default: break;
   }
-  if (form == 3 || form == 4)
+  if (form >= 3)
     return nv_fail(NV_ENOTSUP, "no built window holds 8m+1 = %lld rows within n = %d",
                    (long long)(8 * a.m + 1), a.n);
   return NV_ENOTSUP;
@@ -874,7 +1009,7 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
   st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   if (st != NV_OK) return st;
   const int form = g_tune.heat_step_form;
-  if (form == 0 || form == 3 || form == 4) {
+  if (form == 0 || form >= 3) {
     st = launch_heat_window<T>(a, block, s, tf32out, form);
     if (st != NV_ENOTSUP || form != 0) return st;
   }

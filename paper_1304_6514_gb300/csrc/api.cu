@@ -434,7 +434,7 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 4: g_tune.scan_block = value; break;
     case 5: g_tune.refine_passes = value; break;
     case 6:
-      if (value < 0 || value > 4) return nv_fail(NV_EINVAL, "heat step form is 0..4");
+      if (value < 0 || value > 5) return nv_fail(NV_EINVAL, "heat step form is 0..5");
       g_tune.heat_step_form = value;
       break;
     case 7:

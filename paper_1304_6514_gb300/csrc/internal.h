@@ -131,7 +131,7 @@ struct nv_tunables {
   int chain_cluster;       // CTAs per cluster of the d <= 512 chain (0 auto, < 0 grid-wide)
   int scan_block;          // slices per block of the tensor-core scan (0 auto)
   int refine_passes;       // float64 correction passes of NV_TF32_REFINE (0 = 1, < 0 none)
-  int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil, 3 / 4 one / two windows
+  int heat_step_form;      // homogeneous heat columns: 0 auto, 1 Horner stages, 2 nine-point stencil, 3 / 4 / 5 one / two / three windows
   int test_barrier_extra;  // test hook: participants that never arrive at the row chain's grid barrier
   int mlp_wgrad_splits;    // split-K of the MLP weight-gradient GEMMs (0 auto)
   int tile_chain_form;     // d > 512 chain: 0 auto, 1 register batches, 2 bulk-copy ring

@@ -102,7 +102,8 @@ def test_null_handles(lib):
     assert lib.nv_maps_info(None, None) == nvp.NV_EINVAL
     assert lib.nv_maps_destroy(None) == nvp.NV_OK
     assert lib.nv_tune_set(99, 1) == nvp.NV_EINVAL
-    assert lib.nv_tune_set(6, 5) == nvp.NV_EINVAL           # heat step form is 0..4
+    assert lib.nv_tune_set(6, 6) == nvp.NV_EINVAL           # heat step form is 0..5
+    assert lib.nv_tune_set(6, 5) == nvp.NV_OK
     assert lib.nv_tune_set(6, 4) == nvp.NV_OK
     assert lib.nv_tune_set(6, -1) == nvp.NV_EINVAL
     assert lib.nv_tune_set(6, 3) == nvp.NV_OK

@@ -75,17 +75,20 @@ def test_heat_step_forms_elementwise(form, n, S, prec, tol):
 @pytest.mark.parametrize("n,S,steps,form", [
     (256, 1024, 10, 3), (256, 1024, 10, 4),      # the heat benchmark's build
     (256, 6, 3, 3), (100, 5, 5, 3), (128, 4, 15, 3), (512, 3, 21, 3), (512, 2, 31, 3), (200, 4, 10, 3),
-    (256, 6, 8, 4), (100, 5, 6, 4), (128, 4, 15, 4), (176, 3, 12, 4), (200, 4, 10, 4)])
+    (256, 6, 8, 4), (100, 5, 6, 4), (128, 4, 15, 4), (176, 3, 12, 4), (200, 4, 10, 4),
+    (256, 1024, 10, 5), (256, 6, 8, 5), (100, 5, 6, 5), (88, 3, 10, 5), (200, 4, 9, 5)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_heat_window_matches_full_width(n, S, steps, form, prec):
     """The windowed nine-point builds (each column integrated only over the
     rows its steps reach: form 3 one window of >= 8m+1 rows, form 4 a narrow
-    window for the first steps and a wide one for the rest) write the same
+    window for the first steps and a wide one for the rest, form 5 three
+    windows of 22, 44 and 88 rows) write the same
     maps as the full-width nine-point build, entry for entry (zeros compare
     equal whatever their sign).  n = 256, S = 1024, m = 10 is the heat
     benchmark's build; the others take every built window shape, windows
-    against both Dirichlet ends, windows as wide as n (n = 128, m = 15) and
-    n = 100, 176, 200 (not multiples of a window's rows per lane)."""
+    against both Dirichlet ends, windows as wide as n (n = 128, m = 15;
+    n = 88, m = 10) and n = 100, 176, 200 (not multiples of a window's rows
+    per lane)."""
     torch = need_gpu()
     T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
     w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
@@ -137,12 +140,12 @@ def test_banded_chain_matches_dense(n, S, steps, prec):
     assert not np.any(A[:, np.abs(rows - cols) > 4 * steps])   # the band the chain relies on
 
 
-@pytest.mark.parametrize("form", [3, 4])
+@pytest.mark.parametrize("form", [3, 4, 5])
 def test_heat_window_refused_when_none_fits(form):
-    """Forms 3 and 4 with no built window holding 8m+1 rows within n are
+    """Forms 3, 4 and 5 with no built window holding 8m+1 rows within n are
     refused by the build with NV_ENOTSUP (n = 96, m = 11 needs 89 rows; the
     single windows are 32, 64, 88, 128, 176 and 256 rows, the two-phase ones
-    end at 88 and 128)."""
+    end at 88 and 128, the three-phase one at 88)."""
     torch = need_gpu()
     n, S, steps = 96, 2, 11
     T = S * steps * 2.0 / (5.0 * (n + 1) ** 2)
