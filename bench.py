@@ -354,6 +354,7 @@ def gpu_peak_probe(torch):
 #   heat FP64 build (two-window form), full size: 475.35 MB for 262 144 columns
 #   heat FP64 build (three-window form), full size: 475.15 MB for 262 144 columns
 #   advection-diffusion FP32 build, S = 8 capture: 475.04 MB for 32 776 columns
+#   advection-diffusion FP32 build with windows, S = 8 capture: 475.46 MB for 32 776 columns
 #   Van der Pol batch build, 512 instances: 503.0 MB for 561 987 584 table bytes
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
@@ -365,6 +366,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "heat_window2_kernel<double,4,11,0>": (475.35e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
+    "advdiff_window_kernel<float>": (475.46e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
 }
@@ -627,10 +629,18 @@ def run_advdiff(args):
         d = nvp.maps_info(maps)
         b = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
         c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-        comp_steps = w.S * (w.dim + 1) * d.steps_per_slice * w.dim
+        m = d.steps_per_slice
+        comp_full = w.S * (w.dim + 1) * m * w.dim
+        # the float32 / bfloat16 build runs its first min(m, 3) steps on 32 x 32
+        # windows (1024 of the 4096 points); the float64 build on the whole grid
+        m1 = 0 if prec == "fp64" else min(m, 3)
+        comp_steps = w.S * (w.dim + 1) * (m1 * 1024 + (m - m1) * w.dim)
         nvp.tune_set(5, 0)
         out[name] = {"build_ms": b, "compose_ms": c, "map_bytes": d.bytes,
                      "build_tflops": FLOP_PER_ADV_COMPONENT_STEP * comp_steps / (b * 1e-3) / 1e12,
+                     "build_full_grid_equivalent_tflops":
+                         FLOP_PER_ADV_COMPONENT_STEP * comp_full / (b * 1e-3) / 1e12,
+                     "flop_per_launch": FLOP_PER_ADV_COMPONENT_STEP * comp_steps,
                      "yT": yT.cpu().numpy()}
         if prec.endswith("_refine"):
             # the approximate chain, then per pass float64 defects + a correction chain
@@ -656,14 +666,21 @@ def run_advdiff(args):
             "config": {"workload": w.name, "n": w.dim, "S": w.S, "l2": "maps (34 GB) larger than L2"},
             "variants": out, "fp32_rel_err_vs_fp64_gpu": rel,
             "time_to_solution_ms": {k: v["build_ms"] + v["compose_ms"] for k, v in out.items()},
-            "roofline": {"bound": "alu", "kernel": "advdiff_block_kernel",
+            "roofline": {"bound": "alu", "kernel": "advdiff_window_kernel<float>",
                          "achieved": f32["build_tflops"], "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": f32["build_tflops"] * 1e12 / FP32_PEAK_NOMINAL,
-                         "traffic": ncu_traffic("advdiff_block_kernel", w.S * (w.dim + 1))[0],
-                         "traffic_source": ncu_traffic("advdiff_block_kernel", 1)[1],
+                         "flop_note": "40 FLOP per point-step over the points integrated: the first 3 steps "
+                                      "on 32 x 32 windows around each column's unit point (exactly zero "
+                                      "outside), the rest on the 64 x 64 grid",
+                         "full_grid_equivalent_tflops": f32["build_full_grid_equivalent_tflops"],
+                         "traffic": (ncu_traffic("advdiff_window_kernel<float>", w.S * (w.dim + 1))[0]
+                                     if "advdiff_window_kernel<float>" in NCU_TRAFFIC_PER_UNIT else None),
+                         "traffic_source": (ncu_traffic("advdiff_window_kernel<float>", 1)[1]
+                                            if "advdiff_window_kernel<float>" in NCU_TRAFFIC_PER_UNIT else
+                                            "no capture of this kernel yet"),
                          "algorithmic_bytes": f32["map_bytes"],
                          "peak_source": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                         "flop_per_launch": FLOP_PER_ADV_COMPONENT_STEP * w.S * (w.dim + 1) * 10 * w.dim},
+                         "flop_per_launch": f32["flop_per_launch"]},
             "chain_roofline": {"bound": "hbm", "kernel": "affine_chain_tile_kernel<float,float>",
                                "achieved": f32["chain_hbm_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                "frac": f32["chain_frac_of_hbm"],

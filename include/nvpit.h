@@ -432,8 +432,13 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          column of banded maps (those of the heat equations, zero off
  *          |r - c| <= 4m) instead of the band around each CTA's rows; the
  *          results are the same bit for bit.
+ *   key 15: 0 (default) or 1: with 1 the float32 / bfloat16 advection-diffusion
+ *          build integrates every column on the whole grid for all m steps;
+ *          by default the first min(m, 3) steps run on 32 x 32 windows
+ *          around each column's unit point (the rows those steps cannot
+ *          reach are exactly zero), with the same maps bit for bit.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13 and 14. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14 and 15. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */

@@ -779,6 +779,169 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_block_kernel(AdvA
   }
 }
 
+// The float32 build with the first steps on windows.  The four Horner stages
+// of a step on the five-point operator carry information one point each, so
+// the column started from the unit point (cx, cy) is exactly zero outside
+// |x - cx| + |y - cy| <= 4k (periodically) after k steps.  For the first
+// m1 <= 3 steps (radius <= 12) each column is integrated on a window of 4 x 4
+// blocks (32 x 32 points) whose block-aligned origin bx0 = floor((cx-12)/8)
+// (mod 8) puts the radius-12 diamond inside it with the cut edges at least 13
+// points from the centre: the zeros read there are the exact values at every
+// stage that reads them (the reach before the last stage is 4*m1 - 1).  So
+// the 64 threads of a CTA carry four columns through those steps, 16 threads
+// (4 x 4 blocks of 8 x 8 points) each, then take the columns one after another
+// through the remaining steps on the whole periodic grid, starting from the
+// windows staged in shared memory.  One step loop serves both (its halo
+// sources are set per segment; a missing neighbour reads a zero edge slot), so
+// the unrolled stages appear once in the code.  Every point is the same
+// floating-point expression as in advdiff_block_kernel (inputs differ at most
+// in the sign of a zero), so the maps are the same; the point-steps per column
+// fall from 4096 m to 1024 m1 + 4096 (m - m1).
+template <typename OutT>
+__global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_window_kernel(AdvArgs a, int m1) {
+  constexpr int n = kAdvNx * kAdvNx;
+  constexpr int TB = kAdvNx / kAdvB;           // 8 blocks per direction
+  constexpr int WB = 4;                        // window edge in blocks
+  constexpr int CPC = kAdvBlockThreads / (WB * WB);   // columns per CTA in the windows
+  constexpr int kZero = kAdvBlockThreads;      // edge slot that stays zero
+  // edges[buffer][side][half][thread]: as advdiff_block_kernel, plus the zero slot
+  __shared__ float4 edges[2][4][2][kAdvBlockThreads + 1];
+  // the windows' blocks as 16 float4 each, one float4 of padding so that the
+  // threads' slots fall on different banks
+  constexpr int kSlot = kAdvB * kAdvB / 4 + 1;
+  __shared__ float4 win[CPC][WB * WB][kSlot];
+  const int t = threadIdx.x, tx = t % TB, ty = t / TB;
+  const int g = t / (WB * WB), lt = t % (WB * WB), lx = lt % WB, ly = lt / WB;
+  const int reach1 = 4 * m1;                   // launcher: 1 <= m1 <= 3, m1 <= m
+  if (t < 16) edges[t >> 3][(t >> 1) & 3][t & 1][kZero] = make_float4(0.f, 0.f, 0.f, 0.f);
+  OutT* out = reinterpret_cast<OutT*>(a.out);
+  const int64_t total = (int64_t)a.S * (n + 1);
+  int buf = 0;
+  for (int64_t w = blockIdx.x; w * CPC < total; w += gridDim.x) {
+#pragma unroll 1
+    for (int seg = 0; seg <= CPC; ++seg) {     // 0: the windows; s >= 1: column s - 1 on the whole grid
+      const bool windows = seg == 0;
+      const int64_t idx = w * CPC + (windows ? g : seg - 1);
+      if (!windows && idx >= total) break;     // uniform over the CTA
+      const int j = idx < total ? (int)(idx / (n + 1)) : 0;
+      const int c = idx < total ? (int)(idx - (int64_t)j * (n + 1)) : 0;   // 0: no unit point
+      const int cx = c >= 1 ? (c - 1) % kAdvNx : reach1, cy = c >= 1 ? (c - 1) / kAdvNx : reach1;
+      const int bx0 = ((cx - reach1 + kAdvNx) / kAdvB) % TB, by0 = ((cy - reach1 + kAdvNx) / kAdvB) % TB;
+      int bx, by, n_left, n_right, n_up, n_down;
+      if (windows) {                           // block (lx, ly) of this group's window
+        bx = (bx0 + lx) % TB;
+        by = (by0 + ly) % TB;
+        n_left = lx > 0 ? t - 1 : kZero;
+        n_right = lx < WB - 1 ? t + 1 : kZero;
+        n_up = ly > 0 ? t - WB : kZero;
+        n_down = ly < WB - 1 ? t + WB : kZero;
+      } else {                                 // block (tx, ty) of the periodic grid
+        bx = tx;
+        by = ty;
+        n_left = ty * TB + (tx + TB - 1) % TB;
+        n_right = ty * TB + (tx + 1) % TB;
+        n_up = ((ty + TB - 1) % TB) * TB + tx;
+        n_down = ((ty + 1) % TB) * TB + tx;
+      }
+      const int ix0 = kAdvB * bx, iy0 = kAdvB * by;
+      float y[kAdvB][kAdvB], v[kAdvB][kAdvB];
+      if (windows) {
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) y[r][q] = ((iy0 + r) * kAdvNx + ix0 + q == c - 1) ? 1.f : 0.f;
+      } else {
+        const int wx = (tx - bx0 + TB) % TB, wy = (ty - by0 + TB) % TB;   // block in the window
+        const bool inside = wx < WB && wy < WB;
+        const float4* src = win[seg - 1][inside ? wy * WB + wx : 0];
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r) {
+          const float4 p0 = src[2 * r], p1 = src[2 * r + 1];
+          y[r][0] = inside ? p0.x : 0.f;
+          y[r][1] = inside ? p0.y : 0.f;
+          y[r][2] = inside ? p0.z : 0.f;
+          y[r][3] = inside ? p0.w : 0.f;
+          y[r][4] = inside ? p1.x : 0.f;
+          y[r][5] = inside ? p1.y : 0.f;
+          y[r][6] = inside ? p1.z : 0.f;
+          y[r][7] = inside ? p1.w : 0.f;
+        }
+      }
+      const int64_t i1 = windows ? m1 : a.m;
+      for (int64_t i = windows ? 0 : m1; i < i1; ++i) {
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) v[r][q] = y[r][q];
+#pragma unroll
+        for (int kk = 4; kk >= 1; --kk) {
+          const float* cw = a.cw32[4 - kk];
+          const float cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
+          float4(*e)[2][kAdvBlockThreads + 1] = edges[buf];
+          e[0][0][t] = make_float4(v[0][0], v[1][0], v[2][0], v[3][0]);
+          e[0][1][t] = make_float4(v[4][0], v[5][0], v[6][0], v[7][0]);
+          e[1][0][t] = make_float4(v[0][7], v[1][7], v[2][7], v[3][7]);
+          e[1][1][t] = make_float4(v[4][7], v[5][7], v[6][7], v[7][7]);
+          e[2][0][t] = make_float4(v[0][0], v[0][1], v[0][2], v[0][3]);
+          e[2][1][t] = make_float4(v[0][4], v[0][5], v[0][6], v[0][7]);
+          e[3][0][t] = make_float4(v[7][0], v[7][1], v[7][2], v[7][3]);
+          e[3][1][t] = make_float4(v[7][4], v[7][5], v[7][6], v[7][7]);
+          __syncthreads();
+          const float4 l0 = e[1][0][n_left], l1 = e[1][1][n_left];
+          const float4 r0 = e[0][0][n_right], r1 = e[0][1][n_right];
+          const float4 u0 = e[3][0][n_up], u1 = e[3][1][n_up];
+          const float4 d0 = e[2][0][n_down], d1 = e[2][1][n_down];
+          const float hl[kAdvB] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+          const float hr[kAdvB] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+          const float hu[kAdvB] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+          const float hd[kAdvB] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+          float prev[kAdvB];                   // row r - 1 before this stage
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) prev[q] = hu[q];
+#pragma unroll
+          for (int r = 0; r < kAdvB; ++r) {
+            float nrow[kAdvB];
+#pragma unroll
+            for (int q = 0; q < kAdvB; ++q) {
+              const float xm = q == 0 ? hl[r] : v[r][q - 1];
+              const float xp = q == kAdvB - 1 ? hr[r] : v[r][q + 1];
+              const float yp = r == kAdvB - 1 ? hd[q] : v[r + 1][q];
+              float acc = fmaf(c0, v[r][q], y[r][q]);
+              acc = fmaf(cxm, xm, acc);
+              acc = fmaf(cxp, xp, acc);
+              acc = fmaf(cym, prev[q], acc);
+              nrow[q] = fmaf(cyp, yp, acc);
+            }
+#pragma unroll
+            for (int q = 0; q < kAdvB; ++q) {
+              prev[q] = v[r][q];
+              v[r][q] = nrow[q];
+            }
+          }
+          buf ^= 1;
+        }
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r)
+#pragma unroll
+          for (int q = 0; q < kAdvB; ++q) y[r][q] = v[r][q];
+      }
+      if (windows) {
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r) {
+          win[g][lt][2 * r] = make_float4(y[r][0], y[r][1], y[r][2], y[r][3]);
+          win[g][lt][2 * r + 1] = make_float4(y[r][4], y[r][5], y[r][6], y[r][7]);
+        }
+        __syncthreads();
+      } else {
+        OutT* col = out + ((int64_t)j * (n + 1) + c) * n;
+#pragma unroll
+        for (int r = 0; r < kAdvB; ++r) adv_store_row(col + (iy0 + r) * kAdvNx + ix0, y[r]);
+      }
+    }
+    __syncthreads();                           // the windows are rewritten next
+  }
+}
+
 // Serial fine solve of the advection-diffusion system (one CTA, S*m steps).
 template <typename T>
 __global__ void __launch_bounds__(256) advdiff_serial_kernel(AdvArgs a, const double* y0, double* yT) {
@@ -1174,7 +1337,17 @@ nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
   } else {
     // columns start at j * (n + 1) * n values: 16-byte aligned for the
     // vector stores since n = 4096 and the map buffer is 256-byte aligned
-    if (M->prec == NV_BF16_REFINE) {
+    // windows for the first min(m, 3) steps unless the whole-grid form is asked for
+    const int m1 = g_tune.adv_build_form == 1 ? 0 : (int)std::min<int64_t>(M->m, 3);
+    if (m1 > 0 && M->prec == NV_BF16_REFINE) {
+      st = persistent_grid(advdiff_window_kernel<uint16_t>, kAdvBlockThreads, cols / 2 + 2, &grid);
+      if (st != NV_OK) return st;
+      advdiff_window_kernel<uint16_t><<<grid, kAdvBlockThreads, 0, s>>>(a, m1);
+    } else if (m1 > 0) {
+      st = persistent_grid(advdiff_window_kernel<float>, kAdvBlockThreads, cols / 2 + 2, &grid);
+      if (st != NV_OK) return st;
+      advdiff_window_kernel<float><<<grid, kAdvBlockThreads, 0, s>>>(a, m1);
+    } else if (M->prec == NV_BF16_REFINE) {
       st = persistent_grid(advdiff_block_kernel<uint16_t>, kAdvBlockThreads, cols * 2, &grid);
       if (st != NV_OK) return st;
       advdiff_block_kernel<uint16_t><<<grid, kAdvBlockThreads, 0, s>>>(a);

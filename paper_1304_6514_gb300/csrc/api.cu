@@ -465,6 +465,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "chain band use is 0 or 1");
       g_tune.chain_dense = value;
       break;
+    case 15:
+      if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "advection-diffusion build form is 0 or 1");
+      g_tune.adv_build_form = value;
+      break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }
   return NV_OK;

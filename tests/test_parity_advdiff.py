@@ -104,6 +104,45 @@ def test_advdiff_fp32_refined_full_size():
     _check(torch, workloads.advdiff2d(), "fp32_refine", [0, 511], 1e-5, 1e-7)
 
 
+@pytest.mark.parametrize("S,m", [(3, 10), (2, 1), (2, 2), (4, 3), (3, 4), (5, 7)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16_refine"])
+def test_advdiff_window_build_matches_whole_grid(prec, S, m):
+    """The float32 / bfloat16 build integrates the first min(m, 3) steps of
+    each column on a 32 x 32 window around its unit point (the points those
+    steps cannot reach are exactly zero) and the rest on the whole periodic
+    grid: every map entry equals the whole-grid build's (tunable 15 = 1) bit
+    for bit, for every column of every slice (windows across the periodic
+    seams included), with m = 10 as in the benchmark, m <= 3 (the windows
+    only) and m = 4, 7; and the entries farther than 4m points (periodic
+    Manhattan distance) from a column's unit point are exactly zero."""
+    torch = need_gpu()
+    w = workloads.advdiff2d(S=S, T=S * m * 2e-4, dt=2e-4)
+    assert nv.workload_steps(w) == m
+    r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
+    got = {}
+    for form in (0, 1):
+        nvp.tune_set(15, form)
+        try:
+            maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"),
+                                         nvp.steps("rk4", w.dt, 0, prec))
+            nvp.maps_check(maps)
+            got[form] = nvp.maps_slice(maps, 0, w.S).cpu()
+            maps.destroy()
+        finally:
+            nvp.tune_set(15, 0)
+    assert torch.equal(got[0], got[1])
+    n = w.dim
+    blocks = got[0].float().numpy().reshape(w.S, n + 1, n)     # [slice, column, point]
+    assert not np.any(blocks[:, 0])                            # b_j = 0: no forcing
+    pts = np.arange(n)
+    px, py = pts % 64, pts // 64
+    for c in (1, 13, 64, 65, 2080, 4033, 4096):
+        cx, cy = (c - 1) % 64, (c - 1) // 64
+        dx = np.minimum((px - cx) % 64, (cx - px) % 64)
+        dy = np.minimum((py - cy) % 64, (cy - py) % 64)
+        assert not np.any(blocks[:, c, dx + dy > 4 * m])
+
+
 @pytest.mark.parametrize("S", [1, 2, 5])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16_refine"])
 def test_tiled_chain_ring_and_register_kernels_agree(prec, S):
