@@ -111,26 +111,34 @@ def test_heat_window_matches_full_width(n, S, steps, form, prec):
     assert not np.any(A[:, outside])
 
 
-@pytest.mark.parametrize("n,S,steps", [(256, 1024, 10), (256, 7, 3), (128, 5, 2), (64, 3, 1), (192, 6, 5),
-                                       (256, 4, 40)])
+@pytest.mark.parametrize("n,S,steps,rhs_name", [(256, 1024, 10, "heat1d"), (256, 7, 3, "heat1d"),
+                                                (128, 5, 2, "heat1d"), (64, 3, 1, "heat1d"),
+                                                (192, 6, 5, "heat1d"), (256, 4, 40, "heat1d"),
+                                                (128, 5, 4, "heat1d_varcoef")])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_refine"])
-def test_banded_chain_matches_dense(n, S, steps, prec):
+def test_banded_chain_matches_dense(n, S, steps, rhs_name, prec):
     """The heat maps are zero off the band |r - c| <= 4m, and the cluster
     chain then reads only the columns of that band around each CTA's rows
     (rounded out to 16 so that every thread keeps its columns and their
     order): every boundary state equals the dense chain's (tunable 14 = 1)
     bit for bit, for the plain float64 / float32 compositions and the
     pipelined float64 refinement.  n = 256, S = 1024, m = 10 is the heat
-    benchmark; m = 40 at n = 256 has a band wider than the matrix (dense)."""
+    benchmark; m = 40 at n = 256 has a band wider than the matrix (dense);
+    the variable-coefficient equation (time-dependent three-point operator)
+    has the same band."""
     torch = need_gpu()
-    T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
-    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * 1.25 * (n + 1) ** 2)
+    if rhs_name == "heat1d":
+        w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    else:
+        w = workloads.Workload("v", "heat1d_varcoef", n, 0.0, T, S, "rk4", T / (S * steps), 0, "affine",
+                               y0=np.sin(np.pi * nv.heat1d_grid(n)))
     assert nv.workload_steps(w) == steps
     got = {}
     for dense in (0, 1):
         nvp.tune_set(14, dense)
         try:
-            _, A, b, yT, lam = _heat(torch, w, prec)
+            _, A, b, yT, lam = _heat(torch, w, prec, rhs_name)
         finally:
             nvp.tune_set(14, 0)
         got[dense] = (yT, lam)
