@@ -37,41 +37,6 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 FP64_PEAK_NOMINAL = 1.25e12          # FLOP/s, FMA = 2 (GB300 FP64)
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9
 FLOP_PER_COMPONENT_STEP = 20         # Horner-form RK4 step of the 3-point stencil
-# Window shapes (lanes per column, rows per lane) built for the heat equation's
-# homogeneous columns: one window of W = lanes * rows >= 8m+1 (the rows that m
-# nine-point steps reach from one basis vector), or two (lanes x rows for the
-# first m1 = (W-1) // 8 steps, twice the lanes for the rest), or three (the
-# lanes doubling twice).  The build takes
-# the option with the fewest row-steps per column, windows narrower than n only.
-HEAT_WINDOWS = ((8, 4), (8, 8), (8, 11), (16, 8), (16, 11), (32, 8))
-HEAT_WINDOWS2 = ((4, 11), (8, 8))
-HEAT_WINDOWS3 = ((2, 11),)          # lanes of the first of three windows (then x2, x4), rows
-
-
-def heat_window(n, m):
-    """(row-steps per homogeneous column, kernel name) of the FP64 heat build."""
-    best = None
-    for g, r in HEAT_WINDOWS:
-        if 8 * m + 1 <= g * r < n and (best is None or m * g * r < best[0]):
-            best = (m * g * r, f"heat_window_kernel<double,{g},{r},0>")
-    for g, r in HEAT_WINDOWS2:
-        wa, m1 = g * r, (g * r - 1) // 8
-        if 8 * m + 1 <= 2 * wa < n and m1 < m:
-            cost = m1 * wa + (m - m1) * 2 * wa
-            if best is None or cost < best[0]:
-                best = (cost, f"heat_window2_kernel<double,{g},{r},0>")
-    for g, r in HEAT_WINDOWS3:
-        w1, m1, m2 = g * r, (g * r - 1) // 8, (2 * g * r - 1) // 8
-        if 8 * m + 1 <= 4 * w1 < n and 1 <= m1 and m2 < m:
-            cost = m1 * w1 + (m2 - m1) * 2 * w1 + (m - m2) * 4 * w1
-            if best is None or cost < best[0]:
-                best = (cost, f"heat_window3_kernel<double,{g},{r},0>")
-    if best is None:
-        r = max(4, 1 << (max(1, -(-n // 32)) - 1).bit_length())
-        best = (m * n, f"heat_poly9_kernel<double,{r},0>")
-    return best
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,9 +239,11 @@ def time_variant(nvp, torch, w, prec, K, W, flush, stream):
     build = [e[0].elapsed_time(e[1]) for e in ev]
     comp = [e[1].elapsed_time(e[2]) for e in ev]
     tot = [a + b for a, b in zip(build, comp)]
-    m = nvp.maps_info(maps).steps_per_slice
+    info = nvp.maps_info(maps)
     maps.destroy()
-    return {"build_ms": build, "compose_ms": comp, "step_ms": tot, "yT": yT.cpu().numpy(), "m": m}
+    return {"build_ms": build, "compose_ms": comp, "step_ms": tot, "yT": yT.cpu().numpy(),
+            "m": info.steps_per_slice, "work_per_slice": info.work_per_slice,
+            "build_kernel": info.build_kernel.decode()}
 
 
 def time_serial_gpu(nvp, torch, w, stream, reps=3):
@@ -365,7 +332,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "heat_poly9_kernel<double,8,0>": (207.06e6 / 131072, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "heat_window2_kernel<double,4,11,0>": (475.35e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
-    "advdiff_block_kernel": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
+    "advdiff_block_kernel<float>": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "advdiff_window_kernel<float>": (475.46e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
@@ -631,12 +598,12 @@ def run_advdiff(args):
         c = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
         m = d.steps_per_slice
         comp_full = w.S * (w.dim + 1) * m * w.dim
-        # the float32 / bfloat16 build runs its first min(m, 3) steps on 32 x 32
-        # windows (1024 of the 4096 points); the float64 build on the whole grid
-        m1 = 0 if prec == "fp64" else min(m, 3)
-        comp_steps = w.S * (w.dim + 1) * (m1 * 1024 + (m - m1) * w.dim)
+        # the build reports the point-steps it integrated: the float32 / bfloat16
+        # build runs its first min(m, 3) steps on 32 x 32 windows (1024 of the
+        # 4096 points), the float64 build all steps on the whole grid
+        comp_steps = w.S * d.work_per_slice
         nvp.tune_set(5, 0)
-        out[name] = {"build_ms": b, "compose_ms": c, "map_bytes": d.bytes,
+        out[name] = {"build_ms": b, "compose_ms": c, "map_bytes": d.bytes, "build_kernel": d.build_kernel.decode(),
                      "build_tflops": FLOP_PER_ADV_COMPONENT_STEP * comp_steps / (b * 1e-3) / 1e12,
                      "build_full_grid_equivalent_tflops":
                          FLOP_PER_ADV_COMPONENT_STEP * comp_full / (b * 1e-3) / 1e12,
@@ -666,17 +633,17 @@ def run_advdiff(args):
             "config": {"workload": w.name, "n": w.dim, "S": w.S, "l2": "maps (34 GB) larger than L2"},
             "variants": out, "fp32_rel_err_vs_fp64_gpu": rel,
             "time_to_solution_ms": {k: v["build_ms"] + v["compose_ms"] for k, v in out.items()},
-            "roofline": {"bound": "alu", "kernel": "advdiff_window_kernel<float>",
+            "roofline": {"bound": "alu", "kernel": f32["build_kernel"],
                          "achieved": f32["build_tflops"], "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": f32["build_tflops"] * 1e12 / FP32_PEAK_NOMINAL,
                          "flop_note": "40 FLOP per point-step over the points integrated: the first 3 steps "
                                       "on 32 x 32 windows around each column's unit point (exactly zero "
                                       "outside), the rest on the 64 x 64 grid",
                          "full_grid_equivalent_tflops": f32["build_full_grid_equivalent_tflops"],
-                         "traffic": (ncu_traffic("advdiff_window_kernel<float>", w.S * (w.dim + 1))[0]
-                                     if "advdiff_window_kernel<float>" in NCU_TRAFFIC_PER_UNIT else None),
-                         "traffic_source": (ncu_traffic("advdiff_window_kernel<float>", 1)[1]
-                                            if "advdiff_window_kernel<float>" in NCU_TRAFFIC_PER_UNIT else
+                         "traffic": (ncu_traffic(f32["build_kernel"], w.S * (w.dim + 1))[0]
+                                     if f32["build_kernel"] in NCU_TRAFFIC_PER_UNIT else None),
+                         "traffic_source": (ncu_traffic(f32["build_kernel"], 1)[1]
+                                            if f32["build_kernel"] in NCU_TRAFFIC_PER_UNIT else
                                             "no capture of this kernel yet"),
                          "algorithmic_bytes": f32["map_bytes"],
                          "peak_source": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)",
@@ -1030,9 +997,11 @@ def main():
     units = traj_steps(w, m)
     value, dev_s, _ = aggregate_over_ranks(units * K, sum(res["step_ms"]) * 1e-3)
     build_s = statistics.mean(res["build_ms"]) * 1e-3
-    row_steps, build_kernel = heat_window(w.dim, m)
-    rows = row_steps / m                              # mean rows integrated per step and column
-    flop = FLOP_PER_COMPONENT_STEP * units * rows      # over the rows each column is integrated on
+    # the build reports the point-steps it integrated (the windowed builds count
+    # only the rows each column's steps reach) and its kernel
+    build_kernel = res["build_kernel"]
+    flop = FLOP_PER_COMPONENT_STEP * w.S * res["work_per_slice"]
+    rows = res["work_per_slice"] / ((w.dim + 1) * m)   # mean rows integrated per step and column
     flop_full = FLOP_PER_COMPONENT_STEP * units * w.dim
     achieved = flop / build_s
 

@@ -152,6 +152,11 @@ typedef struct {
   int64_t elems_per_slice;
   int64_t bytes;           /* total bytes of map data        */
   int32_t elem_bytes;      /* 8 (double) or 4 (float)        */
+  int32_t band;            /* AFFINE: 0 dense; > 0: A_j[r][c] == 0 whenever |r - c| >= band */
+  int64_t work_per_slice;  /* point-steps the last build integrated per slice: rows times fine
+                              steps, summed over the slice's columns (a windowed build counts
+                              the rows it integrates); 0 where not recorded */
+  char build_kernel[64];   /* the last build's main kernel, "" where not recorded */
 } nv_maps_desc;
 
 /* Computation phase (Figure "pseudocode"; eqs. lineardiscrete and

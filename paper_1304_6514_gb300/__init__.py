@@ -14,7 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
-from ctypes import POINTER, Structure, byref, c_double, c_int32, c_int64, c_void_p
+from ctypes import POINTER, Structure, byref, c_char, c_double, c_int32, c_int64, c_void_p
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libnvpit.so")
@@ -49,7 +49,8 @@ class NvMapsDesc(Structure):
     _fields_ = [("map", c_int32), ("prec", c_int32), ("scheme", c_int32), ("S", c_int32),
                 ("dim", c_int32), ("per_dim", c_int32), ("steps_per_slice", c_int64),
                 ("h", c_double), ("elems_per_slice", c_int64), ("bytes", c_int64),
-                ("elem_bytes", c_int32)]
+                ("elem_bytes", c_int32), ("band", c_int32), ("work_per_slice", c_int64),
+                ("build_kernel", c_char * 64)]
 
 
 class NvError(RuntimeError):

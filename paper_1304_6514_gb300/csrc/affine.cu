@@ -16,7 +16,10 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <stdarg.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -1103,12 +1106,32 @@ static nv_status launch_window3(const HeatArgs& a, int m1, int m2, cudaStream_t 
 // the same work.  Form 3 takes single windows only, form 4 two-phase windows
 // only, form 5 three-phase windows only, form 0 any.  NV_ENOTSUP, with no
 // launch, when nothing fits.
+// What a heat build launched for the homogeneous columns: the point-steps it
+// integrates per column and the kernel, for nv_maps_info.
+struct BuildInfo {
+  int64_t work_per_column = 0;
+  char kernel[64] = "";
+};
+
+template <typename T>
+static const char* type_name() { return sizeof(T) == 8 ? "double" : "float"; }
+
+static void note_build(BuildInfo* bi, int64_t work, const char* fmt, ...) {
+  if (!bi) return;
+  bi->work_per_column = work;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(bi->kernel, sizeof(bi->kernel), fmt, ap);
+  va_end(ap);
+}
+
 static const int kWindow1[][2] = {{8, 4}, {8, 8}, {8, 11}, {16, 8}, {16, 11}, {32, 8}};
 static const int kWindow2[][2] = {{4, 11}, {8, 8}};
 static const int kWindow3[][2] = {{2, 11}};
 
 template <typename T>
-static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form) {
+static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form,
+                                    BuildInfo* bi) {
   int64_t best = INT64_MAX;
   int pick = -1, m1 = 0;
   int m2 = 0;
@@ -1136,6 +1159,14 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
       if (cost < best) best = cost, pick = 8 + k, m1 = k1, m2 = k2;
     }
   }
+  const int t32 = tf32out ? 1 : 0;
+  if (pick >= 0 && pick < 6)
+    note_build(bi, best, "heat_window_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow1[pick][0], kWindow1[pick][1], t32);
+  else if (pick >= 6 && pick < 8)
+    note_build(bi, best, "heat_window2_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow2[pick - 6][0],
+               kWindow2[pick - 6][1], t32);
+  else if (pick == 8)
+    note_build(bi, best, "heat_window3_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow3[0][0], kWindow3[0][1], t32);
   switch (pick) {
     case 0: return launch_window_GR<T, 8, 4>(a, block, s, tf32out);
     case 1: return launch_window_GR<T, 8, 8>(a, block, s, tf32out);
@@ -1155,12 +1186,14 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
 }
 
 template <typename T, int R>
-static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) {
+static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out, BuildInfo* bi) {
   const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
   const int block = 32 * warps_per_cta;
+  const int t32 = tf32out ? 1 : 0;
   int grid = 0;
   nv_status st;
   if (a.varcoef) {
+    note_build(bi, (int64_t)a.n * a.m, "heat_literal_kernel<%s,%d>", type_name<T>(), R);
     st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S * (a.n + 1), &grid);
     if (st != NV_OK) return st;
     heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 1);
@@ -1173,11 +1206,12 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
   if (st != NV_OK) return st;
   const int form = g_tune.heat_step_form;
   if (form == 0 || form >= 3) {
-    st = launch_heat_window<T>(a, block, s, tf32out, form);
+    st = launch_heat_window<T>(a, block, s, tf32out, form, bi);
     if (st != NV_ENOTSUP || form != 0) return st;
   }
   if constexpr (R >= 4) {
     if (g_tune.heat_step_form != 1 && a.n % R == 0) {
+      note_build(bi, (int64_t)a.n * a.m, "heat_poly9_kernel<%s,%d,%d>", type_name<T>(), R, t32);
       if constexpr (sizeof(T) == 4) {
         if (tf32out) {
           st = persistent_grid(heat_poly9_kernel<T, R, true>, block, (int64_t)a.S * a.n, &grid);
@@ -1192,6 +1226,7 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
       return nv_cuda_check(cudaGetLastError(), "heat_poly9_kernel launch");
     }
   }
+  note_build(bi, (int64_t)a.n * a.m, "heat_horner_kernel<%s,%d,%d>", type_name<T>(), R, t32);
   if constexpr (sizeof(T) == 4) {
     if (tf32out) {
       st = persistent_grid(heat_horner_kernel<T, R, true>, block, (int64_t)a.S * a.n, &grid);
@@ -1207,18 +1242,18 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out) 
 }
 
 template <typename T>
-static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s, bool tf32out) {
+static nv_status launch_heat_typed(const HeatArgs& a, int R, cudaStream_t s, bool tf32out, BuildInfo* bi) {
   switch (R) {
-    case 1: return launch_heat_R<T, 1>(a, s, tf32out);
-    case 2: return launch_heat_R<T, 2>(a, s, tf32out);
-    case 4: return launch_heat_R<T, 4>(a, s, tf32out);
-    case 8: return launch_heat_R<T, 8>(a, s, tf32out);
-    case 16: return launch_heat_R<T, 16>(a, s, tf32out);
+    case 1: return launch_heat_R<T, 1>(a, s, tf32out, bi);
+    case 2: return launch_heat_R<T, 2>(a, s, tf32out, bi);
+    case 4: return launch_heat_R<T, 4>(a, s, tf32out, bi);
+    case 8: return launch_heat_R<T, 8>(a, s, tf32out, bi);
+    case 16: return launch_heat_R<T, 16>(a, s, tf32out, bi);
     default: return nv_fail(NV_ENOTSUP, "heat equation dimension %d exceeds 512", a.n);
   }
 }
 
-nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s);
+nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s);
 nv_status launch_wave_build(const nv_maps* M, cudaStream_t s);
 
 nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
@@ -1231,8 +1266,14 @@ nv_status launch_affine_build(nv_maps* M, cudaStream_t s) {
     // four rows on each side (four stages), so A_j is zero off the band
     // |r - c| <= 4m
     M->band = M->m < (1 << 28) ? (int32_t)(4 * M->m + 1) : 0;
-    if (M->prec == NV_FP64) return launch_heat_typed<double>(a, R, s, false);
-    return launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE);
+    BuildInfo bi;
+    const nv_status st = M->prec == NV_FP64 ? launch_heat_typed<double>(a, R, s, false, &bi)
+                                            : launch_heat_typed<float>(a, R, s, M->prec == NV_TF32_REFINE, &bi);
+    // the forcing column (full width; every column for the variable-coefficient
+    // equation, whose kernel records the work of one) and the homogeneous ones
+    M->work_per_slice = (int64_t)M->dim * M->m + (int64_t)M->dim * bi.work_per_column;
+    memcpy(M->build_kernel, bi.kernel, sizeof(M->build_kernel));
+    return st;
   }
   if (M->rhs_kind == NV_RHS_ADVDIFF2D) return launch_advdiff_build(M, s);
   if (M->rhs_kind == NV_RHS_WAVE_CHEB) return launch_wave_build(M, s);
@@ -1323,7 +1364,7 @@ static AdvArgs adv_args(const nv_maps* M) {
   return a;
 }
 
-nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
+nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s) {
   if (M->dim != kAdvNx * kAdvNx) return nv_fail(NV_ENOTSUP, "advection-diffusion is built for a 64 x 64 grid");
   if (M->scheme != NV_RK4) return nv_fail(NV_ENOTSUP, "affine maps are built with RK4");
   const AdvArgs a = adv_args(M);
@@ -1331,6 +1372,8 @@ nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
   nv_status st;
   const int64_t cols = (int64_t)M->S * (M->dim + 1);
   if (M->prec == NV_FP64) {
+    M->work_per_slice = (int64_t)(M->dim + 1) * M->dim * M->m;
+    snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");
     st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);
     if (st != NV_OK) return st;
     advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
@@ -1339,6 +1382,10 @@ nv_status launch_advdiff_build(const nv_maps* M, cudaStream_t s) {
     // vector stores since n = 4096 and the map buffer is 256-byte aligned
     // windows for the first min(m, 3) steps unless the whole-grid form is asked for
     const int m1 = g_tune.adv_build_form == 1 ? 0 : (int)std::min<int64_t>(M->m, 3);
+    const char* out_t = M->prec == NV_BF16_REFINE ? "uint16_t" : "float";
+    M->work_per_slice = (int64_t)(M->dim + 1) * (1024 * m1 + (int64_t)M->dim * (M->m - m1));
+    snprintf(M->build_kernel, sizeof(M->build_kernel), m1 > 0 ? "advdiff_window_kernel<%s>" : "advdiff_block_kernel<%s>",
+             out_t);
     if (m1 > 0 && M->prec == NV_BF16_REFINE) {
       st = persistent_grid(advdiff_window_kernel<uint16_t>, kAdvBlockThreads, cols / 2 + 2, &grid);
       if (st != NV_OK) return st;

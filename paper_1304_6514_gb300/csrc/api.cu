@@ -386,6 +386,10 @@ extern "C" nv_status nv_maps_info(const nv_maps* maps, nv_maps_desc* out) {
   out->elems_per_slice = maps->elems_per_slice;
   out->bytes = maps->bytes;
   out->elem_bytes = maps->elem_bytes;
+  out->band = maps->band;
+  out->work_per_slice = maps->work_per_slice;
+  memcpy(out->build_kernel, maps->build_kernel, sizeof(out->build_kernel));
+  out->build_kernel[sizeof(out->build_kernel) - 1] = '\0';
   return NV_OK;
 }
 

@@ -46,6 +46,9 @@ struct nv_maps {
   // 0: dense maps; > 0: every A_j[r][c] with |r - c| >= band is exactly zero
   // (set by the build where the scheme fixes it; the chains then skip them)
   int32_t band;
+  // what the last build ran: point-steps integrated per slice, main kernel
+  int64_t work_per_slice;
+  char build_kernel[64];
   // reduced-precision composition scratch (NV_TF32_REFINE), allocated lazily
   void* scan_ws;
   size_t scan_ws_bytes;

@@ -133,3 +133,36 @@ def test_null_handles(lib):
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
     h = ctypes.c_void_p()
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the C
+    compiler's size and field offsets (a field added on one side only would
+    shift every later one)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    mirrors = {"nv_rhs": nvp.NvRhs, "nv_samples": nvp.NvSamples, "nv_steps": nvp.NvSteps,
+               "nv_maps_desc": nvp.NvMapsDesc}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "nvpit.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", include, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)

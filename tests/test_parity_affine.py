@@ -148,6 +148,43 @@ def test_banded_chain_matches_dense(n, S, steps, rhs_name, prec):
     assert not np.any(A[:, np.abs(rows - cols) > 4 * steps])   # the band the chain relies on
 
 
+def test_build_reports_work_kernel_and_band():
+    """nv_maps_info reports what the build ran: the point-steps integrated per
+    slice (the forcing column at full width, each homogeneous column over its
+    windows: 22·2 + 44·3 + 88·5 = 616 row-steps for m = 10), the kernel, and
+    the band |r - c| <= 4m of the heat maps; the full-width form integrates
+    all d rows; the advection-diffusion maps are dense, and their float32
+    build integrates 3 steps on 32 x 32 windows and 7 on the 64 x 64 grid."""
+    torch = need_gpu()
+    n, S, steps = 256, 4, 10
+    T = S * steps * 2.0 / (5.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    r = nvp.rhs("heat1d", n, w.params)
+    for form, work, kernel in ((0, n * steps + n * 616, "heat_window3_kernel<double,2,11,0>"),
+                               (2, (n + 1) * n * steps, "heat_poly9_kernel<double,8,0>")):
+        nvp.tune_set(6, form)
+        try:
+            maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), nvp.steps("rk4", w.dt))
+        finally:
+            nvp.tune_set(6, 0)
+        d = nvp.maps_info(maps)
+        assert (d.work_per_slice, d.build_kernel.decode(), d.band) == (work, kernel, 4 * steps + 1)
+        maps.destroy()
+    wa = workloads.advdiff2d(S=2, T=2 * 10 * 2e-4, dt=2e-4)
+    ra = nvp.rhs("advdiff2d", wa.dim, wa.params[:3])
+    for form, work, kernel in ((0, 4097 * (3 * 1024 + 7 * 4096), "advdiff_window_kernel<float>"),
+                               (1, 4097 * 4096 * 10, "advdiff_block_kernel<float>")):
+        nvp.tune_set(15, form)
+        try:
+            maps = nvp.build_propagators(ra, wa.t0, wa.T, wa.S, nvp.samples("affine"),
+                                         nvp.steps("rk4", wa.dt, 0, "fp32"))
+        finally:
+            nvp.tune_set(15, 0)
+        d = nvp.maps_info(maps)
+        assert (d.work_per_slice, d.build_kernel.decode(), d.band) == (work, kernel, 0)
+        maps.destroy()
+
+
 @pytest.mark.parametrize("form", [3, 4, 5])
 def test_heat_window_refused_when_none_fits(form):
     """Forms 3, 4 and 5 with no built window holding 8m+1 rows within n are
