@@ -1199,11 +1199,9 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out, 
     heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 1);
     return nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   }
-  // the forcing columns: one warp each, in CTAs of two warps so that they
-  // spread over every SM (S = 1024 warps in CTAs of eight left 24 SMs idle)
-  st = persistent_grid(heat_literal_kernel<T, R>, 64, (int64_t)a.S, &grid);
+  st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S, &grid);
   if (st != NV_OK) return st;
-  heat_literal_kernel<T, R><<<grid, 64, 0, s>>>(a, 0);
+  heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
   st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   if (st != NV_OK) return st;
   const int form = g_tune.heat_step_form;
