@@ -520,6 +520,27 @@ __global__ void heat_serial_kernel(HeatArgs a, const double* y0, double* yT) {
 // d_j = g^j(lt_j) - lt_{j+1}, one warp per slice j integrating the full
 // inhomogeneous right-hand side over slice j from lt_j with literal RK4
 // stages in float64 (lt has S+1 rows of n, d has S rows).
+// The forcing column b_j of float64 maps (time-invariant operator): the
+// slice's forced solve from 0, in the nine-point form of the defects (the
+// forcing lies along the sine eigenvector of the operator, so each RK4 step
+// adds phi times that vector; the literal stages where the form does not
+// apply), one warp per slice, stored like the homogeneous columns.
+template <int R>
+__global__ void __launch_bounds__(256) heat_forcing_kernel(HeatArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  double* out = reinterpret_cast<double*>(a.out);
+  for (int64_t j = warp0; j < a.S; j += nwarps) {
+    double y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = 0.0;
+    heat_forced_solve<R>(a, y, j, lane);
+    store_column<R, false>(y, column_stage<R, double>(), out + j * (int64_t)(n + 1) * n, lane, n);
+  }
+}
+
 template <int R>
 __global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const double* lt, double* d) {
   const int lane = threadIdx.x & 31;
@@ -1199,10 +1220,17 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out, 
     heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 1);
     return nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   }
-  st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S, &grid);
-  if (st != NV_OK) return st;
-  heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
-  st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
+  if constexpr (sizeof(T) == 8) {              // the forcing columns
+    st = persistent_grid(heat_forcing_kernel<R>, block, (int64_t)a.S, &grid);
+    if (st != NV_OK) return st;
+    heat_forcing_kernel<R><<<grid, block, 0, s>>>(a);
+    st = nv_cuda_check(cudaGetLastError(), "heat_forcing_kernel launch");
+  } else {
+    st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S, &grid);
+    if (st != NV_OK) return st;
+    heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
+    st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
+  }
   if (st != NV_OK) return st;
   const int form = g_tune.heat_step_form;
   if (form == 0 || form >= 3) {

@@ -242,26 +242,23 @@ __device__ __forceinline__ Rk4Poly9 rk4_poly9(double h, double u0, double uh, do
 
 __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
-// Float64 defect of slice j (the residual correction the Conclusion
-// proposes): d_j = g^j(lt_j) - lt_{j+1}, one RK4 fine solve of the forced
-// equation from lt_j over the slice.  One warp; lane l holds rows
-// l*R .. l*R+R-1.  Where every lane holds 4 to 8 whole rows (4 <= R <= 8,
+// One RK4 fine solve of the forced equation over slice j, float64, from the
+// state in y (one warp; lane l holds rows l*R .. l*R+R-1; rows past n - 1
+// hold 0).  Where every lane holds 4 to 8 whole rows (4 <= R <= 8,
 // n % R == 0) the steps take the nine-point form (13 instead of 24 float64
 // operations per row and step: the stencil's weights and phi for steps
 // i0 .. i0+14 are computed one step per lane and broadcast by shuffle);
 // otherwise the literal stages.
 template <int R>
-__device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const double* lt, double* d, int64_t j,
-                                                  int lane) {
+__device__ __forceinline__ void heat_forced_solve(const HeatArgs& a, double (&y)[R], int64_t j, int lane) {
   const int n = a.n;
   const double dx = 1.0 / (double)(n + 1);
   const double cdx = a.kappa / (dx * dx);
   const double Tj = __dadd_rn(a.t0, __dmul_rn((double)j, a.H));
-  double y[R], sx[R];
+  double sx[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = lane * R + i;
-    y[i] = r < n ? lt[j * n + r] : 0.0;
     sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
   }
   HalfStepCoefs hc{};
@@ -327,6 +324,21 @@ __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const doubl
       heat_rk4_step<R>(y, z, acc, a.h, step_coefs<double>(hc, i, i0, cdx), sx, true, lane, n);
     }
   }
+}
+
+// Float64 defect of slice j (the residual correction the Conclusion
+// proposes): d_j = g^j(lt_j) - lt_{j+1}, the forced solve from lt_j.
+template <int R>
+__device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const double* lt, double* d, int64_t j,
+                                                  int lane) {
+  const int n = a.n;
+  double y[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int r = lane * R + i;
+    y[i] = r < n ? lt[j * n + r] : 0.0;
+  }
+  heat_forced_solve<R>(a, y, j, lane);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = lane * R + i;
