@@ -2,17 +2,19 @@
 // linearreconstruct): per slice j, one solve from 0 with the forcing on gives
 // b_j and d homogeneous solves from e_c give the columns of A_j.
 //
-// Heat equation kernels: one warp integrates one basis column.  Lane l holds
-// rows l*R .. l*R+R-1 of the d-vector in registers (R = ceil(d/32)); the
-// three-point stencil reaches the neighbouring lanes with two shuffles per
-// stage.  No shared or global memory is touched until the column is written.
+// Heat equation kernels: one warp (or a group of lanes) integrates one basis
+// column.  Lane l holds rows l*R .. l*R+R-1 of the d-vector (or of a window of
+// it) in registers; the stencil reaches the neighbouring lanes by shuffles.
+// No shared or global memory is touched until the column is written.
 //
-// Time-invariant homogeneous columns use the Horner form of the RK4 step,
-// y <- y + hL(y + hL/2(y + hL/3(y + hL/4 y))): for y' = L y with constant L
-// this is the classical RK4 step exactly (both equal the degree-4 Taylor
-// polynomial of hL applied to y), with 3 instead of 5 float operations per
-// element and stage.  The forcing column and time-dependent operators take
-// the four RK4 stages literally.
+// Time-invariant homogeneous columns take the RK4 step as one nine-point
+// stencil (or in Horner form, y <- y + hL(y + hL/2(y + hL/3(y + hL/4 y))):
+// for y' = L y with constant L both are the classical RK4 step exactly, the
+// degree-4 Taylor polynomial of hL applied to y), by default only over the
+// rows each column's steps can reach.  The float64 forcing column takes the
+// nine-point form plus the forcing's contribution along the sine eigenvector;
+// the float32 one and every column of a time-dependent operator take the four
+// RK4 stages literally.
 #include <cuda_bf16.h>
 #include <math.h>
 
