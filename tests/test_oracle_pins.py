@@ -448,3 +448,53 @@ def test_counter_based_slices_agree():
     assert np.array_equal(z[4:], workloads.splitmix64(7, 6, 4))
     s = workloads.chain3_samples(3, 4, 8, 2)
     assert s.shape == (6, 8) and np.all(np.abs(s) <= 1.0)
+
+
+@pytest.mark.parametrize("n,steps", [(64, 1), (64, 3), (100, 5), (48, 11)])
+def test_heat_maps_vanish_outside_the_reach_of_their_steps(n, steps):
+    """An RK4 step of the three-point operator applies it four times (one per
+    stage), so the column of A_j started from e_c is exactly zero in every row
+    more than 4m from c-1, and nonzero at distance 4m where the domain allows
+    (the largest power of L reaches exactly that far).  The windowed GPU build
+    and the banded chain rely on exactly this; here the oracle's own maps
+    (constant and variable coefficients) show it, in exact zeros."""
+    for name in ("heat1d", "heat1d_varcoef"):
+        T = 5 * steps * 2.0 / (5.0 * 1.25 * (n + 1) ** 2)
+        if name == "heat1d":
+            w = workloads.heat1d(n=n, S=5, T=T, dt=T / (5 * steps))
+        else:
+            w = workloads.Workload("v", "heat1d_varcoef", n, 0.0, T, 5, "rk4", T / (5 * steps), 0, "affine")
+        m = nv.workload_steps(w)
+        assert m == steps
+        Ac, _ = nv.build_affine_slice(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                                      w.t0, w.T, w.S, m, n, 2)
+        rows, cols = np.indices((n, n))
+        dist = np.abs(rows - cols)
+        assert np.all(Ac[dist > 4 * steps] == 0.0), name
+        reach = dist == 4 * steps
+        if np.any(reach):
+            assert np.all(Ac[reach] != 0.0), name
+
+
+def test_advdiff_maps_vanish_outside_the_periodic_diamond():
+    """The advection-diffusion step (RK4 of the five-point operator on the
+    periodic 64 x 64 grid) moves information one point per stage in x or y,
+    so after k steps a basis column is exactly zero at periodic Manhattan
+    distance > 4k from its unit point: the fact the windowed float32 build
+    rests on, shown by the oracle for sampled columns near the seams."""
+    steps = 3
+    w = workloads.advdiff2d(S=4, T=4 * steps * 2e-4, dt=2e-4)
+    m = nv.workload_steps(w)
+    assert m == steps
+    cols = [0, 63, 64 * 31 + 17, 4095]
+    Ac, b = nv.build_affine_slice(nv.workload_rhs(w, True), nv.workload_rhs(w, False), "rk4",
+                                  w.t0, w.T, w.S, m, w.dim, 1, columns=cols)
+    assert not np.any(b)
+    pts = np.arange(w.dim)
+    px, py = pts % 64, pts // 64
+    for k, c in enumerate(cols):
+        cx, cy = c % 64, c // 64
+        dx = np.minimum((px - cx) % 64, (cx - px) % 64)
+        dy = np.minimum((py - cy) % 64, (cy - py) % 64)
+        assert np.all(Ac[dx + dy > 4 * steps, k] == 0.0)
+        assert np.any(Ac[dx + dy == 4 * steps, k] != 0.0)
