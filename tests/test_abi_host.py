@@ -166,3 +166,20 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_every_tunable_is_documented_in_the_header(lib):
+    """The keys nv_tune_set accepts (api.cu) are exactly the keys the header
+    documents ("key N:")."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = open(os.path.join(root, "include", "nvpit.h")).read()
+    api = open(os.path.join(root, "paper_1304_6514_gb300", "csrc", "api.cu")).read()
+    body = api[api.index("nv_status nv_tune_set("):]
+    body = body[:body.index("default:")]
+    accepted = {int(k) for k in re.findall(r"case (\d+):", body)}
+    documented = {int(k) for k in re.findall(r"\bkey (\d+):", header)}
+    assert accepted == documented
+    for key in sorted(accepted):
+        assert lib.nv_tune_set(key, 0) == nvp.NV_OK, key
