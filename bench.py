@@ -300,7 +300,7 @@ def time_variant(nvp, torch, w, prec, K, W, flush, stream):
 
 def time_serial_gpu(nvp, torch, w, stream, reps=3):
     """The plain serial fine solve on the GPU (nv_serial_fine: one warp, all S m
-    RK4 steps in sequence), the other reference the method is judged against."""
+    RK4 steps in sequence), the other reference the method is measured against."""
     r = nvp.rhs("heat1d", w.dim, w.params)
     st = nvp.steps("rk4", w.dt, 0, "fp64")
     y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
@@ -972,7 +972,7 @@ def run_chain3_mlp(args):
     train_tflops = MLP_FLOP_PER_SAMPLE_STEP * 4096 * nsteps / train_s / 1e12
     line = {"metric": METRIC, "value": pair_steps / (pairs_ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": pairs_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 pairs, bf16 MLP (f32 accumulate), f64 judge", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 pairs, bf16 MLP (f32 accumulate), f64 reference", "data": "synthetic",
             "config": {"workload": w.name, "S": S, "M": M, "steps_per_slice": m, "hidden": [256, 256, 256],
                        "train_steps": nsteps, "batch": 4096},
             "pairs_ms": pairs_ms,

@@ -198,7 +198,7 @@ nv_status nv_solve(const nv_rhs* rhs, double t0, double T, int32_t S,
                    const double* y0_dev, double* yT_dev, void* stream);
 
 /* Serial fine solve over all slices from y0 with the same step size and step
- * times as the slices: the "plain" reference the method is judged against
+ * times as the slices: the "plain" reference the method is measured against
  * (Section 4, Theorem).  One thread per component group; latency-bound. */
 nv_status nv_serial_fine(const nv_rhs* rhs, double t0, double T, int32_t S,
                          const nv_steps* steps, const double* y0_dev, double* yT_dev,
@@ -293,7 +293,7 @@ nv_status nv_batch_destroy(nv_batch* batch);
  * computation phase produces training pairs; a slice-conditioned MLP
  * (x = (y0/sx, T_{j-1}/T) -> 256 -> 256 -> 256 -> (y_end - y0)/sd, GELU)
  * trained on the GPU with bf16 tensor-core forward/backward stands in for the
- * table; float64 fine integration judges it and replaces it on slices whose
+ * table; float64 fine integration checks it and replaces it on slices whose
  * validation error is too large.  Built for the 3-mass chain (NV_RHS_CHAIN3).
  * ------------------------------------------------------------------------- */
 typedef struct nv_mlp nv_mlp;   /* opaque, library-owned */
@@ -307,7 +307,7 @@ nv_status nv_build_pairs(const nv_rhs* rhs, double t0, double T, int32_t S, cons
                          void* stream);
 
 /* Fine integration in float64 of `count` states (y_dev, count x 6 doubles, in
- * place) over slices j0 .. j0+nslices-1: the judge and the fallback. */
+ * place) over slices j0 .. j0+nslices-1: the reference and the fallback. */
 nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
                        int32_t j0, int32_t nslices, int64_t count, double* y_dev, void* stream);
 

@@ -1,5 +1,5 @@
 """GPU parity of the learned-propagator path: training pairs from the method's
-integrator, float64 propagation (judge and fallback), and the MLP's bf16
+integrator, float64 propagation (reference and fallback), and the MLP's bf16
 tensor-core forward/backward gradients against the FP64 oracle."""
 import numpy as np
 import pytest

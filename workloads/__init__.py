@@ -68,7 +68,7 @@ class Stream:
 
 # --------------------------------------------------------------------------
 # Workload definitions.  Sizes follow the five benchmark configurations; the
-# readings of points the configurations leave open are listed in the design doc.
+# docstrings state the readings taken where a configuration leaves a point open.
 # --------------------------------------------------------------------------
 
 @dataclass
