@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnvpit.so")
 
-SOURCES = ["api.cu", "tables.cu", "affine.cu", "compose.cu", "scan.cu", "noalloc.cu", "batch.cu", "gemm.cu", "mlp.cu",
+SOURCES = ["api.cu", "tables.cu", "affine.cu", "advdiff.cu", "compose.cu", "scan.cu", "noalloc.cu", "batch.cu", "gemm.cu", "mlp.cu",
            "wave.cu", "refine.cu", "wavefront.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,

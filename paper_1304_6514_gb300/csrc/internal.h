@@ -145,3 +145,20 @@ struct nv_tunables {
   int adv_build_form;        // advection-diffusion float32 build: 0 auto (windows first), 1 whole grid only
 };
 extern nv_tunables g_tune;
+
+// Grid of a persistent kernel: the CTAs that fit on every SM at once (from the
+// occupancy of `kernel` with `block` threads), or fewer when work_warps warps
+// need fewer.
+template <typename K>
+inline nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* grid_out) {
+  int sms = 152, dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  nv_status st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0),
+                               "occupancy query");
+  if (st != NV_OK) return st;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  grid = std::min<int64_t>(grid, (work_warps * 32 + block - 1) / block);
+  *grid_out = (int)std::max<int64_t>(grid, 1);
+  return NV_OK;
+}
