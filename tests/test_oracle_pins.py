@@ -126,7 +126,114 @@ def test_rk4_forced_order_pins_stage_times():
         assert abs(math.log2(errs[i] / errs[i + 1]) - 4) < 0.2, errs
 
 
-# ------------------------------------------------------------- interpolation
+# ------------------------------------------- nonlinear right-hand sides, exact
+
+def _simpson(g, a, b, n):
+    """Composite Simpson rule with n (even) intervals, written out here."""
+    x = np.linspace(a, b, n + 1)
+    w = np.full(n + 1, 2.0)
+    w[1::2] = 4.0
+    w[0] = w[-1] = 1.0
+    return (b - a) / (3.0 * n) * float(np.dot(w, g(x)))
+
+
+def _cos_cubic_exact(t0, y0, t):
+    """y' = cos(t) y - y^3 is a Bernoulli equation: v = y^-2 obeys the linear
+    equation v' = -2 cos(t) v + 2, so
+        v(t) = e^{-2 sin t} (e^{2 sin t0} v0 + 2 int_{t0}^{t} e^{2 sin s} ds),
+    and y = sign(y0) v^{-1/2} (the cubic is odd, so -y is a solution too).
+    The integral is taken by Simpson's rule with steps of ~1e-4 (error ~1e-15)."""
+    n = 2 * max(1, int(math.ceil((t - t0) / 2e-4)))
+    integral = _simpson(lambda s: np.exp(2.0 * np.sin(s)), t0, t, n)
+    v = math.exp(-2.0 * math.sin(t)) * (math.exp(2.0 * math.sin(t0)) / (y0 * y0) + 2.0 * integral)
+    return math.copysign(v ** -0.5, y0)
+
+
+def test_cos_cubic_closed_form_is_a_solution():
+    """The closed form itself satisfies y' = cos(t) y - y^3 (central difference
+    of the closed form against the right-hand side written out here), so the
+    pins below rest on the differential equation, not on the oracle."""
+    for t0, y0 in [(0.0, 0.5), (1.0, -1.3), (2.5, 2.0)]:
+        for t in [t0 + 0.3, t0 + 2.0]:
+            e = 1e-3
+            dy = (_cos_cubic_exact(t0, y0, t + e) - _cos_cubic_exact(t0, y0, t - e)) / (2 * e)
+            y = _cos_cubic_exact(t0, y0, t)
+            assert abs(dy - (math.cos(t) * y - y ** 3)) < 1e-5 * max(1.0, abs(dy))
+        assert abs(_cos_cubic_exact(t0, y0, t0 + 1e-9) - y0) < 1e-8
+
+
+@pytest.mark.parametrize("scheme,order,ms,T", [("euler", 1, [1000, 2000, 4000], 10.0),
+                                               ("rk4", 4, [40, 80, 160], 3.0)])
+def test_cos_cubic_converges_to_bernoulli_closed_form(scheme, order, ms, T):
+    """The oracle's y' = cos(t) y - y^3 (the scalar workload's right-hand
+    side), integrated by its Euler and RK4 steps at halving h, converges to the
+    Bernoulli closed form at order 1 and 4, from slice starts t0 != 0 and for
+    initial values of both signs.  A dropped cos, sin for cos, +y^3 or a
+    missing factor fails this."""
+    f = nv.rhs_cos_cubic()
+    for t0, y0 in [(0.0, 0.5), (0.7, -1.3), (4.0, 0.9)]:
+        exact = _cos_cubic_exact(t0, y0, t0 + T)
+        errs = []
+        for m in ms:
+            y = nv.integrate(f, scheme, t0, np.array([[y0]]), T / m, m)[0, 0]
+            errs.append(abs(y - exact))
+        for i in range(2):
+            assert abs(math.log2(errs[i] / errs[i + 1]) - order) < 0.15, (t0, y0, errs)
+        assert errs[-1] < (2e-3 if scheme == "euler" else 1e-6), errs
+
+
+def test_cos_cubic_workload_serial_solve_matches_closed_form():
+    """The scalar workload exactly as benchmarked (t in [0, 10], y(0) = 0.5,
+    16 slices of 10^4 Euler steps): its serial fine solve lies within the
+    first-order error of the exact solution, and each slice's table entry at a
+    node equals the exact flow from that node within the same bound."""
+    w = workloads.scalar_cos_cubic()
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, w.S, m)
+    f = nv.workload_rhs(w)
+    ser = nv.serial_fine(f, "euler", w.t0, w.T, w.S, m, w.y0)[0]
+    exact = _cos_cubic_exact(w.t0, float(np.asarray(w.y0).ravel()[0]), w.T)
+    assert abs(ser - exact) < 50 * h * abs(exact), (ser, exact)
+    assert abs(ser - exact) > 1e-3 * h            # Euler's error is there: not an exact solver
+    tab = nv.build_table_1d(f, "euler", w.t0, w.T, 2, m, np.array([-2.0, -0.5, 1.0, 2.0]))
+    Tj = nv.slice_times(w.t0, w.T, 2)
+    for j in range(2):
+        for k, xi in enumerate([-2.0, -0.5, 1.0, 2.0]):
+            ex = _cos_cubic_exact(Tj[j], xi, Tj[j + 1])
+            assert abs(tab[j, k] - ex) < 50 * nv.step_size(w.t0, w.T, 2, m) * max(1.0, abs(ex))
+
+
+@pytest.mark.parametrize("scheme,order,ms", [("euler", 1, [400, 800, 1600]), ("rk4", 4, [20, 40, 80])])
+def test_square_converges_to_closed_form(scheme, order, ms):
+    """Section 3, eq. scalarmodel: y' = y^2 has y = y0 / (1 - y0 (t - t0)).
+    The oracle's right-hand side under its Euler and RK4 steps converges to it
+    at order 1 and 4 (y0 = 1 on [0, 1/2] as in the paper, plus a negative start
+    and a start at t0 != 0).  A sign error, y for y^2 or y^3 fails this."""
+    f = nv.rhs_square()
+    for t0, y0, T in [(0.0, 1.0, 0.5), (0.3, -1.5, 1.0), (1.0, 0.8, 0.6)]:
+        exact = y0 / (1.0 - y0 * T)
+        errs = []
+        for m in ms:
+            y = nv.integrate(f, scheme, t0, np.array([[y0]]), T / m, m)[0, 0]
+            errs.append(abs(y - exact))
+        for i in range(2):
+            assert abs(math.log2(errs[i] / errs[i + 1]) - order) < 0.15, (t0, y0, errs)
+
+
+def test_square_paper_sweep_workload_reaches_exact_solution():
+    """The paper-shaped sweep's problem (y' = y^2, y(0) = 1, t in [0, 1/2],
+    dt = 2^-14): the oracle's serial Euler solve ends within Euler's first-order
+    error of y(1/2) = 2, and its piecewise-linear composition within that plus
+    the interpolation error of Section 3's table."""
+    w = workloads.square_paper(14, 32, 7)
+    m = nv.workload_steps(w)
+    f = nv.workload_rhs(w)
+    ser = nv.serial_fine(f, "euler", w.t0, w.T, w.S, m, w.y0)[0]
+    h = nv.step_size(w.t0, w.T, w.S, m)
+    # Euler's global error e obeys e' = 2 y e + (h/2) y'' to leading order; with
+    # y = 1/(1-t), y'' = 2 y^3 this gives e(t) = h ln(1/(1-t)) / (1-t)^2, so the
+    # solve falls short of y(1/2) = 2 by 4 ln(2) h.
+    assert abs((2.0 - ser) / h - 4.0 * math.log(2.0)) < 0.01 * 4.0 * math.log(2.0), ((2.0 - ser) / h)
 
 def test_pl_map_exact_for_linear_ode():
     """For y' = lambda y the slice map is linear, so the piecewise-linear table
