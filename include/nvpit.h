@@ -371,9 +371,15 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  * the library, held until the process exits; it serves 1 <= dim <=
  * NVPIT_NOALLOC_MAX_DIM, larger dim returns NV_EINVAL.  The first call on a
  * device looks up that array's device address with cudaGetSymbolAddress (make
- * that first call before any stream capture on that device).  All calls share
+ * that first call before any stream capture on that device) and keeps it for
+ * the process, so the entry point must not be used on a device after
+ * cudaDeviceReset.  All calls share
  * the array: calls that overlap on the GPU (other streams, other threads)
  * race and give wrong results; order them on one stream or synchronise.
+ * Each call runs the chain with 16 rows per CTA (nv_tune_set key 1 does not
+ * apply): a cooperative grid of ceil(dim/16) CTAs, NV_ENOTSUP if the device
+ * cannot hold them all at once (a GB300 holds them for every dim up to the
+ * limit); NV_ECUDA if a CUDA call fails.
  * Calls no cudaMalloc, cudaFree or allocating library routine. */
 nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t dim, int32_t S,
                                     const double* y0_dev, double* yT_dev, double* lambdas_dev,
@@ -445,6 +451,16 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
  * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14 and 15. */
 nv_status nv_tune_set(int32_t key, int32_t value);
+
+/* Measured fused multiply-add throughput of the current device's float64
+ * (prec = NV_FP64) or float32 (NV_FP32) pipe, in FLOP/s (FMA = 2): the peak
+ * the ALU-bound map builds are reported against.  The paper has no
+ * counterpart (a measurement helper).  Launches a persistent grid of eight
+ * independent FMA chains per thread on `stream`, about 20 ms per launch at the
+ * nominal rates (one warm-up and three timed launches), and synchronises the
+ * stream.  Writes *flops_per_s; NV_EINVAL for another precision or a NULL
+ * pointer, NV_ECUDA if a launch fails.  Allocates no device memory. */
+nv_status nv_alu_rate(int32_t prec, double* flops_per_s, void* stream);
 
 /* Fine steps per slice and step size by the rule stated above (host only). */
 nv_status nv_plan_steps(double t0, double T, int32_t S, double dt, int64_t steps_per_slice,

@@ -111,6 +111,7 @@ def load_library(path: str = LIB_PATH):
         "nv_mlp_compose": [P, POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), P, c_int64, P, P, P],
         "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
                           POINTER(c_double)],
+        "nv_alu_rate": [c_int32, POINTER(c_double), P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +295,13 @@ def plan_steps(t0, T, S, dt=0.0, steps_per_slice=0):
     m, h = c_int64(0), c_double(0.0)
     _check(load_library().nv_plan_steps(t0, T, S, dt, steps_per_slice, byref(m), byref(h)))
     return m.value, h.value
+
+
+def alu_rate(prec: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput of the device's float64 / float32 pipe (FLOP/s)."""
+    out = c_double(0.0)
+    _check(load_library().nv_alu_rate(PREC[prec], byref(out), _stream(stream)))
+    return out.value
 
 
 def tune_set(key: int, value: int):

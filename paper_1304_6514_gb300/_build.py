@@ -13,7 +13,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnvpit.so")
 
 SOURCES = ["api.cu", "tables.cu", "affine.cu", "advdiff.cu", "compose.cu", "scan.cu", "noalloc.cu", "batch.cu", "gemm.cu", "mlp.cu",
-           "wave.cu", "refine.cu", "wavefront.cu"]
+           "wave.cu", "refine.cu", "wavefront.cu", "alu_rate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                  "--expt-relaxed-constexpr"]

@@ -963,8 +963,10 @@ nv_status launch_affine_chain_buffers(const void* maps, int prec, int n, int S, 
   while (block % rpc) --rpc;
   const int G = (n + rpc - 1) / rpc;
   int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  nv_status st0 = nv_cuda_check(cudaGetDevice(&dev), "current device");
+  if (st0 != NV_OK) return st0;
+  st0 = nv_cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  if (st0 != NV_OK) return st0;
   const size_t smem = sizeof(double) * (size_t)(n + 1);
   const void* fn = (prec == NV_FP64) ? (const void*)affine_chain_kernel<double, double>
                                      : (const void*)affine_chain_kernel<float, double>;

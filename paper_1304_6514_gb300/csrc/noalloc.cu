@@ -29,7 +29,9 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up on the
-// first call made with that device current.
+// first call made with that device current and kept for the process: after a
+// cudaDeviceReset of that device the kept address is stale, so the entry
+// point must not be used on a device that was reset.
 nv_status noalloc_scratch(void** out) {
   int dev = -1;
   nv_status st = nv_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -72,8 +74,10 @@ extern "C" nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t pre
   // vectors are fully written before they are read.
   st = nv_cuda_check(cudaMemsetAsync(base, 0, kStateOffset, s), "no-alloc scratch reset");
   if (st != NV_OK) return st;
+  // 16 rows per CTA, whatever nv_tune_set key 1 says: every dim up to the
+  // limit then needs at most 256 resident CTAs
   st = launch_affine_chain_buffers(maps_dev, prec, dim, S, y0_dev, yT_dev, lambdas_dev, xbuf, bar,
-                                   status, s, g_tune.chain_rows_per_cta);
+                                   status, s, 16);
   if (st != NV_OK) return st;
   if (status_dev)
     st = nv_cuda_check(cudaMemcpyAsync(status_dev, status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s),
