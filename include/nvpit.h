@@ -103,14 +103,17 @@ typedef enum {
   NV_BF16_REFINE = 3,      /* affine only: maps integrated in float32 and stored rounded
                               to bfloat16 (half the bytes of float32), composed by the
                               HBM-bound chain with float32 accumulation, then float64
-                              residual-correction passes (two by default) whose chains
-                              reuse the bfloat16 maps.  Advection-diffusion, d > 512,
-                              d % 8 == 0.  Each pass contracts the error by about
-                              S 2^-9 (the maps' rounding compounds along the chain), so
-                              it converges for chains of up to ~100 slices             */
+                              residual-correction passes whose chains reuse the
+                              bfloat16 maps.  Advection-diffusion, d > 512, d % 8 == 0.
+                              The maps' rounding compounds along the chain in the
+                              slowly decaying modes, so a pass contracts the error by
+                              roughly S / 1500 on the 64 x 64 problem: the default is
+                              two passes up to S = 32 and one more per doubling of S
+                              (six at S = 512)                                          */
   NV_FP32_REFINE = 4       /* affine only: float32 maps and float32 chain as NV_FP32,
-                              then float64 residual-correction passes (one by default;
-                              contraction about S 2^-24).  Advection-diffusion, d > 512 */
+                              then float64 residual-correction passes (default one;
+                              two for the undamped wave equation).  Heat equations,
+                              wave equation, advection-diffusion with d > 512          */
 } nv_precision;
 
 typedef enum { NV_OOB_EXTRAPOLATE = 0, NV_OOB_ERROR = 1 } nv_oob_policy;
@@ -393,7 +396,8 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          fits, up to 16; a negative value selects the grid-wide chain)
  *   key 4: slices per block of the NV_TF32_REFINE scan (default round(sqrt(S)))
  *   key 5: float64 correction passes of NV_TF32_REFINE / NV_BF16_REFINE /
- *          NV_FP32_REFINE (default 0 = three / two / one; a negative value
+ *          NV_FP32_REFINE (default 0 = three / 2 + ceil(log2(S/32)) for S > 32, else
+ *          two / one, two for the wave equation; a negative value
  *          returns the unrefined reduced-precision states)
  *   key 6: form of the RK4 step for the homogeneous heat columns: 0 auto (the
  *          windowed nine-point stencil where a built window fits, else the

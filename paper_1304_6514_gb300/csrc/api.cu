@@ -179,8 +179,9 @@ static nv_status plan(const nv_rhs* rhs, double t0, double T, int32_t S, const n
         return nv_fail(NV_ENOTSUP, "bfloat16 refinement is built for advection-diffusion with d > 512, d %% 8 == 0");
       if (st->prec == NV_FP32_REFINE &&
           !((rhs->kind == NV_RHS_ADVDIFF2D && d > 512 && d % 8 == 0) ||
-            (rhs->kind == NV_RHS_HEAT1D || rhs->kind == NV_RHS_HEAT1D_VARCOEF)))
-        return nv_fail(NV_ENOTSUP, "float32 refinement is built for the heat equations and advection-diffusion");
+            (rhs->kind == NV_RHS_HEAT1D || rhs->kind == NV_RHS_HEAT1D_VARCOEF) ||
+            rhs->kind == NV_RHS_WAVE_CHEB))
+        return nv_fail(NV_ENOTSUP, "float32 refinement is built for the heat, wave and advection-diffusion equations");
       if (rhs->kind == NV_RHS_WAVE_CHEB) {
         if (st->prec == NV_TF32_REFINE) return nv_fail(NV_ENOTSUP, "TF32 refinement is built for the heat equation");
         P->aux_elems = wave_aux_elems(d / 2);

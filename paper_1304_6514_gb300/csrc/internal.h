@@ -125,6 +125,10 @@ struct ChainsArgs {
 
 nv_status launch_chains(const ChainsArgs& args, bool f64, cudaStream_t s, int want_csize);
 nv_status launch_heat_defect(const nv_maps* M, const double* lam_tilde, double* d, cudaStream_t s);
+// float64 defects of the wave maps (leapfrog from each approximate state)
+nv_status launch_wave_defect(const nv_maps* M, const double* lam, double* d, cudaStream_t s);
+// float64 correction passes NV_*_REFINE runs when nv_tune_set key 5 is 0
+int default_refine_passes(const nv_maps* M);
 
 // Tunables (set by nv_tune_set, read by the launchers).
 struct nv_tunables {

@@ -36,11 +36,14 @@ static nv_status ensure_scratch(nv_maps* M, size_t need, cudaStream_t s) {
   return st;
 }
 
-// The heat equations (d <= 512): the same passes with the cluster chain
-// (compose.cu), whose options carry d_j (v), the approximate states (add) and
-// every state written; the defects come from the heat float64 defect kernel.
-static nv_status heat_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
-                                   double* lt, double* lt2, double* d, int passes, cudaStream_t s) {
+// The heat equations and the wave equation (d <= 512): the same passes with
+// the cluster chain (compose.cu), whose options carry d_j (v), the
+// approximate states (add) and every state written; the defects come from
+// the family's float64 defect kernel (heat: nine-point / literal RK4 stages;
+// wave: leapfrog on the two-level state).
+static nv_status cluster_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas,
+                                      double* lt, double* lt2, double* d, int passes, cudaStream_t s) {
+  const bool wave = M->rhs_kind == NV_RHS_WAVE_CHEB;
   const int n = M->dim, S = M->S;
   const float* maps = static_cast<const float*>(M->data);
   ChainsArgs c{};
@@ -65,7 +68,7 @@ static nv_status heat_chain_refine(nv_maps* M, const double* y0, double* yT, dou
   for (int p = 0; p < passes; ++p) {
     const bool last = p == passes - 1;
     double* out = last ? lambdas : (cur == lt ? lt2 : lt);
-    if ((st = launch_heat_defect(M, cur, d, s)) != NV_OK) return st;
+    if ((st = wave ? launch_wave_defect(M, cur, d, s) : launch_heat_defect(M, cur, d, s)) != NV_OK) return st;
     ChainsArgs corr = c;                 // e_{j+1} = At_j e_j + d_j from e_0 = 0, written as cur + e
     corr.v = d;
     corr.v_double = 1;
@@ -79,12 +82,28 @@ static nv_status heat_chain_refine(nv_maps* M, const double* y0, double* yT, dou
   return NV_OK;
 }
 
+// Default number of float64 passes: one for float32 maps of the damped
+// problems; two for the undamped wave equation, whose float32 map error
+// (~3e-6 per map) composes coherently over all S slices, so that one pass
+// only contracts its 6e-3 to about 1e-5; and for bfloat16 maps two passes
+// up to 32 slices and one more for every doubling of S beyond (each pass
+// contracts by roughly S / 1500 at the advection-diffusion problem).
+int default_refine_passes(const nv_maps* M) {
+  if (M->prec == NV_BF16_REFINE) {
+    int p = 2;
+    for (int64_t s = 32; s < M->S; s *= 2) ++p;
+    return p;
+  }
+  return M->rhs_kind == NV_RHS_WAVE_CHEB ? 2 : 1;
+}
+
 nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* lambdas, cudaStream_t s) {
   const bool heat = M->rhs_kind == NV_RHS_HEAT1D || M->rhs_kind == NV_RHS_HEAT1D_VARCOEF;
-  if (M->rhs_kind != NV_RHS_ADVDIFF2D && !heat)
-    return nv_fail(NV_ENOTSUP, "chain refinement is built for the heat equations and advection-diffusion");
+  const bool wave = M->rhs_kind == NV_RHS_WAVE_CHEB;
+  if (M->rhs_kind != NV_RHS_ADVDIFF2D && !heat && !wave)
+    return nv_fail(NV_ENOTSUP, "chain refinement is built for the heat, wave and advection-diffusion equations");
   const int n = M->dim, S = M->S;
-  const int dflt = M->prec == NV_BF16_REFINE ? 2 : 1;
+  const int dflt = default_refine_passes(M);
   const int passes = g_tune.refine_passes > 0 ? g_tune.refine_passes : (g_tune.refine_passes < 0 ? 0 : dflt);
   const bool pipelined = heat && passes >= 1 && g_tune.refine_schedule != 1;
   const size_t states = (size_t)(S + 1) * n;
@@ -100,7 +119,7 @@ nv_status launch_chain_refine(nv_maps* M, const double* y0, double* yT, double* 
   double* lt = static_cast<double*>(M->scan_ws);
   double* lt2 = lt + states;
   double* d = lt2 + states;
-  if (heat) return heat_chain_refine(M, y0, yT, lambdas, lt, lt2, d, passes, s);
+  if (heat || wave) return cluster_chain_refine(M, y0, yT, lambdas, lt, lt2, d, passes, s);
   double* zero = d + (size_t)S * n;
   if ((st = nv_cuda_check(cudaMemsetAsync(zero, 0, sizeof(double) * n, s), "zero state")) != NV_OK) return st;
   // approximate boundary states over the bfloat16 maps

@@ -202,6 +202,43 @@ __global__ void wave_serial_kernel(WaveArgs a, int DP, int64_t steps, const doub
   }
 }
 
+// Float64 defects of approximate boundary states for the correction passes
+// of NV_FP32_REFINE: d_j = g^j(lam_j) - lam_{j+1}, one CTA per slice running
+// the m leapfrog steps of slice j from lam_j = (u^n, u^{n-1}) with the
+// arithmetic of wave_serial_kernel.  lam: (S+1) x n, d: S x n.
+__global__ void wave_defect_kernel(WaveArgs a, int DP, const double* lam, double* dout) {
+  __shared__ double u[kWaveMaxDP], uo[kWaveMaxDP];
+  const int d = a.d, n = a.n, i = threadIdx.x;
+  for (int j = blockIdx.x; j < a.S; j += gridDim.x) {
+    const double* l0 = lam + (int64_t)j * n;
+    if (i < d) {
+      u[i] = l0[i];
+      uo[i] = l0[d + i];
+    }
+    __syncthreads();
+    for (int64_t s = 0; s < a.m; ++s) {
+      double un = 0.0;
+      if (i < d) {
+        double w = 0.0;
+        for (int k = 0; k < d; ++k) w = fma(a.d2t[k * DP + i], u[k], w);
+        un = fma(a.h2, w, 2.0 * u[i] - uo[i]);
+      }
+      __syncthreads();
+      if (i < d) {
+        uo[i] = u[i];
+        u[i] = un;
+      }
+      __syncthreads();
+    }
+    if (i < d) {
+      const double* l1 = lam + (int64_t)(j + 1) * n;
+      dout[(int64_t)j * n + i] = u[i] - l1[i];
+      dout[(int64_t)j * n + d + i] = uo[i] - l1[d + i];
+    }
+    __syncthreads();                                    // u, uo are reused by the next slice
+  }
+}
+
 template <typename T, int DP, int CB>
 static nv_status launch_wave_tiles(const WaveArgs& a, cudaStream_t s) {
   using W = WaveTile<T, DP, CB>;
@@ -259,6 +296,22 @@ nv_status launch_wave_build(const nv_maps* M, cudaStream_t s) {
   if (M->prec == NV_FP64)
     return DP == 40 ? launch_wave_tiles<double, 40, 2>(a, s) : launch_wave_tiles<double, 80, 2>(a, s);
   return DP == 40 ? launch_wave_tiles<float, 40, 4>(a, s) : launch_wave_tiles<float, 80, 4>(a, s);
+}
+
+nv_status launch_wave_defect(const nv_maps* M, const double* lam, double* d, cudaStream_t s) {
+  const int n = M->dim, dd = n / 2;
+  if (dd < 1 || dd > kWaveMaxDP || n != 2 * dd) return nv_fail(NV_ENOTSUP, "wave state dimension must be 2(M-1) <= 160");
+  if (!M->aux) return nv_fail(NV_EINVAL, "wave maps have no operator storage");
+  WaveArgs a{};
+  a.d2t = M->aux + (int64_t)(dd + 2) * (dd + 2);
+  a.d = dd;
+  a.n = n;
+  a.S = M->S;
+  a.m = M->m;
+  a.h2 = M->h * M->h;
+  const int grid = (int)std::min<int64_t>(M->S, 4096);
+  wave_defect_kernel<<<grid, 128, 0, s>>>(a, wave_dp(dd), lam, d);
+  return nv_cuda_check(cudaGetLastError(), "wave_defect_kernel launch");
 }
 
 nv_status launch_serial_wave(const nv_maps* P, const double* y0, double* yT, cudaStream_t s) {

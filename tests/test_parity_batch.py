@@ -95,10 +95,24 @@ def test_graph_replay_and_autotune_are_bitwise_stable():
     b.destroy()
 
 
+def full_batch_check_instances(vb):
+    """Instances of the 4096-instance batch checked element by element: the
+    three cheapest, the longest horizon, the most slices, the largest damping
+    (its limit cycle leaves [-3,3]^2, so lookups extrapolate) and the two
+    instances with the most steps per slice."""
+    m = np.ceil(vb.T / vb.S / vb.dt - 1e-9)
+    pick = list(np.argsort(vb.T)[:3]) + [int(np.argmax(vb.T)), int(np.argmax(vb.S)), int(np.argmax(vb.mu))]
+    pick += list(np.argsort(-m)[:2])
+    return list(dict.fromkeys(int(i) for i in pick))
+
+
 def test_full_batch_sampled_instances():
     """4096 Van der Pol instances (mu ~ U[0.1,2], T ~ U[5,20], S ~ U{8..256},
     32 x 32 grid on [-3,3]^2, RK4 dt = 1e-3, float32 tables, float64
-    composition): the three cheapest instances checked element by element."""
+    composition): the instances of full_batch_check_instances (cheap and
+    hard: longest horizon, most slices, largest damping with out-of-range
+    lookups) checked element by element against the oracle, every table entry
+    and the composed final state."""
     torch = need_gpu()
     vb = workloads.vdp_batch()
     P = vb.per_dim
@@ -106,11 +120,14 @@ def test_full_batch_sampled_instances():
     info = nvp.batch_info(b)
     assert info["total_slices"] == int(np.sum(vb.S))
     parts_off = np.concatenate([[0], np.cumsum(vb.S.astype(np.int64) * P * P * 2)])
-    cost = vb.T                                   # steps per sample ~ T / dt
-    for i in np.argsort(cost)[:3]:
-        otab, oy, _ = _oracle_instance(vb.mu[i], vb.T[i], vb.S[i], vb.y0[i], P, vb.dt)
+    extrapolated = 0
+    for i in full_batch_check_instances(vb):
+        otab, oy, o = _oracle_instance(vb.mu[i], vb.T[i], vb.S[i], vb.y0[i], P, vb.dt)
+        extrapolated += o
         g = tabs[parts_off[i]:parts_off[i + 1]].reshape(int(vb.S[i]), P, P, 2).transpose(0, 2, 1, 3)
         assert rel_max(g, otab) <= 1e-5, i
-        assert rel_max(yT[i], oy) <= 1e-4, i
+        assert rel_max(yT[i], oy) <= 1e-4, (i, rel_max(yT[i], oy))
+    assert extrapolated > 0                      # the hard path (EXTRAPOLATE) was among them
+    assert oob >= extrapolated
     assert np.all(np.isfinite(yT))
     b.destroy()
