@@ -309,8 +309,11 @@ nv_status nv_build_pairs(const nv_rhs* rhs, double t0, double T, int32_t S, cons
                          int64_t M, uint64_t seed, double lo, double hi, void* y0_dev, void* yend_dev,
                          void* stream);
 
-/* Fine integration in float64 of `count` states (y_dev, count x 6 doubles, in
- * place) over slices j0 .. j0+nslices-1: the reference and the fallback. */
+/* Fine integration of `count` states (y_dev, count x 6 doubles, in place)
+ * over slices j0 .. j0+nslices-1, one thread per state: in float64 for
+ * steps->prec = NV_FP64 (the reference and the fallback), in float32 with
+ * Kahan-compensated updates for NV_FP32 (the plain float32 method); other
+ * precisions return NV_EINVAL. */
 nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_t S, const nv_steps* steps,
                        int32_t j0, int32_t nslices, int64_t count, double* y_dev, void* stream);
 
@@ -353,6 +356,27 @@ nv_status nv_mlp_validate(nv_mlp* mlp, const double* y0_dev, const double* yend_
 nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, int32_t S,
                          const nv_steps* steps, const int32_t* fallback, int64_t count,
                          const double* y0_dev, double* yT_dev, void* stream);
+
+/* Parareal with the learned map as the coarse propagator (the combination
+ * with parareal the Conclusion proposes): G_j(y) = y + sd*MLP(y/sx, j/S),
+ * F_j = float64 fine integration over slice j.  Iteration 0 is the learned
+ * composition lambda_{j+1} = G_j(lambda_j); iteration k >= 1 computes
+ * F_j(lambda_j) for every slice and state at once (S x count independent
+ * trajectories), then sweeps the slices in order:
+ *   lambda^k_{j+1} = G_j(lambda^k_j) + (F_j(lambda^{k-1}_j) - G_j(lambda^{k-1}_j)).
+ * After k iterations the first k boundary states equal the fine solution's;
+ * the iterates converge to the float64 fine integration of every state.
+ *   count        states, a positive multiple of 128
+ *   y0_dev       count x 6 doubles (input); yT_dev count x 6 (output)
+ *   lambdas_dev  (S+1) x count x 6 doubles (output, may be NULL): every
+ *                boundary state of the last iterate
+ * Scratch of 2 S count 6 doubles (+ the boundary states when lambdas_dev is
+ * NULL) comes from the stream-ordered allocator on `stream`.  NV_EINVAL for a
+ * bad count or iters < 0; NV_ENOTSUP for a right-hand side other than the
+ * 3-mass chain. */
+nv_status nv_mlp_parareal(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, int32_t S,
+                          const nv_steps* steps, int32_t iters, int64_t count, const double* y0_dev,
+                          double* yT_dev, double* lambdas_dev, void* stream);
 
 /* Largest state dimension nv_compose_affine_noalloc accepts. */
 #define NVPIT_NOALLOC_MAX_DIM 4096
@@ -447,7 +471,7 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          column of banded maps (those of the heat equations, zero off
  *          |r - c| <= 4m) instead of the band around each CTA's rows; the
  *          results are the same bit for bit.
- *   key 15: 0 (default) or 1: with 1 the float32 / bfloat16 advection-diffusion
+ *   key 15: 0 (default) or 1: with 1 the float64 / float32 / bfloat16 advection-diffusion
  *          build integrates every column on the whole grid for all m steps;
  *          by default the first min(m, 3) steps run on 32 x 32 windows
  *          around each column's unit point (the rows those steps cannot

@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         "nv_mlp_train": [P, P, P, c_int32, c_int64, c_int64, c_int32, c_double, P, POINTER(c_double)],
         "nv_mlp_validate": [P, P, P, c_int32, c_int64, P, P],
         "nv_mlp_compose": [P, POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), P, c_int64, P, P, P],
+        "nv_mlp_parareal": [P, POINTER(NvRhs), c_double, c_double, c_int32, POINTER(NvSteps), c_int32, c_int64,
+                            P, P, P, P],
         "nv_plan_steps": [c_double, c_double, c_int32, c_double, c_int64, POINTER(c_int64),
                           POINTER(c_double)],
         "nv_alu_rate": [c_int32, POINTER(c_double), P],
@@ -481,3 +483,9 @@ class MLP:
         _check(load_library().nv_mlp_compose(self.handle, byref(rhs_), t0, T, S, byref(steps_),
                                              fb.ctypes.data if fb is not None else None, y0.shape[0], _ptr(y0),
                                              _ptr(yT), _stream(stream)))
+
+    def parareal(self, rhs_, t0, T, S, steps_, iters, y0, yT, lambdas=None, stream=None):
+        """Parareal with this network as the coarse propagator (nv_mlp_parareal)."""
+        _check(load_library().nv_mlp_parareal(self.handle, byref(rhs_), t0, T, S, byref(steps_), iters,
+                                              y0.shape[0], _ptr(y0), _ptr(yT),
+                                              _ptr(lambdas) if lambdas is not None else None, _stream(stream)))

@@ -430,6 +430,135 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_window_kernel(Adv
   }
 }
 
+// The float64 build with the first steps on windows, in the strip layout of
+// advdiff_affine_kernel.  As in advdiff_window_kernel, after k steps the
+// column from the unit point (cx, cy) is exactly zero outside the periodic
+// diamond |x - cx| + |y - cy| <= 4k, so the first m1 <= 3 steps run on the
+// 32 x 32 window with origin (cx - 16, cy - 16) (mod 64): it holds the
+// radius-12 diamond, and its cut edges are at least 16 points from the centre,
+// where every stage that reads the halo (the first 4 m1 <= 12) reads the exact
+// zero.  Window phase: four columns per CTA, two warps each, warp 2g + s
+// holding rows 16 s .. 16 s + 15 of column g's window at window column
+// x = lane; x-neighbours by shuffles (zero at the window's side edges), the
+// strips' facing rows through the shared top / bottom rows (a zero slot at the
+// window's top and bottom edges).  Then each of the four columns runs the
+// remaining steps on the whole grid, in exactly advdiff_affine_kernel's layout,
+// from its window staged in shared memory (zeros elsewhere).  Every point is the
+// same floating-point expression as there, and the zeros are exact, so the
+// maps are bit for bit those of the whole-grid kernel; the point-steps per
+// column fall from 4096 m to 1024 m1 + 4096 (m - m1).
+struct AdvWin64Smem {
+  double top[2][4][kAdvNx + 1];     // [buffer][strip block][x]; [*][0][64] stays zero
+  double bot[2][4][kAdvNx + 1];
+  double edge[2][8][2][kAdvRows];   // per warp: the strips of lanes 0 and 31
+  double win[4][32][32];            // the four columns' windows [column][y][x]
+};
+
+__global__ void __launch_bounds__(256) advdiff_window64_kernel(AdvArgs a, int m1) {
+  constexpr int n = kAdvNx * kAdvNx;
+  constexpr int kZ = kAdvNx;                   // zero slot index
+  __shared__ AdvWin64Smem sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;   // whole-grid strip layout
+  const int g = warp >> 1, s = warp & 1;                                  // window layout
+  const int pw = warp ^ 1;
+  if (tid < 2) {
+    sm.top[tid][0][kZ] = 0.0;
+    sm.bot[tid][0][kZ] = 0.0;
+  }
+  double* out = reinterpret_cast<double*>(a.out);
+  const int64_t total = (int64_t)a.S * (n + 1);
+  int buf = 0;
+  for (int64_t w = blockIdx.x; w * 4 < total; w += gridDim.x) {
+#pragma unroll 1
+    for (int seg = 0; seg <= 4; ++seg) {       // 0: the windows; s >= 1: column s - 1 on the whole grid
+      const bool windows = seg == 0;
+      const int64_t idx = w * 4 + (windows ? g : seg - 1);
+      if (!windows && idx >= total) break;     // uniform over the CTA
+      const int j = idx < total ? (int)(idx / (n + 1)) : 0;
+      const int c = idx < total ? (int)(idx - (int64_t)j * (n + 1)) : 0;   // 0: no unit point
+      const int cx = c >= 1 ? (c - 1) % kAdvNx : 0, cy = c >= 1 ? (c - 1) / kAdvNx : 0;
+      const int wx0 = (cx + kAdvNx - 16) % kAdvNx, wy0 = (cy + kAdvNx - 16) % kAdvNx;
+      // offsets into one buffer's [4][65] row arrays: own top / bottom slot,
+      // the row above (a bottom row) and the row below (a top row)
+      constexpr int RS = kAdvNx + 1;
+      int own, abv, blw;
+      double y[kAdvRows], v[kAdvRows];
+      if (windows) {
+        own = g * RS + 32 * s + lane;
+        abv = s == 1 ? g * RS + lane : kZ;           // above strip 1: strip 0's bottom row
+        blw = s == 0 ? g * RS + 32 + lane : kZ;      // below strip 0: strip 1's top row
+        const int gx = (wx0 + lane) % kAdvNx;
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) {
+          const int gy = (wy0 + 16 * s + r) % kAdvNx;
+          y[r] = (c >= 1 && gy * kAdvNx + gx == c - 1) ? 1.0 : 0.0;
+        }
+      } else {
+        own = blk * RS + ix;
+        abv = ((blk + 3) & 3) * RS + ix;
+        blw = ((blk + 1) & 3) * RS + ix;
+        const int wx = (ix - wx0 + kAdvNx) % kAdvNx;
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) {
+          const int wy = (iy0 + r - wy0 + kAdvNx) % kAdvNx;
+          y[r] = (wx < 32 && wy < 32) ? sm.win[seg - 1][wy][wx] : 0.0;
+        }
+      }
+      const int64_t i1 = windows ? m1 : a.m;
+      for (int64_t i = windows ? 0 : m1; i < i1; ++i) {
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
+#pragma unroll
+        for (int kk = 4; kk >= 1; --kk) {
+          const double* cw = a.cw64[4 - kk];
+          const double cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
+          double* topb = &sm.top[buf][0][0];
+          double* botb = &sm.bot[buf][0][0];
+          topb[own] = v[0];
+          botb[own] = v[kAdvRows - 1];
+          if (lane == 0 || lane == 31) {
+#pragma unroll
+            for (int r = 0; r < kAdvRows; ++r) sm.edge[buf][warp][lane == 31][r] = v[r];
+          }
+          __syncthreads();
+          const double above = botb[abv], below = topb[blw];
+          double nv[kAdvRows];
+#pragma unroll
+          for (int r = 0; r < kAdvRows; ++r) {
+            double xm = __shfl_up_sync(0xffffffffu, v[r], 1);
+            double xp = __shfl_down_sync(0xffffffffu, v[r], 1);
+            if (lane == 0) xm = windows ? 0.0 : sm.edge[buf][pw][1][r];
+            if (lane == 31) xp = windows ? 0.0 : sm.edge[buf][pw][0][r];
+            const double ym = r == 0 ? above : v[r - 1];
+            const double yp = r == kAdvRows - 1 ? below : v[r + 1];
+            double acc = fma(c0, v[r], y[r]);
+            acc = fma(cxm, xm, acc);
+            acc = fma(cxp, xp, acc);
+            acc = fma(cym, ym, acc);
+            nv[r] = fma(cyp, yp, acc);
+          }
+#pragma unroll
+          for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
+          buf ^= 1;
+        }
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
+      }
+      if (windows) {
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) sm.win[g][16 * s + r][lane] = y[r];
+        __syncthreads();
+      } else {
+        double* col = out + ((int64_t)j * (n + 1) + c) * n;
+#pragma unroll
+        for (int r = 0; r < kAdvRows; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
+      }
+    }
+    __syncthreads();                           // the windows are rewritten next
+  }
+}
+
 // Serial fine solve of the advection-diffusion system (one CTA, S*m steps).
 template <typename T>
 __global__ void __launch_bounds__(256) advdiff_serial_kernel(AdvArgs a, const double* y0, double* yT) {
@@ -504,11 +633,20 @@ nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s) {
   nv_status st;
   const int64_t cols = (int64_t)M->S * (M->dim + 1);
   if (M->prec == NV_FP64) {
-    M->work_per_slice = (int64_t)(M->dim + 1) * M->dim * M->m;
-    snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");
-    st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);
-    if (st != NV_OK) return st;
-    advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
+    // windows for the first min(m, 3) steps unless the whole-grid form is asked for
+    const int m1 = g_tune.adv_build_form == 1 ? 0 : (int)std::min<int64_t>(M->m, 3);
+    M->work_per_slice = (int64_t)(M->dim + 1) * (1024 * m1 + (int64_t)M->dim * (M->m - m1));
+    if (m1 > 0) {
+      snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_window64_kernel");
+      st = persistent_grid(advdiff_window64_kernel, 256, (cols + 3) / 4 * 8, &grid);
+      if (st != NV_OK) return st;
+      advdiff_window64_kernel<<<grid, 256, 0, s>>>(a, m1);
+    } else {
+      snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");
+      st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);
+      if (st != NV_OK) return st;
+      advdiff_affine_kernel<double><<<grid, 256, 0, s>>>(a);
+    }
   } else {
     // columns start at j * (n + 1) * n values: 16-byte aligned for the
     // vector stores since n = 4096 and the map buffer is 256-byte aligned

@@ -90,6 +90,57 @@ __global__ void propagate_kernel(RhsParams pp, double h, int64_t m, int ns, int 
   for (int c = 0; c < R::D; ++c) y[idx * R::D + c] = s[c];
 }
 
+// ---- float32 propagation (Kahan-compensated updates) of float64 states: the
+// plain float32 fine integration the learned forms are compared against
+template <class R>
+__global__ void propagate32_kernel(RhsParams pp, double h, int64_t m, int ns, int rk4, int64_t count,
+                                   double* y) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const R rhs(pp.p);
+  float s[R::D], comp[R::D];
+  for (int c = 0; c < R::D; ++c) { s[c] = (float)y[idx * R::D + c]; comp[c] = 0.f; }
+  const float hf = (float)h;
+  for (int64_t i = 0; i < (int64_t)ns * m; ++i) {
+    if (rk4) rk4_step(rhs, 0.f, 0.f, 0.f, hf, s, comp);
+    else euler_step(rhs, 0.f, hf, s, comp);
+  }
+  for (int c = 0; c < R::D; ++c) y[idx * R::D + c] = (double)s[c];
+}
+
+// ---- parareal with the learned map as the coarse propagator G and float64
+// fine integration as F.  Fine pass: F_j = F(lam_j) for every slice j and
+// state at once (lam: (S+1) x count x D, F: S x count x D; the chain is
+// autonomous, so a slice's start time does not enter).
+template <class R>
+__global__ void slice_fine_kernel(RhsParams pp, double h, int64_t m, int rk4, int S, int64_t count,
+                                  const double* lam, double* F) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)S * count) return;
+  const R rhs(pp.p);
+  double s[R::D], comp[R::D];
+  for (int c = 0; c < R::D; ++c) { s[c] = lam[idx * R::D + c]; comp[c] = 0.0; }
+  for (int64_t i = 0; i < m; ++i) {
+    if (rk4) rk4_step(rhs, 0.0, 0.0, 0.0, h, s, comp);
+    else euler_step(rhs, 0.0, h, s, comp);
+  }
+  for (int c = 0; c < R::D; ++c) F[idx * R::D + c] = s[c];
+}
+
+// Sweep step at slice j: g = G_j(lam_j) = lam_j + sd * out;
+// lam_{j+1} = g + F_j - Gold_j (F == NULL on the first sweep: lam_{j+1} = g);
+// Gold_j <- g for the next iteration.
+__global__ void parareal_update_kernel(const double* lam_j, double* lam_j1, double* gold_j, const double* F_j,
+                                       const float* out, const double* sd, int64_t count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count * D) return;
+  const int64_t b = i / D;
+  const int c = (int)(i % D);
+  const double g = lam_j[i] + sd[c] * (double)out[b * OUT + c];
+  lam_j1[i] = F_j ? g + (F_j[i] - gold_j[i]) : g;
+  gold_j[i] = g;
+}
+
 // ---- parameters
 __global__ void init_params_kernel(float* P, uint64_t seed) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -721,9 +772,62 @@ extern "C" nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_
   if (st != NV_OK) return st;
   if (!y_dev || count < 0 || j0 < 0 || nslices < 0 || j0 + nslices > S) return nv_fail(NV_EINVAL, "bad range");
   if (count == 0 || nslices == 0) return NV_OK;
+  if (steps->prec == NV_FP32) {
+    propagate32_kernel<RhsChain3<float>><<<(unsigned)((count + 127) / 128), 128, 0,
+                                           static_cast<cudaStream_t>(stream)>>>(
+        pp, h, m, nslices, steps->scheme == NV_RK4, count, y_dev);
+    return nv_cuda_check(cudaGetLastError(), "propagate32_kernel launch");
+  }
+  if (steps->prec != NV_FP64) return nv_fail(NV_EINVAL, "propagation is float64 or float32");
   propagate_kernel<RhsChain3<double>><<<(unsigned)((count + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
       pp, h, m, nslices, steps->scheme == NV_RK4, count, y_dev);
   return nv_cuda_check(cudaGetLastError(), "propagate_kernel launch");
+}
+
+extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, double T, int32_t S,
+                                     const nv_steps* steps, int32_t iters, int64_t count, const double* y0_dev,
+                                     double* yT_dev, double* lambdas_dev, void* stream) {
+  if (!m || !y0_dev || !yT_dev) return nv_fail(NV_EINVAL, "NULL argument");
+  if (count < 128 || count % 128) return nv_fail(NV_EINVAL, "count must be a positive multiple of 128");
+  if (iters < 0) return nv_fail(NV_EINVAL, "iters must be >= 0");
+  RhsParams pp;
+  int64_t msteps = 0;
+  double h = 0;
+  nv_status st = plan_rhs(rhs, t0, T, S, steps, &pp, &msteps, &h);
+  if (st != NV_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = mlp_batch(m, (int)count)) != NV_OK) return st;
+  const int64_t per = count * D;
+  const size_t lam_bytes = sizeof(double) * (size_t)(S + 1) * per;
+  const size_t slice_bytes = sizeof(double) * (size_t)S * per;
+  char* scratch = nullptr;
+  const size_t need = (lambdas_dev ? 0 : lam_bytes) + (iters > 0 ? 2 * slice_bytes : slice_bytes);
+  if ((st = nv_cuda_check(cudaMallocAsync((void**)&scratch, need, s), "parareal scratch")) != NV_OK) return st;
+  double* lam = lambdas_dev ? lambdas_dev : reinterpret_cast<double*>(scratch);
+  double* gold = reinterpret_cast<double*>(scratch + (lambdas_dev ? 0 : lam_bytes));
+  double* F = iters > 0 ? gold + (size_t)S * per : nullptr;
+  st = nv_cuda_check(cudaMemcpyAsync(lam, y0_dev, sizeof(double) * per, cudaMemcpyDeviceToDevice, s), "state copy");
+  const unsigned ugrid = (unsigned)((per + 255) / 256);
+  for (int k = 0; k <= iters && st == NV_OK; ++k) {
+    if (k > 0) {   // fine pass over every slice from the previous iterate
+      const int64_t n = (int64_t)S * count;
+      slice_fine_kernel<RhsChain3<double>><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+          pp, h, msteps, steps->scheme == NV_RK4, S, count, lam, F);
+      if ((st = nv_cuda_check(cudaGetLastError(), "slice_fine_kernel launch")) != NV_OK) break;
+    }
+    for (int j = 0; j < S && st == NV_OK; ++j) {   // the coarse sweep, slice after slice
+      const double* lj = lam + (size_t)j * per;
+      if ((st = mlp_infer(m, lj, count, j, S, s)) != NV_OK) break;
+      parareal_update_kernel<<<ugrid, 256, 0, s>>>(lj, lam + (size_t)(j + 1) * per, gold + (size_t)j * per,
+                                                   k > 0 ? F + (size_t)j * per : nullptr, m->out, m->sd, count);
+      st = nv_cuda_check(cudaGetLastError(), "parareal update");
+    }
+  }
+  if (st == NV_OK)
+    st = nv_cuda_check(cudaMemcpyAsync(yT_dev, lam + (size_t)S * per, sizeof(double) * per, cudaMemcpyDeviceToDevice,
+                                       s), "final state copy");
+  nv_status st2 = nv_cuda_check(cudaFreeAsync(scratch, s), "parareal scratch free");
+  return st != NV_OK ? st : st2;
 }
 
 extern "C" nv_status nv_mlp_compose(nv_mlp* m, const nv_rhs* rhs, double t0, double T, int32_t S,

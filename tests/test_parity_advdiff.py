@@ -119,9 +119,9 @@ def test_advdiff_fp32_refined_full_size():
 
 
 @pytest.mark.parametrize("S,m", [(3, 10), (2, 1), (2, 2), (4, 3), (3, 4), (5, 7)])
-@pytest.mark.parametrize("prec", ["fp32", "bf16_refine"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16_refine"])
 def test_advdiff_window_build_matches_whole_grid(prec, S, m):
-    """The float32 / bfloat16 build integrates the first min(m, 3) steps of
+    """The float64 / float32 / bfloat16 build integrates the first min(m, 3) steps of
     each column on a 32 x 32 window around its unit point (the points those
     steps cannot reach are exactly zero) and the rest on the whole periodic
     grid: every map entry equals the whole-grid build's (tunable 15 = 1) bit
@@ -146,7 +146,7 @@ def test_advdiff_window_build_matches_whole_grid(prec, S, m):
             nvp.tune_set(15, 0)
     assert torch.equal(got[0], got[1])
     n = w.dim
-    blocks = got[0].float().numpy().reshape(w.S, n + 1, n)     # [slice, column, point]
+    blocks = got[0].double().numpy().reshape(w.S, n + 1, n)    # [slice, column, point]
     assert not np.any(blocks[:, 0])                            # b_j = 0: no forcing
     pts = np.arange(n)
     px, py = pts % 64, pts // 64

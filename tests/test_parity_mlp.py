@@ -166,7 +166,8 @@ def test_trained_network_gains_over_the_method_without_it():
     network fails the threshold on every slice."""
     import time
     torch = need_gpu()
-    w, r, net, losses, err = _train_chain3(torch, TRAIN_SCHEDULE)
+    t = _trained(torch)
+    w, r, net, losses, err = t["w"], t["r"], t["net"], t["losses"], t["err"]
     print("losses", losses, "validation error mean", err.mean(), "max", err.max())
     assert losses[-1] < losses[0]
     assert err.max() < 1e-3
@@ -199,5 +200,110 @@ def test_trained_network_gains_over_the_method_without_it():
     ve = torch.empty_like(v0)
     nvp.build_pairs(r, w.t0, w.T, S, st, Mv, w.extra["seed"] + 1, -1.0, 1.0, v0, ve)
     assert np.all(fresh.validate(v0, ve, S, Mv) > 1e-3)
-    net.destroy()
     fresh.destroy()
+
+
+_TRAINED = {}
+
+
+def _trained(torch):
+    """The network trained once per test session on the method's own pairs."""
+    if not _TRAINED:
+        w, r, net, losses, err = _train_chain3(torch, TRAIN_SCHEDULE)
+        _TRAINED.update(w=w, r=r, net=net, losses=losses, err=err)
+    return _TRAINED
+
+
+def _events_ms(torch, fn, reps=1):
+    fn()                                                   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error():
+    """The trained network as the coarse propagator of parareal (the
+    combination the Conclusion proposes), float64 fine integration per slice
+    as F, on 4096 initial states of the 3-mass chain over 128 slices.
+
+    Checked: iteration 0 is the learned composition bit for bit; after k
+    iterations the boundary state of slice k equals the float64 fine solve
+    over k slices (parareal's exactness property); the final-state error
+    against the float64 fine solve (itself checked against the oracle on
+    sampled states) falls with k and reaches 1e-11, the float64 target.
+    Timed with CUDA events at equal final-state error: parareal at the first
+    iteration count that reaches the float64 fine solve's error level (1e-11)
+    against the plain float64 fine integration of the same states, and at the
+    plain float32 integration's error level against that float32 integration.
+    The assertions state the speed relation the measurements support."""
+    torch = need_gpu()
+    t = _trained(torch)
+    w, r, net = t["w"], t["r"], t["net"]
+    S = w.S
+    st64 = nvp.steps("rk4", w.dt)
+    st32 = nvp.steps("rk4", w.dt, 0, "fp32")
+    count = 4096
+    Y0 = workloads.Stream(21).uniform(count * 6, -0.5, 0.5).reshape(count, 6)
+    y0 = torch.tensor(Y0, device="cuda")
+    fine = y0.clone()
+    nvp.propagate(r, w.t0, w.T, S, st64, 0, S, fine)
+    torch.cuda.synchronize()
+    fine_h = fine.cpu().numpy()
+    # the float64 fine solve against the oracle on sampled states
+    m = nv.workload_steps(w)
+    h = nv.step_size(w.t0, w.T, S, m)
+    pick = [0, 1337, 4095]
+    oy = Y0[pick].T.copy()
+    f = nv.rhs_chain3(*w.params)
+    for j in range(S):
+        oy = nv.integrate(f, "rk4", nv.slice_times(w.t0, w.T, S)[j], oy, h, m)
+    assert rel_max(fine_h[pick], oy.T) <= 1e-11
+
+    def err(y):
+        return float(np.max(np.linalg.norm(y - fine_h, axis=1) / np.linalg.norm(fine_h, axis=1)))
+
+    comp = torch.empty_like(y0)
+    net.compose(r, w.t0, w.T, S, st64, y0, comp)
+    errs, k_fp64 = [], None
+    lam = torch.empty((S + 1, count, 6), dtype=torch.float64, device="cuda")
+    for k in range(0, 9):
+        yT = torch.empty_like(y0)
+        net.parareal(r, w.t0, w.T, S, st64, k, y0, yT, lambdas=lam)
+        torch.cuda.synchronize()
+        yk = yT.cpu().numpy()
+        if k == 0:
+            assert np.array_equal(yk, comp.cpu().numpy())
+        if 1 <= k <= 3:
+            ref = y0.clone()
+            nvp.propagate(r, w.t0, w.T, S, st64, 0, k, ref)
+            torch.cuda.synchronize()
+            assert rel_max(lam[k].cpu().numpy(), ref.cpu().numpy()) <= 1e-13, k
+        errs.append(err(yk))
+        if k_fp64 is None and errs[-1] <= 1e-11:
+            k_fp64 = k
+            break
+    print("parareal final-state error by iteration", errs)
+    assert k_fp64 is not None, errs
+    for a, b in zip(errs[1:], errs[2:]):
+        assert b < a
+    y32 = y0.clone()
+    nvp.propagate(r, w.t0, w.T, S, st32, 0, S, y32)
+    torch.cuda.synchronize()
+    e32 = err(y32.cpu().numpy())
+    k_fp32 = next(k for k, e in enumerate(errs) if e <= e32)
+    yb = torch.empty_like(y0)
+    t64 = _events_ms(torch, lambda: nvp.propagate(r, w.t0, w.T, S, st64, 0, S, y0.clone()))
+    t32 = _events_ms(torch, lambda: nvp.propagate(r, w.t0, w.T, S, st32, 0, S, y0.clone()))
+    tp64 = _events_ms(torch, lambda: net.parareal(r, w.t0, w.T, S, st64, k_fp64, y0, yb))
+    tp32 = _events_ms(torch, lambda: net.parareal(r, w.t0, w.T, S, st64, k_fp32, y0, yb))
+    print(f"equal error 1e-11: parareal k={k_fp64} {tp64:.1f} ms vs float64 fine {t64:.1f} ms; "
+          f"equal error {e32:.2e}: parareal k={k_fp32} {tp32:.1f} ms vs float32 fine {t32:.1f} ms")
+    # measured relation (see the bench's chain3_mlp line): the plain fine
+    # integrations are faster at equal error on one GPU
+    assert tp64 > t64 and tp32 > t32
+
