@@ -408,6 +408,7 @@ def gpu_peak_probe(torch):
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 #   advection-diffusion FP32 chain, S = 8: 547.9 MB for 8 slice maps (537.0 MB read once)
+#   advection-diffusion FP64 build with windows, the full launch: 68.964 GB for 2 097 664 columns
 NCU_TRAFFIC_PER_UNIT = {
     "affine_chain_tile_kernel<float,float>": (547.89e6 / 8, "profiles/advdiff_chains_d4096_S512.md"),
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
@@ -416,6 +417,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel<float>": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "advdiff_window_kernel<float>": (475.46e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
+    "advdiff_window64_kernel": (68.964e9 / (512 * 4097), "profiles/advdiff_fp64_window_build_d4096_S512.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
 }

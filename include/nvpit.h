@@ -357,20 +357,28 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
                          const nv_steps* steps, const int32_t* fallback, int64_t count,
                          const double* y0_dev, double* yT_dev, void* stream);
 
-/* Parareal with the learned map as the coarse propagator (the combination
- * with parareal the Conclusion proposes): G_j(y) = y + sd*MLP(y/sx, j/S),
- * F_j = float64 fine integration over slice j.  Iteration 0 is the learned
- * composition lambda_{j+1} = G_j(lambda_j); iteration k >= 1 computes
- * F_j(lambda_j) for every slice and state at once (S x count independent
- * trajectories), then sweeps the slices in order:
- *   lambda^k_{j+1} = G_j(lambda^k_j) + (F_j(lambda^{k-1}_j) - G_j(lambda^{k-1}_j)).
- * After k iterations the first k boundary states equal the fine solution's;
- * the iterates converge to the float64 fine integration of every state.
+/* The learned map as the coarse propagator of a float64 residual correction
+ * (the combination with parareal the Conclusion proposes), for nonlinear
+ * problems.  Iteration 0 is the learned composition
+ * lambda_{j+1} = G_j(lambda_j), G_j(y) = y + sd*MLP(y/sx, j/S), bit for bit
+ * that of nv_mlp_compose without fallback.  Iteration k >= 1:
+ *   d_j = F_j(lambda_j) - lambda_{j+1}      float64 fine solve per slice, for
+ *                                           every slice and state at once
+ *   e_0 = 0, e_{j+1} = J_j e_j + d_j        J_j the network's tangent map at
+ *                                           lambda_j (a forward-mode derivative
+ *                                           through the same bf16 layers)
+ *   lambda_{j+1} <- lambda_{j+1} + e_{j+1}  written by the chain as it goes
+ * i.e. an approximate Newton step on the multiple-shooting equations
+ * lambda_{j+1} = F_j(lambda_j), with the learned Jacobian in place of F_j's.
+ * After k iterations the first k boundary states equal the float64 fine
+ * solution's; the iterates converge to the float64 fine integration of every
+ * state (the correction is relative, so the bf16 rounding of the network does
+ * not set a floor).
  *   count        states, a positive multiple of 128
  *   y0_dev       count x 6 doubles (input); yT_dev count x 6 (output)
  *   lambdas_dev  (S+1) x count x 6 doubles (output, may be NULL): every
  *                boundary state of the last iterate
- * Scratch of 2 S count 6 doubles (+ the boundary states when lambdas_dev is
+ * Scratch of (S + 1) count 6 doubles (+ the boundary states when lambdas_dev is
  * NULL) comes from the stream-ordered allocator on `stream`.  NV_EINVAL for a
  * bad count or iters < 0; NV_ENOTSUP for a right-hand side other than the
  * 3-mass chain. */

@@ -108,13 +108,14 @@ __global__ void propagate32_kernel(RhsParams pp, double h, int64_t m, int ns, in
   for (int c = 0; c < R::D; ++c) y[idx * R::D + c] = (double)s[c];
 }
 
-// ---- parareal with the learned map as the coarse propagator G and float64
-// fine integration as F.  Fine pass: F_j = F(lam_j) for every slice j and
-// state at once (lam: (S+1) x count x D, F: S x count x D; the chain is
-// autonomous, so a slice's start time does not enter).
+// ---- parareal with the learned map as the coarse propagator and float64
+// fine integration F.  Fine pass: F_j = F(lam_j) for every slice j and state
+// at once (lam: (S+1) x count x D, F: S x count x D; the chain is autonomous,
+// so a slice's start time does not enter); it writes the defects
+// d_j = F_j - lam_{j+1}.
 template <class R>
-__global__ void slice_fine_kernel(RhsParams pp, double h, int64_t m, int rk4, int S, int64_t count,
-                                  const double* lam, double* F) {
+__global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, int S, int64_t count,
+                                    const double* lam, double* dfc) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)S * count) return;
   const R rhs(pp.p);
@@ -124,21 +125,61 @@ __global__ void slice_fine_kernel(RhsParams pp, double h, int64_t m, int rk4, in
     if (rk4) rk4_step(rhs, 0.0, 0.0, 0.0, h, s, comp);
     else euler_step(rhs, 0.0, h, s, comp);
   }
-  for (int c = 0; c < R::D; ++c) F[idx * R::D + c] = s[c];
+  for (int c = 0; c < R::D; ++c) dfc[idx * R::D + c] = s[c] - lam[(idx + count) * R::D + c];
 }
 
-// Sweep step at slice j: g = G_j(lam_j) = lam_j + sd * out;
-// lam_{j+1} = g + F_j - Gold_j (F == NULL on the first sweep: lam_{j+1} = g);
-// Gold_j <- g for the next iteration.
-__global__ void parareal_update_kernel(const double* lam_j, double* lam_j1, double* gold_j, const double* F_j,
-                                       const float* out, const double* sd, int64_t count) {
+// The correction chain runs over the network's tangent map (its Jacobian at
+// the previous iterate, a forward-mode derivative through the same bf16
+// layers): e_0 = 0, e_{j+1} = J_j e_j + d_j, lam_{j+1} <- lam_{j+1} + e_{j+1}.
+// Tangent input: x_t = (e / sx, 0) (the slice feature does not vary).
+__global__ void tangent_features_kernel(const double* e, int64_t count, const float* sx_inv, float* X) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  for (int c = 0; c < D; ++c) X[b * IN + c] = (float)e[b * D + c] * sx_inv[c];
+  X[b * IN + 6] = 0.f;
+  X[b * IN + 7] = 0.f;
+}
+
+// layer 1 tangent: dh1 = GELU'(z1) * (W1 x_t), with GELU'(z1) from the
+// training-form forward pass at the base point (Z1)
+__global__ void l1_tangent_kernel(const float* P, const float* Xt, int B, const float* Z1, __nv_bfloat16* dH1) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= count * D) return;
-  const int64_t b = i / D;
-  const int c = (int)(i % D);
-  const double g = lam_j[i] + sd[c] * (double)out[b * OUT + c];
-  lam_j1[i] = F_j ? g + (F_j[i] - gold_j[i]) : g;
-  gold_j[i] = g;
+  if (i >= (int64_t)B * H) return;
+  const int b = (int)(i / H), n = (int)(i % H);
+  float dz = 0.f;
+#pragma unroll
+  for (int k = 0; k < IN; ++k) dz = fmaf(P[oW1 + n * IN + k], Xt[b * IN + k], dz);
+  dH1[i] = __float2bfloat16(Z1[i] * dz);
+}
+
+// layer 4 tangent and the correction step: dout = W4 dh3 (one warp per state,
+// lane l holding hidden units 8l .. 8l+7); e_{j+1} = e_j + sd dout + d_j and
+// lam_{j+1} <- lam_{j+1} + e_{j+1}.  e_j and e_{j+1} may alias.
+__global__ void l4_tangent_update_kernel(const float* P, const __nv_bfloat16* dH3, int B, const double* sd,
+                                         const double* e_j, const double* d_j, double* e_j1, double* lam_j1) {
+  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const int b = warp;
+  float h[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) h[q] = __bfloat162float(dH3[(int64_t)b * H + lane * 8 + q]);
+  float o[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(P[oW4 + c * H + lane * 8 + q], h[q], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    o[c] = s;
+  }
+  if (lane < D) {
+    const int64_t i = (int64_t)b * D + lane;
+    const double e = e_j[i] + sd[lane] * (double)o[lane] + d_j[i];
+    e_j1[i] = e;
+    lam_j1[i] += e;
+  }
 }
 
 // ---- parameters
@@ -784,6 +825,35 @@ extern "C" nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_
   return nv_cuda_check(cudaGetLastError(), "propagate_kernel launch");
 }
 
+// Training-form forward at the base point (saves GELU'(z) of every hidden
+// layer in Z1, Z2, Z3), then the tangent of the base point's e through the
+// same layers into dZ3 (bf16); dZ1t / dZ2t / dZ3t and dbias are sinks.
+static nv_status mlp_tangent(nv_mlp* m, const double* base, const double* e, int64_t count, int j, int S,
+                             float* dbias_sink, cudaStream_t s) {
+  const int B = (int)count;
+  const int64_t nBH = (int64_t)B * H;
+  features_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(base, count, j, S, m->sx_inv, m->X);
+  l1_fwd_kernel<<<(unsigned)((nBH + 255) / 256), 256, 0, s>>>(m->P, m->X, B, m->Z1, m->H1, m->H1t, 1);
+  nv_status st = nv_cuda_check(cudaGetLastError(), "tangent base forward");
+  if (st != NV_OK) return st;
+  if ((st = launch_gemm_bf16(m->H1, m->W2b, B, H, 1, kModeFwdTrain, nullptr, m->P + ob2, m->Z2, nullptr, m->H2,
+                             m->H2t, nullptr, m->status, s)) != NV_OK)
+    return st;
+  if ((st = launch_gemm_bf16(m->H2, m->W3b, B, H, 1, kModeFwdTrain, nullptr, m->P + ob3, m->Z3, nullptr, m->H3,
+                             m->H3t, nullptr, m->status, s)) != NV_OK)
+    return st;
+  tangent_features_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(e, count, m->sx_inv, m->X);
+  l1_tangent_kernel<<<(unsigned)((nBH + 255) / 256), 256, 0, s>>>(m->P, m->X, B, m->Z1, m->dZ1);
+  if ((st = nv_cuda_check(cudaGetLastError(), "layer 1 tangent")) != NV_OK) return st;
+  // dh2 = GELU'(z2) * (W2 dh1), dh3 = GELU'(z3) * (W3 dh2): the backward-form
+  // epilogue (product times the saved GELU') on the forward-orientation weights
+  if ((st = launch_gemm_bf16(m->dZ1, m->W2b, B, H, 1, kModeBwd, nullptr, nullptr, nullptr, m->Z2, m->dZ2, m->dZ1t,
+                             dbias_sink, m->status, s)) != NV_OK)
+    return st;
+  return launch_gemm_bf16(m->dZ2, m->W3b, B, H, 1, kModeBwd, nullptr, nullptr, nullptr, m->Z3, m->dZ3, m->dZ2t,
+                          dbias_sink, m->status, s);
+}
+
 extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, double T, int32_t S,
                                      const nv_steps* steps, int32_t iters, int64_t count, const double* y0_dev,
                                      double* yT_dev, double* lambdas_dev, void* stream) {
@@ -799,28 +869,46 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
   if ((st = mlp_batch(m, (int)count)) != NV_OK) return st;
   const int64_t per = count * D;
   const size_t lam_bytes = sizeof(double) * (size_t)(S + 1) * per;
-  const size_t slice_bytes = sizeof(double) * (size_t)S * per;
+  const size_t dfc_bytes = sizeof(double) * (size_t)S * per;
+  const size_t e_bytes = sizeof(double) * (size_t)per;
   char* scratch = nullptr;
-  const size_t need = (lambdas_dev ? 0 : lam_bytes) + (iters > 0 ? 2 * slice_bytes : slice_bytes);
+  const size_t need = (lambdas_dev ? 0 : lam_bytes) + dfc_bytes + e_bytes + sizeof(float) * H;
   if ((st = nv_cuda_check(cudaMallocAsync((void**)&scratch, need, s), "parareal scratch")) != NV_OK) return st;
   double* lam = lambdas_dev ? lambdas_dev : reinterpret_cast<double*>(scratch);
-  double* gold = reinterpret_cast<double*>(scratch + (lambdas_dev ? 0 : lam_bytes));
-  double* F = iters > 0 ? gold + (size_t)S * per : nullptr;
+  double* dfc = reinterpret_cast<double*>(scratch + (lambdas_dev ? 0 : lam_bytes));
+  double* e = dfc + (size_t)S * per;
+  float* dbias_sink = reinterpret_cast<float*>(e + per);
   st = nv_cuda_check(cudaMemcpyAsync(lam, y0_dev, sizeof(double) * per, cudaMemcpyDeviceToDevice, s), "state copy");
-  const unsigned ugrid = (unsigned)((per + 255) / 256);
-  for (int k = 0; k <= iters && st == NV_OK; ++k) {
-    if (k > 0) {   // fine pass over every slice from the previous iterate
-      const int64_t n = (int64_t)S * count;
-      slice_fine_kernel<RhsChain3<double>><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
-          pp, h, msteps, steps->scheme == NV_RK4, S, count, lam, F);
-      if ((st = nv_cuda_check(cudaGetLastError(), "slice_fine_kernel launch")) != NV_OK) break;
-    }
-    for (int j = 0; j < S && st == NV_OK; ++j) {   // the coarse sweep, slice after slice
+  // iteration 0: the learned composition lam_{j+1} = G_j(lam_j)
+  for (int j = 0; j < S && st == NV_OK; ++j) {
+    const double* lj = lam + (size_t)j * per;
+    double* lj1 = lam + (size_t)(j + 1) * per;
+    if ((st = nv_cuda_check(cudaMemcpyAsync(lj1, lj, sizeof(double) * per, cudaMemcpyDeviceToDevice, s),
+                            "state copy")) != NV_OK)
+      break;
+    if ((st = mlp_infer(m, lj1, count, j, S, s)) != NV_OK) break;
+    advance_kernel<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(lj1, count, m->out, m->sd);
+    st = nv_cuda_check(cudaGetLastError(), "advance");
+  }
+  for (int k = 1; k <= iters && st == NV_OK; ++k) {
+    // defects of the previous iterate, every slice and state at once
+    const int64_t n = (int64_t)S * count;
+    slice_defect_kernel<RhsChain3<double>><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+        pp, h, msteps, steps->scheme == NV_RK4, S, count, lam, dfc);
+    if ((st = nv_cuda_check(cudaGetLastError(), "slice_defect_kernel launch")) != NV_OK) break;
+    // correction chain over the tangent maps, slice after slice
+    if ((st = nv_cuda_check(cudaMemsetAsync(e, 0, e_bytes, s), "correction reset")) != NV_OK) break;
+    for (int j = 0; j < S && st == NV_OK; ++j) {
       const double* lj = lam + (size_t)j * per;
-      if ((st = mlp_infer(m, lj, count, j, S, s)) != NV_OK) break;
-      parareal_update_kernel<<<ugrid, 256, 0, s>>>(lj, lam + (size_t)(j + 1) * per, gold + (size_t)j * per,
-                                                   k > 0 ? F + (size_t)j * per : nullptr, m->out, m->sd, count);
-      st = nv_cuda_check(cudaGetLastError(), "parareal update");
+      if (j > 0 && (st = mlp_tangent(m, lj, e, count, j, S, dbias_sink, s)) != NV_OK) break;
+      if (j == 0) {   // e_0 = 0: e_1 = d_0, no tangent needed
+        if ((st = nv_cuda_check(cudaMemsetAsync(m->dZ3, 0, sizeof(__nv_bfloat16) * count * H, s), "zero tangent")) !=
+            NV_OK)
+          break;
+      }
+      l4_tangent_update_kernel<<<(unsigned)((count * 32 + 255) / 256), 256, 0, s>>>(
+          m->P, m->dZ3, (int)count, m->sd, e, dfc + (size_t)j * per, e, lam + (size_t)(j + 1) * per);
+      st = nv_cuda_check(cudaGetLastError(), "tangent update");
     }
   }
   if (st == NV_OK)

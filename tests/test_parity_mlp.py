@@ -271,7 +271,7 @@ def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error(
     net.compose(r, w.t0, w.T, S, st64, y0, comp)
     errs, k_fp64 = [], None
     lam = torch.empty((S + 1, count, 6), dtype=torch.float64, device="cuda")
-    for k in range(0, 9):
+    for k in range(0, 13):
         yT = torch.empty_like(y0)
         net.parareal(r, w.t0, w.T, S, st64, k, y0, yT, lambdas=lam)
         torch.cuda.synchronize()
@@ -303,7 +303,12 @@ def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error(
     tp32 = _events_ms(torch, lambda: net.parareal(r, w.t0, w.T, S, st64, k_fp32, y0, yb))
     print(f"equal error 1e-11: parareal k={k_fp64} {tp64:.1f} ms vs float64 fine {t64:.1f} ms; "
           f"equal error {e32:.2e}: parareal k={k_fp32} {tp32:.1f} ms vs float32 fine {t32:.1f} ms")
-    # measured relation (see the bench's chain3_mlp line): the plain fine
-    # integrations are faster at equal error on one GPU
+    # Measured on a GB300: the correction contracts the error ~50x per
+    # iteration (0.12, 4.1e-3, 6.5e-5, 1.3e-6, 1.9e-8, 2.8e-10, 2.7e-12) and
+    # reaches 1e-11 at k = 6 in 213 ms against 81 ms for the float64 fine
+    # integration of the same states, and the float32 level (1.2e-6) at k = 4
+    # in 146 ms against 2.3 ms.  On one GPU the plain integration, already
+    # parallel over the 4096 states, is faster at equal error: the learned form
+    # does the fine work k times to gain a parallelism the GPU already has.
     assert tp64 > t64 and tp32 > t32
 
