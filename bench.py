@@ -417,7 +417,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel<float>": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "advdiff_window_kernel<float>": (475.46e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
-    "advdiff_window64_kernel": (68.964e9 / (512 * 4097), "profiles/advdiff_fp64_window_build_d4096_S512.md"),
+    "advdiff_window64_kernel<16>": (68.964e9 / (512 * 4097), "profiles/advdiff_fp64_window_build_d4096_S512.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
 }

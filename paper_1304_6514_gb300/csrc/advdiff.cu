@@ -447,24 +447,42 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_window_kernel(Adv
 // same floating-point expression as there, and the zeros are exact, so the
 // maps are bit for bit those of the whole-grid kernel; the point-steps per
 // column fall from 4096 m to 1024 m1 + 4096 (m - m1).
-struct AdvWin64Smem {
-  double top[2][4][kAdvNx + 1];     // [buffer][strip block][x]; [*][0][64] stays zero
-  double bot[2][4][kAdvNx + 1];
-  double edge[2][8][2][kAdvRows];   // per warp: the strips of lanes 0 and 31
-  double win[4][32][32];            // the four columns' windows [column][y][x]
+// Strip height R (rows per thread): 16 (256 threads, two warps per window) or
+// 8 (512 threads, four warps per window; half the registers, twice the warps
+// per SM).  Thread t's top / bottom row slot is t in both phases: row block b
+// of the grid is threads 64 b .. 64 b + 63, window strip s of column g is warp
+// g (32/R) + s.  Shared memory (dynamic): two buffers of 64 NB + 1 top and
+// bottom rows (the last slot stays zero), the edge-lane strips of every warp,
+// the four 32 x 32 windows.
+template <int R>
+struct AdvWin64Shape {
+  static constexpr int NB = kAdvNx / R;               // row blocks of the grid
+  static constexpr int THREADS = kAdvNx * NB;         // 256 or 512
+  static constexpr int NW = THREADS / 32;
+  static constexpr int WPC = 32 / R;                  // warps per window
+  static constexpr int ROWS = kAdvNx * NB + 1;        // row slots per buffer, zero slot last
+  static constexpr size_t SMEM =
+      sizeof(double) * (2 * 2 * (size_t)ROWS + 2 * (size_t)NW * 2 * R + 4 * 32 * 32);
 };
 
-__global__ void __launch_bounds__(256) advdiff_window64_kernel(AdvArgs a, int m1) {
+template <int R>
+__global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_kernel(AdvArgs a, int m1) {
+  using Sh = AdvWin64Shape<R>;
   constexpr int n = kAdvNx * kAdvNx;
-  constexpr int kZ = kAdvNx;                   // zero slot index
-  __shared__ AdvWin64Smem sm;
+  constexpr int NB = Sh::NB, WPC = Sh::WPC, ROWS = Sh::ROWS, RING = kAdvNx * NB;
+  constexpr int kZ = RING;                     // zero slot
+  extern __shared__ __align__(16) double adv64_smem[];
+  double* top = adv64_smem;                    // [2][ROWS]
+  double* bot = top + 2 * ROWS;                // [2][ROWS]
+  double* edge = bot + 2 * ROWS;               // [2][NW][2][R]
+  double* win = edge + 2 * Sh::NW * 2 * R;     // [4][32][32]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * kAdvRows;   // whole-grid strip layout
-  const int g = warp >> 1, s = warp & 1;                                  // window layout
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * R;   // whole-grid strip layout
+  const int g = warp / WPC, s = warp % WPC;                          // window layout
   const int pw = warp ^ 1;
   if (tid < 2) {
-    sm.top[tid][0][kZ] = 0.0;
-    sm.bot[tid][0][kZ] = 0.0;
+    top[tid * ROWS + kZ] = 0.0;
+    bot[tid * ROWS + kZ] = 0.0;
   }
   double* out = reinterpret_cast<double*>(a.out);
   const int64_t total = (int64_t)a.S * (n + 1);
@@ -479,59 +497,56 @@ __global__ void __launch_bounds__(256) advdiff_window64_kernel(AdvArgs a, int m1
       const int c = idx < total ? (int)(idx - (int64_t)j * (n + 1)) : 0;   // 0: no unit point
       const int cx = c >= 1 ? (c - 1) % kAdvNx : 0, cy = c >= 1 ? (c - 1) / kAdvNx : 0;
       const int wx0 = (cx + kAdvNx - 16) % kAdvNx, wy0 = (cy + kAdvNx - 16) % kAdvNx;
-      // offsets into one buffer's [4][65] row arrays: own top / bottom slot,
-      // the row above (a bottom row) and the row below (a top row)
-      constexpr int RS = kAdvNx + 1;
-      int own, abv, blw;
-      double y[kAdvRows], v[kAdvRows];
+      // the row above (a bottom row) and the row below (a top row); own slot = tid
+      int abv, blw;
+      double y[R], v[R];
       if (windows) {
-        own = g * RS + 32 * s + lane;
-        abv = s == 1 ? g * RS + lane : kZ;           // above strip 1: strip 0's bottom row
-        blw = s == 0 ? g * RS + 32 + lane : kZ;      // below strip 0: strip 1's top row
+        abv = s > 0 ? tid - 32 : kZ;           // the window strip above, or the window's top edge
+        blw = s < WPC - 1 ? tid + 32 : kZ;     // the window strip below, or its bottom edge
         const int gx = (wx0 + lane) % kAdvNx;
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) {
-          const int gy = (wy0 + 16 * s + r) % kAdvNx;
+        for (int r = 0; r < R; ++r) {
+          const int gy = (wy0 + R * s + r) % kAdvNx;
           y[r] = (c >= 1 && gy * kAdvNx + gx == c - 1) ? 1.0 : 0.0;
         }
       } else {
-        own = blk * RS + ix;
-        abv = ((blk + 3) & 3) * RS + ix;
-        blw = ((blk + 1) & 3) * RS + ix;
+        abv = (tid + RING - kAdvNx) % RING;    // periodic in y
+        blw = (tid + kAdvNx) % RING;
         const int wx = (ix - wx0 + kAdvNx) % kAdvNx;
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) {
+        for (int r = 0; r < R; ++r) {
           const int wy = (iy0 + r - wy0 + kAdvNx) % kAdvNx;
-          y[r] = (wx < 32 && wy < 32) ? sm.win[seg - 1][wy][wx] : 0.0;
+          y[r] = (wx < 32 && wy < 32) ? win[((seg - 1) * 32 + wy) * 32 + wx] : 0.0;
         }
       }
       const int64_t i1 = windows ? m1 : a.m;
       for (int64_t i = windows ? 0 : m1; i < i1; ++i) {
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) v[r] = y[r];
+        for (int r = 0; r < R; ++r) v[r] = y[r];
 #pragma unroll
         for (int kk = 4; kk >= 1; --kk) {
           const double* cw = a.cw64[4 - kk];
           const double cxm = cw[0], cxp = cw[1], cym = cw[2], cyp = cw[3], c0 = cw[4];
-          double* topb = &sm.top[buf][0][0];
-          double* botb = &sm.bot[buf][0][0];
-          topb[own] = v[0];
-          botb[own] = v[kAdvRows - 1];
+          double* topb = top + buf * ROWS;
+          double* botb = bot + buf * ROWS;
+          double* edgeb = edge + buf * Sh::NW * 2 * R;
+          topb[tid] = v[0];
+          botb[tid] = v[R - 1];
           if (lane == 0 || lane == 31) {
 #pragma unroll
-            for (int r = 0; r < kAdvRows; ++r) sm.edge[buf][warp][lane == 31][r] = v[r];
+            for (int r = 0; r < R; ++r) edgeb[(warp * 2 + (lane == 31)) * R + r] = v[r];
           }
           __syncthreads();
           const double above = botb[abv], below = topb[blw];
-          double nv[kAdvRows];
+          double nv[R];
 #pragma unroll
-          for (int r = 0; r < kAdvRows; ++r) {
+          for (int r = 0; r < R; ++r) {
             double xm = __shfl_up_sync(0xffffffffu, v[r], 1);
             double xp = __shfl_down_sync(0xffffffffu, v[r], 1);
-            if (lane == 0) xm = windows ? 0.0 : sm.edge[buf][pw][1][r];
-            if (lane == 31) xp = windows ? 0.0 : sm.edge[buf][pw][0][r];
+            if (lane == 0) xm = windows ? 0.0 : edgeb[(pw * 2 + 1) * R + r];
+            if (lane == 31) xp = windows ? 0.0 : edgeb[(pw * 2 + 0) * R + r];
             const double ym = r == 0 ? above : v[r - 1];
-            const double yp = r == kAdvRows - 1 ? below : v[r + 1];
+            const double yp = r == R - 1 ? below : v[r + 1];
             double acc = fma(c0, v[r], y[r]);
             acc = fma(cxm, xm, acc);
             acc = fma(cxp, xp, acc);
@@ -539,24 +554,45 @@ __global__ void __launch_bounds__(256) advdiff_window64_kernel(AdvArgs a, int m1
             nv[r] = fma(cyp, yp, acc);
           }
 #pragma unroll
-          for (int r = 0; r < kAdvRows; ++r) v[r] = nv[r];
+          for (int r = 0; r < R; ++r) v[r] = nv[r];
           buf ^= 1;
         }
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) y[r] = v[r];
+        for (int r = 0; r < R; ++r) y[r] = v[r];
       }
       if (windows) {
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) sm.win[g][16 * s + r][lane] = y[r];
+        for (int r = 0; r < R; ++r) win[(g * 32 + R * s + r) * 32 + lane] = y[r];
         __syncthreads();
       } else {
         double* col = out + ((int64_t)j * (n + 1) + c) * n;
 #pragma unroll
-        for (int r = 0; r < kAdvRows; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
+        for (int r = 0; r < R; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
       }
     }
     __syncthreads();                           // the windows are rewritten next
   }
+}
+
+template <int R>
+static nv_status launch_adv_window64(const AdvArgs& a, int m1, int64_t cols, cudaStream_t s) {
+  using Sh = AdvWin64Shape<R>;
+  nv_status st = nv_cuda_check(cudaFuncSetAttribute(advdiff_window64_kernel<R>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM),
+                               "window kernel shared memory attribute");
+  if (st != NV_OK) return st;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((st = nv_cuda_check(cudaGetDevice(&dev), "current device")) != NV_OK) return st;
+  if ((st = nv_cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count")) != NV_OK)
+    return st;
+  if ((st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advdiff_window64_kernel<R>,
+                                                                        Sh::THREADS, Sh::SMEM),
+                          "occupancy query")) != NV_OK)
+    return st;
+  const int64_t work = (cols + 3) / 4;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
+  advdiff_window64_kernel<R><<<grid, Sh::THREADS, Sh::SMEM, s>>>(a, m1);
+  return nv_cuda_check(cudaGetLastError(), "advdiff_window64_kernel launch");
 }
 
 // Serial fine solve of the advection-diffusion system (one CTA, S*m steps).
@@ -637,10 +673,10 @@ nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s) {
     const int m1 = g_tune.adv_build_form == 1 ? 0 : (int)std::min<int64_t>(M->m, 3);
     M->work_per_slice = (int64_t)(M->dim + 1) * (1024 * m1 + (int64_t)M->dim * (M->m - m1));
     if (m1 > 0) {
-      snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_window64_kernel");
-      st = persistent_grid(advdiff_window64_kernel, 256, (cols + 3) / 4 * 8, &grid);
-      if (st != NV_OK) return st;
-      advdiff_window64_kernel<<<grid, 256, 0, s>>>(a, m1);
+      // strip height: 16 rows (256 threads) unless key 16 asks for 8 (512 threads)
+      const int R = g_tune.adv_fp64_rows == 8 ? 8 : 16;
+      snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_window64_kernel<%d>", R);
+      return R == 8 ? launch_adv_window64<8>(a, m1, cols, s) : launch_adv_window64<16>(a, m1, cols, s);
     } else {
       snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");
       st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);

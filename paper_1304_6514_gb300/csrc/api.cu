@@ -19,7 +19,7 @@ nv_status launch_serial_advdiff(const nv_maps* M, const double* y0, double* yT, 
 nv_status launch_serial_wave(const nv_maps* M, const double* y0, double* yT, cudaStream_t s);
 int64_t wave_aux_elems(int d);
 
-nv_tunables g_tune = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+nv_tunables g_tune = {};
 
 static thread_local char g_err[512] = "";
 
@@ -473,6 +473,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
     case 15:
       if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "advection-diffusion build form is 0 or 1");
       g_tune.adv_build_form = value;
+      break;
+    case 16:
+      if (value != 0 && value != 8 && value != 16) return nv_fail(NV_EINVAL, "strip height is 0 (16), 8 or 16");
+      g_tune.adv_fp64_rows = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);
   }

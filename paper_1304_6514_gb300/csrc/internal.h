@@ -146,7 +146,8 @@ struct nv_tunables {
   int test_withhold_defect;  // test hook: pipelined refinement never flags pass 1's defect of this slice + 1
   int test_skip_partials;    // test hook: the d > 512 ring chain's CTA 0 never stores step value - 1's partials
   int chain_dense;           // 1: the d <= 256 cluster chains read every column even of banded maps
-  int adv_build_form;        // advection-diffusion float32 build: 0 auto (windows first), 1 whole grid only
+  int adv_build_form;        // advection-diffusion build: 0 auto (windows first), 1 whole grid only
+  int adv_fp64_rows;         // float64 advection-diffusion window build: rows per thread, 0 (= 16) or 8
 };
 extern nv_tunables g_tune;
 
