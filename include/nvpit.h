@@ -484,10 +484,10 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          by default the first min(m, 3) steps run on 32 x 32 windows
  *          around each column's unit point (the rows those steps cannot
  *          reach are exactly zero), with the same maps bit for bit.
- *   key 16: 0 (default, = 16), 8 or 16: rows of the grid each thread holds in
- *          the float64 advection-diffusion window build (16: 256-thread CTAs,
- *          8: 512-thread CTAs with half the registers per thread); the same
- *          maps bit for bit.
+ *   key 16: 0 (default, = 16), 8, 16 or 32: rows of the grid each thread holds
+ *          in the float64 advection-diffusion window build (16: 256-thread
+ *          CTAs, 8: 512-thread CTAs, 32: 128-thread CTAs); the same maps bit
+ *          for bit.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
  * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15 and 16. */
 nv_status nv_tune_set(int32_t key, int32_t value);

@@ -674,8 +674,9 @@ nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s) {
     M->work_per_slice = (int64_t)(M->dim + 1) * (1024 * m1 + (int64_t)M->dim * (M->m - m1));
     if (m1 > 0) {
       // strip height: 16 rows (256 threads) unless key 16 asks for 8 (512 threads)
-      const int R = g_tune.adv_fp64_rows == 8 ? 8 : 16;
+      const int R = g_tune.adv_fp64_rows == 8 || g_tune.adv_fp64_rows == 32 ? g_tune.adv_fp64_rows : 16;
       snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_window64_kernel<%d>", R);
+      if (R == 32) return launch_adv_window64<32>(a, m1, cols, s);
       return R == 8 ? launch_adv_window64<8>(a, m1, cols, s) : launch_adv_window64<16>(a, m1, cols, s);
     } else {
       snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");

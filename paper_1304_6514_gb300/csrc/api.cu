@@ -475,7 +475,8 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       g_tune.adv_build_form = value;
       break;
     case 16:
-      if (value != 0 && value != 8 && value != 16) return nv_fail(NV_EINVAL, "strip height is 0 (16), 8 or 16");
+      if (value != 0 && value != 8 && value != 16 && value != 32)
+        return nv_fail(NV_EINVAL, "strip height is 0 (16), 8, 16 or 32");
       g_tune.adv_fp64_rows = value;
       break;
     default: return nv_fail(NV_EINVAL, "unknown tunable %d", key);

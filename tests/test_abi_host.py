@@ -130,7 +130,7 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(12, 0) == nvp.NV_OK
     assert lib.nv_tune_set(13, -1) == nvp.NV_EINVAL         # skipped step is >= 0
     assert lib.nv_tune_set(13, 0) == nvp.NV_OK
-    assert lib.nv_tune_set(16, 4) == nvp.NV_EINVAL          # strip height is 0, 8 or 16
+    assert lib.nv_tune_set(16, 4) == nvp.NV_EINVAL          # strip height is 0, 8, 16 or 32
     assert lib.nv_tune_set(16, 8) == nvp.NV_OK
     assert lib.nv_tune_set(16, 0) == nvp.NV_OK
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL

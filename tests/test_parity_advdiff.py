@@ -235,14 +235,14 @@ def test_ring_chain_bounded_wait_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("S,m", [(3, 10), (2, 2)])
 def test_advdiff_fp64_window_strip_heights_agree(S, m):
-    """The float64 window build with 8-row strips (512-thread CTAs, key 16 = 8)
-    and with 16-row strips (the default) computes every point with the same
-    expression: the maps agree bit for bit."""
+    """The float64 window build with 8-row strips (512-thread CTAs, key 16 = 8),
+    32-row strips (128-thread CTAs) and 16-row strips (the default) computes
+    every point with the same expression: the maps agree bit for bit."""
     torch = need_gpu()
     w = workloads.advdiff2d(S=S, T=S * m * 2e-4, dt=2e-4)
     r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
     got = {}
-    for rows in (16, 8):
+    for rows in (16, 8, 32):
         nvp.tune_set(16, rows)
         try:
             maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), nvp.steps("rk4", w.dt))
@@ -252,5 +252,5 @@ def test_advdiff_fp64_window_strip_heights_agree(S, m):
             maps.destroy()
         finally:
             nvp.tune_set(16, 0)
-    assert torch.equal(got[16], got[8])
+    assert torch.equal(got[16], got[8]) and torch.equal(got[16], got[32])
 
