@@ -488,8 +488,12 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          in the float64 advection-diffusion window build (16: 256-thread
  *          CTAs, 8: 512-thread CTAs, 32: 128-thread CTAs); the same maps bit
  *          for bit.
+ *   key 17: 0 (default, = 1), 1 or 2: lanes per column in the first of the
+ *          float32 heat build's three windows (22, 44, 88 rows): 1 lane of 22
+ *          rows (then 2 and 4), or 2 lanes of 11 rows (then 4 and 8, the
+ *          float64 shape); the same maps bit for bit.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15 and 16. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16 and 17. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Measured fused multiply-add throughput of the current device's float64

@@ -161,10 +161,12 @@ template <typename T, int G, int R>
 __device__ __forceinline__ void window_step(T (&y)[R], int gl, bool lo_end, bool hi_end, T c0, T c1, T c2,
                                             T c3, T c4) {
   T e[R + 8];                                       // rows w0+gl*R-4 .. w0+gl*R+R+3
+  if constexpr (G > 1) {                            // one lane per window: both ends are set below
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    e[k] = __shfl_up_sync(0xffffffffu, y[R - 4 + k], 1, G);
-    e[R + 4 + k] = __shfl_down_sync(0xffffffffu, y[k], 1, G);
+    for (int k = 0; k < 4; ++k) {
+      e[k] = __shfl_up_sync(0xffffffffu, y[R - 4 + k], 1, G);
+      e[R + 4 + k] = __shfl_down_sync(0xffffffffu, y[k], 1, G);
+    }
   }
   if (gl == 0) {                                    // rows w0-4..w0-1
     e[0] = lo_end ? -y[2] : (T)0;
@@ -195,13 +197,42 @@ __device__ __forceinline__ int window_origin(int c, int reach, int n, int W) {
   return min(max(c - 1 - reach, 0), n - W);
 }
 
+// Window staging in shared memory: a column's W = G*R rows contiguous, in
+// slots of G*(R+1) values per column (the same 32*(R+1) values per warp as a
+// lane-blocked column), so that a row's offset in its window is its index in
+// the slot.  Lane l = q*G + gl writes its rows gl*R .. gl*R+R-1 of column q at
+// l*(R+1) - gl.
+template <int G, int R>
+__device__ __forceinline__ int window_slot(int lane) {
+  return lane * (R + 1) - lane % G;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static constexpr int V = 4;
+  __device__ static void store(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec16<double> {
+  static constexpr int V = 2;
+  __device__ static void store(double* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
 // Write the windows of 32/G columns (w*CPW .. w*CPW+CPW-1 of the flattened
-// (slice, column) order), staged in buf as lane*(R+1)+i, as full columns of n
-// rows with zeros outside the windows; consecutive rows in consecutive lanes.
+// (slice, column) order), staged by window_slot, as full columns of n rows
+// with zeros outside the windows: 16-byte stores of consecutive rows by
+// consecutive lanes where the columns are 16-byte aligned (n a multiple of 4
+// floats or 2 doubles), else one row per lane and store.
 template <typename T, int G, int R, bool TF32OUT>
 __device__ __forceinline__ void store_windows(const T* buf, T* out, int64_t first, int64_t total, int n,
                                               int reach, int lane) {
-  constexpr int W = G * R, CPW = 32 / G;
+  constexpr int W = G * R, CPW = 32 / G, SW = G * (R + 1), V = Vec16<T>::V;
   const int cols = n + 1;
 #pragma unroll 1
   for (int g = 0; g < CPW; ++g) {
@@ -211,15 +242,25 @@ __device__ __forceinline__ void store_windows(const T* buf, T* out, int64_t firs
     const int cg = 1 + (int)(id - (int64_t)jg * n);
     const int v0 = window_origin(cg, reach, n, W);
     T* col = out + ((int64_t)jg * cols + cg) * n;
-    for (int r = lane; r < n; r += 32) {
-      const int o = r - v0;
-      T v = (T)0;
-      if (o >= 0 && o < W) {
-        const int src = o / R;
-        v = buf[(g * G + src) * (R + 1) + (o - src * R)];
+    const T* win = buf + g * SW;
+    if (n % V == 0) {
+      for (int r0 = lane * V; r0 < n; r0 += 32 * V) {
+        T v[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int o = r0 + q - v0;
+          v[q] = (unsigned)o < (unsigned)W ? win[o] : (T)0;
+          if constexpr (TF32OUT) v[q] = round_tf32(v[q]);
+        }
+        Vec16<T>::store(col + r0, v);
       }
-      if constexpr (TF32OUT) col[r] = round_tf32(v);
-      else col[r] = v;
+    } else {
+      for (int r = lane; r < n; r += 32) {
+        const int o = r - v0;
+        const T v = (unsigned)o < (unsigned)W ? win[o] : (T)0;
+        if constexpr (TF32OUT) col[r] = round_tf32(v);
+        else col[r] = v;
+      }
     }
   }
 }
@@ -264,7 +305,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
     for (int64_t step = 0; step < a.m; ++step) window_step<T, G, R>(y, gl, lo_end, hi_end, c0, c1, c2, c3, c4);
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[lane * (R + 1) + i] = y[i];
+    for (int i = 0; i < R; ++i) buf[window_slot<G, R>(lane) + i] = y[i];
     __syncwarp();
     store_windows<T, G, R, TF32OUT>(buf, out, w * CPW, total, n, reach, lane);
     __syncwarp();
@@ -309,7 +350,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
         window_step<T, GA, R>(y, gl, w0 == 0, w0 + WA == n, c0, c1, c2, c3, c4);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < R; ++i) narrow[lane * (R + 1) + i] = y[i];
+      for (int i = 0; i < R; ++i) narrow[window_slot<GA, R>(lane) + i] = y[i];
       __syncwarp();
     }
 #pragma unroll 1
@@ -327,8 +368,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
         const int o = wb + gl * R + i - wa;         // row's offset in the narrow window
         T v = (T)0;
         if (o >= 0 && o < WA) {
-          const int src = o / R;
-          v = narrow[(qa * GA + src) * (R + 1) + (o - src * R)];
+          v = narrow[qa * GA * (R + 1) + o];
         }
         y[i] = v;
       }
@@ -336,7 +376,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
         window_step<T, GB, R>(y, gl, wb == 0, wb + WB == n, c0, c1, c2, c3, c4);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < R; ++i) buf[lane * (R + 1) + i] = y[i];
+      for (int i = 0; i < R; ++i) buf[window_slot<GB, R>(lane) + i] = y[i];
       __syncwarp();
       store_windows<T, GB, R, TF32OUT>(buf, out, first, total, n, reach, lane);
       __syncwarp();
@@ -346,7 +386,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) * R <= 64) ? 4 : 2) heat_windo
 
 // Fill a wide window (origin wide0, G lanes of R rows, this lane's rows
 // gl*R ..) from a narrow window of slot `slot` staged by GN lanes per column
-// as lane*(R+1)+i (origin wn, WN rows); rows outside the narrow window are 0.
+// by window_slot (origin wn, WN rows); rows outside the narrow window are 0.
 template <typename T, int GN, int R>
 __device__ __forceinline__ void widen_window(T (&y)[R], const T* narrow, int slot, int wn, int WN, int wide0,
                                              int gl) {
@@ -355,8 +395,7 @@ __device__ __forceinline__ void widen_window(T (&y)[R], const T* narrow, int slo
     const int o = wide0 + gl * R + i - wn;
     T v = (T)0;
     if (o >= 0 && o < WN) {
-      const int src = o / R;
-      v = narrow[(slot * GN + src) * (R + 1) + (o - src * R)];
+      v = narrow[slot * GN * (R + 1) + o];
     }
     y[i] = v;
   }
@@ -373,7 +412,7 @@ template <typename T, int G1, int R, bool TF32OUT>
 __global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, int m2) {
   constexpr int G2 = 2 * G1, G3 = 4 * G1, W1 = G1 * R, W2 = G2 * R, W3 = G3 * R;
   constexpr int C1 = 32 / G1, C2 = 32 / G2, C3 = 32 / G3;
-  static_assert(R >= 4 && G1 >= 2 && 32 % G3 == 0, "R >= 4 rows per lane, 4*G1 lanes dividing the warp");
+  static_assert(R >= 4 && G1 >= 1 && 32 % G3 == 0, "R >= 4 rows per lane, 4*G1 lanes dividing the warp");
   __shared__ T slots[4][3][32 * (R + 1)];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* b1 = slots[warp][0];
@@ -403,7 +442,7 @@ __global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, i
         window_step<T, G1, R>(y, gl, w0 == 0, w0 + W1 == n, c0, c1, c2, c3, c4);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < R; ++i) b1[lane * (R + 1) + i] = y[i];
+      for (int i = 0; i < R; ++i) b1[window_slot<G1, R>(lane) + i] = y[i];
       __syncwarp();
     }
 #pragma unroll 1
@@ -420,7 +459,7 @@ __global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, i
           window_step<T, G2, R>(y, gl, wb == 0, wb + W2 == n, c0, c1, c2, c3, c4);
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < R; ++i) b2[lane * (R + 1) + i] = y[i];
+        for (int i = 0; i < R; ++i) b2[window_slot<G2, R>(lane) + i] = y[i];
         __syncwarp();
       }
 #pragma unroll 1
@@ -436,7 +475,7 @@ __global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, i
           window_step<T, G3, R>(y, gl, wc == 0, wc + W3 == n, c0, c1, c2, c3, c4);
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < R; ++i) stage[lane * (R + 1) + i] = y[i];
+        for (int i = 0; i < R; ++i) stage[window_slot<G3, R>(lane) + i] = y[i];
         __syncwarp();
         store_windows<T, G3, R, TF32OUT>(stage, out, first3, total, n, reach, lane);
         __syncwarp();
@@ -704,7 +743,10 @@ static void note_build(BuildInfo* bi, int64_t work, const char* fmt, ...) {
 
 static const int kWindow1[][2] = {{8, 4}, {8, 8}, {8, 11}, {16, 8}, {16, 11}, {32, 8}};
 static const int kWindow2[][2] = {{4, 11}, {8, 8}};
-static const int kWindow3[][2] = {{2, 11}};
+// three windows of 22, 44 and 88 rows: two lanes of 11 rows for the first
+// (float64), or one lane of 22 rows (float32, where the shuffles and the
+// window edges, not the arithmetic, set the pace); key 17 picks for float32
+static const int kWindow3[][2] = {{2, 11}, {1, 22}};
 
 template <typename T>
 static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form,
@@ -728,7 +770,8 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
     }
   }
   if (form == 0 || form == 5) {
-    for (int k = 0; k < 1; ++k) {
+    const int k3 = sizeof(T) == 4 && g_tune.heat_f32_lanes != 2 ? 1 : 0;
+    for (int k = k3; k <= k3; ++k) {
       const int W1 = kWindow3[k][0] * kWindow3[k][1], W2 = 2 * W1, W3 = 4 * W1;
       const int k1 = (W1 - 1) / 8, k2 = (W2 - 1) / 8;
       if (8 * a.m + 1 > W3 || W3 > a.n || k2 >= a.m || k1 < 1 || (W3 == a.n && form != 5)) continue;
@@ -742,8 +785,9 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
   else if (pick >= 6 && pick < 8)
     note_build(bi, best, "heat_window2_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow2[pick - 6][0],
                kWindow2[pick - 6][1], t32);
-  else if (pick == 8)
-    note_build(bi, best, "heat_window3_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow3[0][0], kWindow3[0][1], t32);
+  else if (pick >= 8)
+    note_build(bi, best, "heat_window3_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow3[pick - 8][0],
+               kWindow3[pick - 8][1], t32);
   switch (pick) {
     case 0: return launch_window_GR<T, 8, 4>(a, block, s, tf32out);
     case 1: return launch_window_GR<T, 8, 8>(a, block, s, tf32out);
@@ -754,6 +798,9 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
     case 6: return launch_window2<T, 4, 11>(a, m1, block, s, tf32out);
     case 7: return launch_window2<T, 8, 8>(a, m1, block, s, tf32out);
     case 8: return launch_window3<T, 2, 11>(a, m1, m2, s, tf32out);
+    case 9:
+      if constexpr (sizeof(T) == 4) return launch_window3<T, 1, 22>(a, m1, m2, s, tf32out);
+      break;
     default: break;
   }
   if (form >= 3)

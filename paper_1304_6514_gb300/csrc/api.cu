@@ -474,6 +474,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "advection-diffusion build form is 0 or 1");
       g_tune.adv_build_form = value;
       break;
+    case 17:
+      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "float32 heat window lanes are 0, 1 or 2");
+      g_tune.heat_f32_lanes = value;
+      break;
     case 16:
       if (value != 0 && value != 8 && value != 16 && value != 32)
         return nv_fail(NV_EINVAL, "strip height is 0 (16), 8, 16 or 32");

@@ -147,7 +147,8 @@ struct nv_tunables {
   int test_skip_partials;    // test hook: the d > 512 ring chain's CTA 0 never stores step value - 1's partials
   int chain_dense;           // 1: the d <= 256 cluster chains read every column even of banded maps
   int adv_build_form;        // advection-diffusion build: 0 auto (windows first), 1 whole grid only
-  int adv_fp64_rows;         // float64 advection-diffusion window build: rows per thread, 0 (= 16) or 8
+  int adv_fp64_rows;         // float64 advection-diffusion window build: rows per thread, 0 (= 16), 8 or 32
+  int heat_f32_lanes;        // float32 heat three-window build: 0 auto (= 1), 1: one lane of 22 rows, 2: two of 11
 };
 extern nv_tunables g_tune;
 

@@ -133,6 +133,9 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(16, 4) == nvp.NV_EINVAL          # strip height is 0, 8, 16 or 32
     assert lib.nv_tune_set(16, 8) == nvp.NV_OK
     assert lib.nv_tune_set(16, 0) == nvp.NV_OK
+    assert lib.nv_tune_set(17, 3) == nvp.NV_EINVAL          # float32 heat window lanes are 0, 1 or 2
+    assert lib.nv_tune_set(17, 2) == nvp.NV_OK
+    assert lib.nv_tune_set(17, 0) == nvp.NV_OK
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
     h = ctypes.c_void_p()
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL

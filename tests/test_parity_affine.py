@@ -111,6 +111,29 @@ def test_heat_window_matches_full_width(n, S, steps, form, prec):
     assert not np.any(A[:, outside])
 
 
+@pytest.mark.parametrize("n,S,steps", [(256, 1024, 10), (256, 6, 8), (200, 4, 9), (88, 3, 10)])
+def test_heat_f32_three_window_lane_shapes_agree(n, S, steps):
+    """The float32 three-window build runs its 22/44/88-row windows on 1/2/4
+    lanes of 22 rows (the default, key 17 = 1) or on 2/4/8 lanes of 11 rows
+    (key 17 = 2, the float64 shape): every row is the same expression on the
+    same values, so the maps and the composed states agree bit for bit."""
+    torch = need_gpu()
+    T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
+    w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
+    got = {}
+    for lanes in (1, 2):
+        nvp.tune_set(6, 5)
+        nvp.tune_set(17, lanes)
+        try:
+            _, A, b, yT, lam = _heat(torch, w, "fp32")
+        finally:
+            nvp.tune_set(6, 0)
+            nvp.tune_set(17, 0)
+        got[lanes] = (A, b, lam)
+    for k in range(3):
+        assert np.array_equal(got[1][k], got[2][k])
+
+
 @pytest.mark.parametrize("n,S,steps,rhs_name", [(256, 1024, 10, "heat1d"), (256, 7, 3, "heat1d"),
                                                 (128, 5, 2, "heat1d"), (64, 3, 1, "heat1d"),
                                                 (192, 6, 5, "heat1d"), (256, 4, 40, "heat1d"),
