@@ -1413,6 +1413,7 @@ def run_heat(args):
     flop_full = FLOP_PER_COMPONENT_STEP * units * w.dim
     achieved = flop / build_s
     fp64_rate = nvp.alu_rate("fp64", stream=stream)
+    fp32_rate = nvp.alu_rate("fp32", stream=stream)
 
     # ---- variants
     variants = {"fp64": {"ms_per_step": statistics.mean(res["step_ms"]),
@@ -1448,7 +1449,8 @@ def run_heat(args):
                        "compose_ms": statistics.mean(rv["compose_ms"]),
                        "traj_steps_per_s": units / (statistics.mean(rv["step_ms"]) * 1e-3),
                        "build_tflops": flop / bs / 1e12,
-                       "build_frac_of_fp32_nominal": flop / bs / FP32_PEAK_NOMINAL,
+                       "build_frac_of_measured_fp32": flop / bs / fp32_rate,
+                       "build_hbm_gbs": w.S * w.dim * (w.dim + 1) * (4 if prec != "fp64" else 8) / bs / 1e9,
                        "speedup_vs_fp64_plain": statistics.mean(res["step_ms"]) / statistics.mean(rv["step_ms"])}
         if seq is not None:
             variants[v]["sequential_passes"] = {

@@ -21,7 +21,8 @@
 // K-major A operand (128B-swizzled, 1024-byte atoms).  Each A_j is stored
 // column-major in HBM, which is exactly the K-major layout of the B operand;
 // TMA streams it in K-slabs of 32 (256 x 128 B boxes, SWIZZLE_128B) through a
-// two-stage mbarrier ring.  One thread issues tcgen05.mma (kind::tf32,
+// three-stage mbarrier ring (the most that fits beside the 128 KB A operand),
+// the next map's first slabs streaming in during the epilogue.  One thread issues tcgen05.mma (kind::tf32,
 // M=128, N=256, K=8) into a 128 x 256 float32 accumulator in tensor memory;
 // four warps read it back with tcgen05.ld and write the next A operand (or,
 // after the last slice, the block total to global memory).  Every mbarrier
@@ -44,10 +45,10 @@ constexpr int kN = 256;                 // UMMA N (padded d)
 constexpr int kSlab = 32;               // K per TMA box / swizzle atom (128 B of tf32)
 constexpr int kSlabBytesA = kRows * 128;
 constexpr int kSlabBytesB = kN * 128;
-constexpr int kStages = 2;
+constexpr int kStages = 3;                // 128 KB A operand + 96 KB of B stages: 225 KB
 constexpr int kMaxSlabs = 8;            // d <= 256
 constexpr int kSmemA = kMaxSlabs * kSlabBytesA;          // 128 KB
-constexpr int kSmemB = kStages * kSlabBytesB;            // 64 KB
+constexpr int kSmemB = kStages * kSlabBytesB;            // 96 KB
 constexpr int kSmemBytes = kSmemA + kSmemB + 128 + 1024; // + barriers + alignment slack
 
 struct ScanArgs {
@@ -116,18 +117,21 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t idesc = idesc_tf32(kRows, kN);
   const uint32_t aop_addr = smem_u32(aop), bst_addr = smem_u32(bst);
 
-  uint32_t fph[kStages] = {0, 0}, eph[kStages] = {0, 0}, dph = 0;
-  bool pending[kStages] = {false, false};
+  uint32_t fph[kStages] = {}, eph[kStages] = {}, dph = 0;
+  bool pending[kStages] = {};
   bool ok = true;
+  bool prefetched = false;                  // the first slabs of this step's map are already in flight
   for (int step = 0; step < len && !abort_flag; ++step) {
     const int j = j0 + len - 1 - step;      // suffix product: last slice of the block first
     if (tid == 0) {
       const int ns = a.nslabs;
-      for (int s = 0; s < min(kStages, ns); ++s) {
-        mbar_expect_tx(&full[s], kSlabBytesB);
-        tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j);
-        pending[s] = true;
-      }
+      if (!prefetched)
+        for (int s = 0; s < min(kStages, ns); ++s) {
+          mbar_expect_tx(&full[s], kSlabBytesB);
+          tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j);
+          pending[s] = true;
+        }
+      prefetched = false;
       for (int s = 0; s < ns && ok; ++s) {
         const int st = s % kStages;
         ok = mbar_wait(&full[st], fph[st]);
@@ -158,6 +162,17 @@ __global__ void __launch_bounds__(128, 1)
           const int st = s % kStages;
           ok = mbar_wait(&empty[st], eph[st]);
           eph[st] ^= 1;
+        }
+        // every MMA of this step has read its B slabs: the first slabs of the
+        // next map stream in while the epilogue turns the accumulator into
+        // the next A operand (stage s % kStages again takes slab s)
+        if (ok && step + 1 < len) {
+          for (int s = 0; s < min(kStages, ns); ++s) {
+            mbar_expect_tx(&full[s], kSlabBytesB);
+            tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j - 1);
+            pending[s] = true;
+          }
+          prefetched = true;
         }
       }
       if (!ok) abort_flag = 1;
