@@ -136,6 +136,10 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(17, 3) == nvp.NV_EINVAL          # float32 heat window lanes are 0, 1 or 2
     assert lib.nv_tune_set(17, 2) == nvp.NV_OK
     assert lib.nv_tune_set(17, 0) == nvp.NV_OK
+    assert lib.nv_alu_rate(0, None, None) == nvp.NV_EINVAL        # no output pointer
+    rate = ctypes.c_double(0.0)
+    assert lib.nv_alu_rate(3, ctypes.byref(rate), None) == nvp.NV_EINVAL   # float64 or float32 only
+    assert lib.nv_mlp_parareal(None, None, 0.0, 1.0, 4, None, 1, 128, None, None, None, None) == nvp.NV_EINVAL
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, None, None) == nvp.NV_EINVAL
     h = ctypes.c_void_p()
     assert lib.nv_build_propagators(None, 0.0, 1.0, 4, None, None, ctypes.byref(h), None) == nvp.NV_EINVAL

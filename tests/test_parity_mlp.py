@@ -312,3 +312,26 @@ def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error(
     # does the fine work k times to gain a parallelism the GPU already has.
     assert tp64 > t64 and tp32 > t32
 
+
+
+def test_parareal_rejects_bad_arguments_and_keeps_iteration_zero_exact():
+    """count must be a positive multiple of 128 and iters >= 0 (checked before
+    any launch); with iters = 0 the result is the learned composition of
+    nv_mlp_compose bit for bit, on 256 states of 3 slices."""
+    torch = need_gpu()
+    S, count = 3, 256
+    w = workloads.chain3(S=S, M=128, T=3 * 0.15625)
+    net = nvp.MLP(seed=8)
+    net.set_scales([0.6] * 6, [0.05] * 6)
+    r, st = nvp.rhs("chain3", 6), nvp.steps("rk4", w.dt)
+    y0 = torch.tensor(workloads.Stream(5).uniform(count * 6, -1.0, 1.0).reshape(count, 6), device="cuda")
+    yT, yc = torch.empty_like(y0), torch.empty_like(y0)
+    with pytest.raises(nvp.NvError):
+        net.parareal(r, w.t0, w.T, S, st, -1, y0, yT)
+    with pytest.raises(nvp.NvError):
+        net.parareal(r, w.t0, w.T, S, st, 1, y0[:100].contiguous(), yT[:100].contiguous())
+    net.parareal(r, w.t0, w.T, S, st, 0, y0, yT)
+    net.compose(r, w.t0, w.T, S, st, y0, yc)
+    torch.cuda.synchronize()
+    assert torch.equal(yT, yc)
+    net.destroy()
