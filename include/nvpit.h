@@ -479,11 +479,15 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          column of banded maps (those of the heat equations, zero off
  *          |r - c| <= 4m) instead of the band around each CTA's rows; the
  *          results are the same bit for bit.
- *   key 15: 0 (default) or 1: with 1 the float64 / float32 / bfloat16 advection-diffusion
- *          build integrates every column on the whole grid for all m steps;
- *          by default the first min(m, 3) steps run on 32 x 32 windows
- *          around each column's unit point (the rows those steps cannot
- *          reach are exactly zero), with the same maps bit for bit.
+ *   key 15: 0 (default), 1 or 2: with 1 the float64 / float32 / bfloat16
+ *          advection-diffusion build integrates every column on the whole grid
+ *          for all m steps; by default the first min(m, 3) steps run on
+ *          32 x 32 windows around each column's unit point (the points those
+ *          steps cannot reach are exactly zero), and the float64 build then
+ *          runs the next steps on the whole width but only the rows they can
+ *          reach (a ladder of 48-row windows for steps 4 and 5 at 16-row
+ *          strips; 40, 48, 56 rows for steps 4-6 at 8-row strips); 2 keeps
+ *          the 32 x 32 windows without the ladder.  The same maps bit for bit.
  *   key 16: 0 (default, = 16), 8, 16 or 32: rows of the grid each thread holds
  *          in the float64 advection-diffusion window build (16: 256-thread
  *          CTAs, 8: 512-thread CTAs, 32: 128-thread CTAs); the same maps bit

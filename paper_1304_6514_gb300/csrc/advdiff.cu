@@ -433,40 +433,60 @@ __global__ void __launch_bounds__(kAdvBlockThreads, 4) advdiff_window_kernel(Adv
 // The float64 build with the first steps on windows, in the strip layout of
 // advdiff_affine_kernel.  As in advdiff_window_kernel, after k steps the
 // column from the unit point (cx, cy) is exactly zero outside the periodic
-// diamond |x - cx| + |y - cy| <= 4k, so the first m1 <= 3 steps run on the
-// 32 x 32 window with origin (cx - 16, cy - 16) (mod 64): it holds the
-// radius-12 diamond, and its cut edges are at least 16 points from the centre,
-// where every stage that reads the halo (the first 4 m1 <= 12) reads the exact
-// zero.  Window phase: four columns per CTA, two warps each, warp 2g + s
-// holding rows 16 s .. 16 s + 15 of column g's window at window column
-// x = lane; x-neighbours by shuffles (zero at the window's side edges), the
-// strips' facing rows through the shared top / bottom rows (a zero slot at the
-// window's top and bottom edges).  Then each of the four columns runs the
-// remaining steps on the whole grid, in exactly advdiff_affine_kernel's layout,
-// from its window staged in shared memory (zeros elsewhere).  Every point is the
-// same floating-point expression as there, and the zeros are exact, so the
-// maps are bit for bit those of the whole-grid kernel; the point-steps per
-// column fall from 4096 m to 1024 m1 + 4096 (m - m1).
-// Strip height R (rows per thread): 16 (256 threads, two warps per window) or
-// 8 (512 threads, four warps per window; half the registers, twice the warps
-// per SM).  Thread t's top / bottom row slot is t in both phases: row block b
-// of the grid is threads 64 b .. 64 b + 63, window strip s of column g is warp
-// g (32/R) + s.  Shared memory (dynamic): two buffers of 64 NB + 1 top and
-// bottom rows (the last slot stays zero), the edge-lane strips of every warp,
-// the four 32 x 32 windows.
+// diamond |x - cx| + |y - cy| <= 4k.  A window of rows cy - a .. cy - a + H - 1
+// that holds the diamond after the last of its steps, k_e (a >= 4 k_e and
+// H - 1 - a >= 4 k_e), also has its cut halo rows at distance >= 4 k_e, where
+// every stage that reads them (the first 4 k_e) reads the exact zero; the
+// same holds in x.  So:
+//   phase 0  the first m1 <= 3 steps on the 32 x 32 window with origin
+//            (cx - 16, cy - 16) (mod 64), four columns per CTA, 32/R warps each
+//            (warp g (32/R) + s holds rows R s .. R s + R - 1 of column g's
+//            window at window column x = lane; x-neighbours by shuffles, zero at
+//            the window's side edges; the strips' facing rows through the
+//            shared top / bottom rows, a zero slot at the window's top and
+//            bottom edges);
+//   ladder   then, column by column, each step i on the whole periodic width
+//            but only the H(i) rows around cy, H(i) the least multiple of R
+//            holding 8 (i + 1) + 1 rows (R = 8: 40, 48, 56 rows for steps 4, 5,
+//            6; R = 16: 48 rows for steps 4 and 5), a = H/2, the strips of
+//            the window active and the others idle (warp-uniform);
+//   full     the remaining steps on the whole grid, in exactly
+//            advdiff_affine_kernel's layout.
+// Each phase starts from the previous one's window staged in shared memory
+// (the 32 x 32 windows, or a 64 x 64 grid buffer), zeros outside it.  Every
+// point is the same floating-point expression as in the whole-grid kernel, and
+// the zeros are exact, so the maps are bit for bit the same; the point-steps
+// per column fall from 4096 m to 1024 m1 + 64 (H(m1) + ... ) for the ladder
+// steps + 4096 for each full step.
+// Strip height R (rows per thread): 16 (256 threads), 8 (512) or 32 (128).
+// Thread t's top / bottom row slot is t in every phase: row block b is threads
+// 64 b .. 64 b + 63, window strip s of column g is warp g (32/R) + s.  Shared
+// memory (dynamic): two buffers of 64 NB + 1 top and bottom rows (the last slot
+// stays zero), the edge-lane strips of every warp, the four 32 x 32 windows,
+// the 64 x 64 grid buffer of the ladder.
 template <int R>
 struct AdvWin64Shape {
   static constexpr int NB = kAdvNx / R;               // row blocks of the grid
-  static constexpr int THREADS = kAdvNx * NB;         // 256 or 512
+  static constexpr int THREADS = kAdvNx * NB;         // 256, 512 or 128
   static constexpr int NW = THREADS / 32;
   static constexpr int WPC = 32 / R;                  // warps per window
   static constexpr int ROWS = kAdvNx * NB + 1;        // row slots per buffer, zero slot last
-  static constexpr size_t SMEM =
-      sizeof(double) * (2 * 2 * (size_t)ROWS + 2 * (size_t)NW * 2 * R + 4 * 32 * 32);
+  static constexpr size_t SMEM = sizeof(double) * (2 * 2 * (size_t)ROWS + 2 * (size_t)NW * 2 * R +
+                                                   4 * 32 * 32 + (size_t)kAdvNx * kAdvNx);
 };
 
+// Rows of the ladder window of step i (0-based): the least multiple of R
+// holding 8 (i + 1) + 1 rows, at most the whole grid (host and device).
 template <int R>
-__global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_kernel(AdvArgs a, int m1) {
+__host__ __device__ __forceinline__ int adv_ladder_rows(int64_t i) {
+  const int64_t need = 8 * (i + 1) + 1;
+  const int64_t h = (need + R - 1) / R * R;
+  return h >= kAdvNx ? kAdvNx : (int)h;
+}
+
+template <int R>
+__global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_kernel(AdvArgs a, int m1,
+                                                                                     int ladder) {
   using Sh = AdvWin64Shape<R>;
   constexpr int n = kAdvNx * kAdvNx;
   constexpr int NB = Sh::NB, WPC = Sh::WPC, ROWS = Sh::ROWS, RING = kAdvNx * NB;
@@ -476,8 +496,9 @@ __global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_ke
   double* bot = top + 2 * ROWS;                // [2][ROWS]
   double* edge = bot + 2 * ROWS;               // [2][NW][2][R]
   double* win = edge + 2 * Sh::NW * 2 * R;     // [4][32][32]
+  double* grid = win + 4 * 32 * 32;            // [64][64], the ladder's staging
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ix = tid % kAdvNx, blk = tid / kAdvNx, iy0 = blk * R;   // whole-grid strip layout
+  const int ix = tid % kAdvNx, blk = tid / kAdvNx;                   // grid strip layout
   const int g = warp / WPC, s = warp % WPC;                          // window layout
   const int pw = warp ^ 1;
   if (tid < 2) {
@@ -488,21 +509,32 @@ __global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_ke
   const int64_t total = (int64_t)a.S * (n + 1);
   int buf = 0;
   for (int64_t w = blockIdx.x; w * 4 < total; w += gridDim.x) {
+    // One loop over the group's phases, so that the unrolled step body appears
+    // once: gc = -1 is phase 0 (the four 32 x 32 windows), then each column gc
+    // runs its ladder phases and its whole-grid phase.
+    int gc = -1, sy = 0, sh = 0;       // sh = 0: the previous window is the column's 32 x 32 one
+    int64_t i = 0;
 #pragma unroll 1
-    for (int seg = 0; seg <= 4; ++seg) {       // 0: the windows; s >= 1: column s - 1 on the whole grid
-      const bool windows = seg == 0;
-      const int64_t idx = w * 4 + (windows ? g : seg - 1);
-      if (!windows && idx >= total) break;     // uniform over the CTA
+    for (;;) {
+      const bool p0 = gc < 0;
+      const int64_t idx = w * 4 + (p0 ? g : gc);
+      if (!p0 && idx >= total) break;  // uniform over the CTA
       const int j = idx < total ? (int)(idx / (n + 1)) : 0;
       const int c = idx < total ? (int)(idx - (int64_t)j * (n + 1)) : 0;   // 0: no unit point
       const int cx = c >= 1 ? (c - 1) % kAdvNx : 0, cy = c >= 1 ? (c - 1) / kAdvNx : 0;
       const int wx0 = (cx + kAdvNx - 16) % kAdvNx, wy0 = (cy + kAdvNx - 16) % kAdvNx;
-      // the row above (a bottom row) and the row below (a top row); own slot = tid
-      int abv, blw;
-      double y[R], v[R];
-      if (windows) {
-        abv = s > 0 ? tid - 32 : kZ;           // the window strip above, or the window's top edge
-        blw = s < WPC - 1 ? tid + 32 : kZ;     // the window strip below, or its bottom edge
+      int H, wy, abv, blw;
+      int64_t count;
+      bool active, cut_x;
+      double y[R];
+      if (p0) {
+        H = 32;
+        wy = wy0;
+        count = m1;
+        active = true;
+        cut_x = true;
+        abv = s > 0 ? tid - 32 : kZ;
+        blw = s < WPC - 1 ? tid + 32 : kZ;
         const int gx = (wx0 + lane) % kAdvNx;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -510,17 +542,33 @@ __global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_ke
           y[r] = (c >= 1 && gy * kAdvNx + gx == c - 1) ? 1.0 : 0.0;
         }
       } else {
-        abv = (tid + RING - kAdvNx) % RING;    // periodic in y
-        blw = (tid + kAdvNx) % RING;
-        const int wx = (ix - wx0 + kAdvNx) % kAdvNx;
+        H = (ladder && i < a.m) ? adv_ladder_rows<R>(i) : kAdvNx;
+        int64_t iend = i;
+        while (iend < a.m && (ladder ? adv_ladder_rows<R>(iend) : kAdvNx) == H) ++iend;
+        count = iend - i;
+        i = iend;
+        const bool full = H == kAdvNx;
+        wy = full ? 0 : (cy - H / 2 + kAdvNx) % kAdvNx;
+        const int strips = H / R;
+        active = blk < strips;
+        cut_x = false;
+        abv = full ? (tid + RING - kAdvNx) % RING : (blk > 0 ? tid - kAdvNx : kZ);
+        blw = full ? (tid + kAdvNx) % RING : (blk < strips - 1 ? tid + kAdvNx : kZ);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const int wy = (iy0 + r - wy0 + kAdvNx) % kAdvNx;
-          y[r] = (wx < 32 && wy < 32) ? win[((seg - 1) * 32 + wy) * 32 + wx] : 0.0;
+          const int gy = (wy + R * blk + r) % kAdvNx;
+          double v = 0.0;
+          if (sh == 0) {
+            const int wx = (ix - wx0 + kAdvNx) % kAdvNx, wyy = (gy - wy0 + kAdvNx) % kAdvNx;
+            if (wx < 32 && wyy < 32) v = win[(gc * 32 + wyy) * 32 + wx];
+          } else if ((gy - sy + kAdvNx) % kAdvNx < sh) {
+            v = grid[gy * kAdvNx + ix];
+          }
+          y[r] = v;
         }
       }
-      const int64_t i1 = windows ? m1 : a.m;
-      for (int64_t i = windows ? 0 : m1; i < i1; ++i) {
+      for (int64_t it = 0; it < count; ++it) {
+        double v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = y[r];
 #pragma unroll
@@ -537,37 +585,56 @@ __global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_ke
             for (int r = 0; r < R; ++r) edgeb[(warp * 2 + (lane == 31)) * R + r] = v[r];
           }
           __syncthreads();
-          const double above = botb[abv], below = topb[blw];
-          double nv[R];
+          if (active) {                          // uniform over each warp
+            const double above = botb[abv], below = topb[blw];
+            double nv[R];
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            double xm = __shfl_up_sync(0xffffffffu, v[r], 1);
-            double xp = __shfl_down_sync(0xffffffffu, v[r], 1);
-            if (lane == 0) xm = windows ? 0.0 : edgeb[(pw * 2 + 1) * R + r];
-            if (lane == 31) xp = windows ? 0.0 : edgeb[(pw * 2 + 0) * R + r];
-            const double ym = r == 0 ? above : v[r - 1];
-            const double yp = r == R - 1 ? below : v[r + 1];
-            double acc = fma(c0, v[r], y[r]);
-            acc = fma(cxm, xm, acc);
-            acc = fma(cxp, xp, acc);
-            acc = fma(cym, ym, acc);
-            nv[r] = fma(cyp, yp, acc);
+            for (int r = 0; r < R; ++r) {
+              double xm = __shfl_up_sync(0xffffffffu, v[r], 1);
+              double xp = __shfl_down_sync(0xffffffffu, v[r], 1);
+              if (lane == 0) xm = cut_x ? 0.0 : edgeb[(pw * 2 + 1) * R + r];
+              if (lane == 31) xp = cut_x ? 0.0 : edgeb[(pw * 2 + 0) * R + r];
+              const double ym = r == 0 ? above : v[r - 1];
+              const double yp = r == R - 1 ? below : v[r + 1];
+              double acc = fma(c0, v[r], y[r]);
+              acc = fma(cxm, xm, acc);
+              acc = fma(cxp, xp, acc);
+              acc = fma(cym, ym, acc);
+              nv[r] = fma(cyp, yp, acc);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = nv[r];
           }
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[r] = nv[r];
           buf ^= 1;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) y[r] = v[r];
       }
-      if (windows) {
+      if (p0) {
 #pragma unroll
         for (int r = 0; r < R; ++r) win[(g * 32 + R * s + r) * 32 + lane] = y[r];
         __syncthreads();
-      } else {
+        gc = 0;
+        i = m1;
+        sh = 0;
+      } else if (H == kAdvNx) {
         double* col = out + ((int64_t)j * (n + 1) + c) * n;
 #pragma unroll
-        for (int r = 0; r < R; ++r) col[(iy0 + r) * kAdvNx + ix] = y[r];
+        for (int r = 0; r < R; ++r) col[(R * blk + r) * kAdvNx + ix] = y[r];
+        ++gc;
+        if (gc == 4) break;
+        i = m1;
+        sh = 0;
+      } else {
+        // every thread loaded the previous window before this phase's first
+        // block barrier (a ladder phase has at least one step)
+        if (active) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) grid[((wy + R * blk + r) % kAdvNx) * kAdvNx + ix] = y[r];
+        }
+        __syncthreads();
+        sy = wy;
+        sh = H;
       }
     }
     __syncthreads();                           // the windows are rewritten next
@@ -575,7 +642,7 @@ __global__ void __launch_bounds__(AdvWin64Shape<R>::THREADS) advdiff_window64_ke
 }
 
 template <int R>
-static nv_status launch_adv_window64(const AdvArgs& a, int m1, int64_t cols, cudaStream_t s) {
+static nv_status launch_adv_window64(const AdvArgs& a, int m1, int ladder, int64_t cols, cudaStream_t s) {
   using Sh = AdvWin64Shape<R>;
   nv_status st = nv_cuda_check(cudaFuncSetAttribute(advdiff_window64_kernel<R>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM),
@@ -591,7 +658,7 @@ static nv_status launch_adv_window64(const AdvArgs& a, int m1, int64_t cols, cud
     return st;
   const int64_t work = (cols + 3) / 4;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)sms * std::max(per_sm, 1)));
-  advdiff_window64_kernel<R><<<grid, Sh::THREADS, Sh::SMEM, s>>>(a, m1);
+  advdiff_window64_kernel<R><<<grid, Sh::THREADS, Sh::SMEM, s>>>(a, m1, ladder);
   return nv_cuda_check(cudaGetLastError(), "advdiff_window64_kernel launch");
 }
 
@@ -671,14 +738,23 @@ nv_status launch_advdiff_build(nv_maps* M, cudaStream_t s) {
   if (M->prec == NV_FP64) {
     // windows for the first min(m, 3) steps unless the whole-grid form is asked for
     const int m1 = g_tune.adv_build_form == 1 ? 0 : (int)std::min<int64_t>(M->m, 3);
-    M->work_per_slice = (int64_t)(M->dim + 1) * (1024 * m1 + (int64_t)M->dim * (M->m - m1));
     if (m1 > 0) {
-      // strip height: 16 rows (256 threads) unless key 16 asks for 8 (512 threads)
+      // strip height: 16 rows (256 threads) unless key 16 asks for 8 or 32;
+      // the ladder of row windows after the first steps unless key 15 = 2
       const int R = g_tune.adv_fp64_rows == 8 || g_tune.adv_fp64_rows == 32 ? g_tune.adv_fp64_rows : 16;
+      const int ladder = g_tune.adv_build_form == 2 ? 0 : 1;
+      int64_t per_col = 1024 * (int64_t)m1;
+      for (int64_t i = m1; i < M->m; ++i) {
+        const int H = !ladder ? kAdvNx : R == 8 ? adv_ladder_rows<8>(i) : R == 16 ? adv_ladder_rows<16>(i)
+                                                                            : adv_ladder_rows<32>(i);
+        per_col += (int64_t)kAdvNx * H;
+      }
+      M->work_per_slice = (int64_t)(M->dim + 1) * per_col;
       snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_window64_kernel<%d>", R);
-      if (R == 32) return launch_adv_window64<32>(a, m1, cols, s);
-      return R == 8 ? launch_adv_window64<8>(a, m1, cols, s) : launch_adv_window64<16>(a, m1, cols, s);
+      if (R == 32) return launch_adv_window64<32>(a, m1, ladder, cols, s);
+      return R == 8 ? launch_adv_window64<8>(a, m1, ladder, cols, s) : launch_adv_window64<16>(a, m1, ladder, cols, s);
     } else {
+      M->work_per_slice = (int64_t)(M->dim + 1) * M->dim * M->m;
       snprintf(M->build_kernel, sizeof(M->build_kernel), "advdiff_affine_kernel<double>");
       st = persistent_grid(advdiff_affine_kernel<double>, 256, cols * 8, &grid);
       if (st != NV_OK) return st;

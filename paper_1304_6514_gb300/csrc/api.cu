@@ -471,7 +471,7 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       g_tune.chain_dense = value;
       break;
     case 15:
-      if (value < 0 || value > 1) return nv_fail(NV_EINVAL, "advection-diffusion build form is 0 or 1");
+      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "advection-diffusion build form is 0, 1 or 2");
       g_tune.adv_build_form = value;
       break;
     case 17:

@@ -116,7 +116,8 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(9, -1) == nvp.NV_EINVAL
     assert lib.nv_tune_set(9, 1) == nvp.NV_OK
     assert lib.nv_tune_set(9, 0) == nvp.NV_OK
-    assert lib.nv_tune_set(15, 2) == nvp.NV_EINVAL          # advection-diffusion build form is 0 or 1
+    assert lib.nv_tune_set(15, 3) == nvp.NV_EINVAL          # advection-diffusion build form is 0, 1 or 2
+    assert lib.nv_tune_set(15, 2) == nvp.NV_OK
     assert lib.nv_tune_set(15, 1) == nvp.NV_OK
     assert lib.nv_tune_set(15, 0) == nvp.NV_OK
     assert lib.nv_tune_set(14, 2) == nvp.NV_EINVAL          # chain band use is 0 or 1

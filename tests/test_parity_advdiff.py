@@ -233,24 +233,31 @@ def test_ring_chain_bounded_wait_reports_timeout_and_context_survives():
         maps.destroy()
 
 
-@pytest.mark.parametrize("S,m", [(3, 10), (2, 2)])
+@pytest.mark.parametrize("S,m", [(3, 10), (2, 2), (2, 4), (3, 5), (2, 6), (2, 7)])
 def test_advdiff_fp64_window_strip_heights_agree(S, m):
-    """The float64 window build with 8-row strips (512-thread CTAs, key 16 = 8),
-    32-row strips (128-thread CTAs) and 16-row strips (the default) computes
-    every point with the same expression: the maps agree bit for bit."""
+    """The float64 window build with 8-, 16- and 32-row strips (key 16; 512,
+    256 and 128 threads per CTA), with the ladder of row windows after the
+    first three steps (key 15 = 0: 40, 48, 56 rows for steps 4-6 at 8-row
+    strips, 48 rows for steps 4-5 at 16) and without it (key 15 = 2), computes
+    every point with the same expression as the whole-grid kernel (key 15 = 1):
+    the maps agree bit for bit, for m covering partial and whole ladders."""
     torch = need_gpu()
     w = workloads.advdiff2d(S=S, T=S * m * 2e-4, dt=2e-4)
     r = nvp.rhs("advdiff2d", w.dim, w.params[:3])
     got = {}
-    for rows in (16, 8, 32):
+    for rows, form in ((16, 1), (8, 0), (16, 0), (32, 0), (8, 2), (16, 2)):
         nvp.tune_set(16, rows)
+        nvp.tune_set(15, form)
         try:
             maps = nvp.build_propagators(r, w.t0, w.T, w.S, nvp.samples("affine"), nvp.steps("rk4", w.dt))
             nvp.maps_check(maps)
-            assert nvp.maps_info(maps).build_kernel.decode() == f"advdiff_window64_kernel<{rows}>"
-            got[rows] = nvp.maps_slice(maps, 0, w.S).cpu()
+            name = nvp.maps_info(maps).build_kernel.decode()
+            assert name == (f"advdiff_window64_kernel<{rows}>" if form != 1 else "advdiff_affine_kernel<double>")
+            got[(rows, form)] = nvp.maps_slice(maps, 0, w.S).cpu()
             maps.destroy()
         finally:
             nvp.tune_set(16, 0)
-    assert torch.equal(got[16], got[8]) and torch.equal(got[16], got[32])
-
+            nvp.tune_set(15, 0)
+    ref = got[(16, 1)]
+    for key, val in got.items():
+        assert torch.equal(val, ref), key
