@@ -408,7 +408,7 @@ def gpu_peak_probe(torch):
 #   chain pairs, the full launch: 341.2 MB for 402 653 184 pair bytes
 #   wave FP64 build, full size: 42.78 MB for 81 408 columns (maps fit in L2)
 #   advection-diffusion FP32 chain, S = 8: 547.9 MB for 8 slice maps (537.0 MB read once)
-#   advection-diffusion FP64 build with windows, the full launch: 68.964 GB for 2 097 664 columns
+#   advection-diffusion FP64 build (windows + row ladder), the full launch: 69.293 GB for 2 097 664 columns
 NCU_TRAFFIC_PER_UNIT = {
     "affine_chain_tile_kernel<float,float>": (547.89e6 / 8, "profiles/advdiff_chains_d4096_S512.md"),
     "wave_build_kernel<double,80,2>": (42.78e6 / 81408, "profiles/wave_leapfrog_build_M80_S512.md"),
@@ -417,7 +417,7 @@ NCU_TRAFFIC_PER_UNIT = {
     "heat_window3_kernel<double,2,11,0>": (475.15e6 / 262144, "profiles/heat_affine_build_and_chain_n256_S1024.md"),
     "advdiff_block_kernel<float>": (475.04e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
     "advdiff_window_kernel<float>": (475.46e6 / 32776, "profiles/advdiff_fp32_block_build_64x64.md"),
-    "advdiff_window64_kernel<16>": (68.964e9 / (512 * 4097), "profiles/advdiff_fp64_window_build_d4096_S512.md"),
+    "advdiff_window64_kernel<16>": (69.293e9 / (512 * 4097), "profiles/advdiff_fp64_window_build_d4096_S512.md"),
     "batch_build_kernel<RhsVdp<float>,float,4,1>": (503.0e6 / 561987584, "profiles/vdp_batch_build_4096_instances.md"),
     "pairs_kernel<float>": (341.2e6 / 402653184, "profiles/chain3_pairs_build_S128_M65536.md"),
 }
@@ -919,8 +919,9 @@ def run_advdiff(args):
                      "flop_per_unit": "40 per point-step: the Horner-form RK4 step, 4 stages x 5 DFMA, "
                                       "the float64 instructions the kernel executes",
                      "points_note": ("the build integrates each column's first min(m, 3) steps on a 32 x 32 "
-                                     "window around its unit point (exactly zero outside), the rest on the "
-                                     "64 x 64 grid; the FLOPs count the points integrated"),
+                                     "window around its unit point and the next two on the 48 rows they can "
+                                     "reach (exactly zero outside), the rest on the 64 x 64 grid; the FLOPs "
+                                     "count the points integrated"),
                      "full_grid_equivalent_tflops": FLOP_PER_ADV_COMPONENT_STEP * units * w.dim / build_s / 1e12,
                      "survey_unit_tflops": SURVEY_FLOP_PER_ADV_COMPONENT_STEP * point_steps / build_s / 1e12,
                      "survey_unit_note": "68 FLOP per point-step (the four literal stages), for comparison",
