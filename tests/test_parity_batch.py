@@ -131,3 +131,26 @@ def test_full_batch_sampled_instances():
     assert oob >= extrapolated
     assert np.all(np.isfinite(yT))
     b.destroy()
+
+
+def test_full_batch_float64_checked_instances():
+    """The same 4096 instances with float64 tables (the float64 method on the
+    batch): every table entry and the final state of the checked instances
+    within the float64 tolerance, and the float32 batch's final states within
+    1e-4 of these over all 4096 instances (its table rounding, amplified by
+    up to 256 bilinear lookups)."""
+    torch = need_gpu()
+    vb = workloads.vdp_batch()
+    P = vb.per_dim
+    b, tabs, yT, oob = _run_batch(torch, vb.mu, vb.T, vb.S, vb.y0, P, vb.dt, "fp64")
+    parts_off = np.concatenate([[0], np.cumsum(vb.S.astype(np.int64) * P * P * 2)])
+    for i in full_batch_check_instances(vb):
+        otab, oy, _ = _oracle_instance(vb.mu[i], vb.T[i], vb.S[i], vb.y0[i], P, vb.dt)
+        g = tabs[parts_off[i]:parts_off[i + 1]].reshape(int(vb.S[i]), P, P, 2).transpose(0, 2, 1, 3)
+        assert rel_max(g, otab) <= 1e-11, i
+        assert rel_max(yT[i], oy) <= 1e-11, (i, rel_max(yT[i], oy))
+    b.destroy()
+    b32, _, y32, _ = _run_batch(torch, vb.mu, vb.T, vb.S, vb.y0, P, vb.dt, "fp32")
+    err = np.linalg.norm(y32 - yT, axis=1) / np.linalg.norm(yT, axis=1)
+    assert err.max() <= 1e-4, err.max()
+    b32.destroy()
