@@ -366,7 +366,8 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  *                                           every slice and state at once
  *   e_0 = 0, e_{j+1} = J_j e_j + d_j        J_j the network's tangent map at
  *                                           lambda_j (a forward-mode derivative
- *                                           through the same bf16 layers)
+ *                                           through its layers, float32, each
+ *                                           state's chain in one launch)
  *   lambda_{j+1} <- lambda_{j+1} + e_{j+1}  written by the chain as it goes
  * i.e. an approximate Newton step on the multiple-shooting equations
  * lambda_{j+1} = F_j(lambda_j), with the learned Jacobian in place of F_j's.
@@ -378,10 +379,15 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  *   y0_dev       count x 6 doubles (input); yT_dev count x 6 (output)
  *   lambdas_dev  (S+1) x count x 6 doubles (output, may be NULL): every
  *                boundary state of the last iterate
- * Scratch of (S + 1) count 6 doubles (+ the boundary states when lambdas_dev is
- * NULL) comes from the stream-ordered allocator on `stream`.  NV_EINVAL for a
- * bad count or iters < 0; NV_ENOTSUP for a right-hand side other than the
- * 3-mass chain. */
+ * steps->prec must be NV_FP64.  The network owns the boundary states and
+ * defects ((2 S + 1) count 6 doubles): the first call for a (count, S)
+ * synchronises `stream` and allocates them, and the first call for a schedule
+ * (count, S, iters, steps, rhs parameters) captures the whole schedule into a
+ * CUDA graph, later calls replay it (at small counts the learned composition's
+ * kernels are launch-bound when issued one by one); make those first calls
+ * outside any stream capture.  Calls on one network must not overlap.  NV_EINVAL for a bad
+ * count, iters < 0 or another precision; NV_ENOTSUP for a right-hand side other
+ * than the 3-mass chain. */
 nv_status nv_mlp_parareal(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, int32_t S,
                           const nv_steps* steps, int32_t iters, int64_t count, const double* y0_dev,
                           double* yT_dev, double* lambdas_dev, void* stream);
