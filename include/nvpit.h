@@ -360,8 +360,11 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
 /* The learned map as the coarse propagator of a float64 residual correction
  * (the combination with parareal the Conclusion proposes), for nonlinear
  * problems.  Iteration 0 is the learned composition
- * lambda_{j+1} = G_j(lambda_j), G_j(y) = y + sd*MLP(y/sx, j/S), bit for bit
- * that of nv_mlp_compose without fallback.  Iteration k >= 1:
+ * lambda_{j+1} = G_j(lambda_j), G_j(y) = y + sd*MLP(y/sx, j/S): by default,
+ * while count <= 16 x (SMs / 2), every state's chain in one launch with
+ * float32 activations (the network's bf16 weights), else, or with
+ * nv_tune_set key 18 = 1, slice by slice through nv_mlp_compose's path
+ * (bf16 activations between the layers), then bit for bit its states.  Iteration k >= 1:
  *   d_j = F_j(lambda_j) - lambda_{j+1}      float64 fine solve per slice, for
  *                                           every slice and state at once
  *   e_0 = 0, e_{j+1} = J_j e_j + d_j        J_j the network's tangent map at
@@ -502,8 +505,15 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          float32 heat build's three windows (22, 44, 88 rows): 1 lane of 22
  *          rows (then 2 and 4), or 2 lanes of 11 rows (then 4 and 8, the
  *          float64 shape); the same maps bit for bit.
+ *   key 18: 0 (default), 1 or 2: iteration 0 of nv_mlp_parareal: 0 the
+ *          fused one-launch sweep while count <= 16 x (SMs / 2), else the
+ *          per-slice path of nv_mlp_compose; 1 always that per-slice path;
+ *          2 always the sweep.  The two differ in the rounding of the
+ *          network's activations (bf16 between layers on the per-slice path,
+ *          float32 in the sweep); the corrected iterates converge to the same
+ *          float64 fine solution either way.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16 and 17. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17 and 18. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Measured fused multiply-add throughput of the current device's float64

@@ -478,6 +478,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "float32 heat window lanes are 0, 1 or 2");
       g_tune.heat_f32_lanes = value;
       break;
+    case 18:
+      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "learned iteration-0 form is 0, 1 or 2");
+      g_tune.learned_first_form = value;
+      break;
     case 16:
       if (value != 0 && value != 8 && value != 16 && value != 32)
         return nv_fail(NV_EINVAL, "strip height is 0 (16), 8, 16 or 32");

@@ -149,6 +149,7 @@ struct nv_tunables {
   int adv_build_form;        // advection-diffusion build: 0 auto (windows first), 1 whole grid only
   int adv_fp64_rows;         // float64 advection-diffusion window build: rows per thread, 0 (= 16), 8 or 32
   int heat_f32_lanes;        // float32 heat three-window build: 0 auto (= 1), 1: one lane of 22 rows, 2: two of 11
+  int learned_first_form;    // iteration 0 of nv_mlp_parareal: 0 auto, 1 per-slice tcgen05 forward, 2 fused sweep
 };
 extern nv_tunables g_tune;
 

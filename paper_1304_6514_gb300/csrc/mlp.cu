@@ -14,6 +14,7 @@
 // Parameter vector (float32, [out][in] weights):
 //   W1 256x8 (column 7 zero) | b1 256 | W2 256x256 | b2 256 | W3 256x256 | b3 256
 //   | W4 8x256 (rows 6, 7 zero) | b4 8
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -128,36 +129,67 @@ __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, 
   for (int c = 0; c < R::D; ++c) dfc[idx * R::D + c] = s[c] - lam[(idx + count) * R::D + c];
 }
 
-// The correction chain runs over the network's tangent map: e_0 = 0,
-// e_{j+1} = J_j e_j + d_j, lambda_{j+1} <- lambda_{j+1} + e_{j+1}, J_j the
-// Jacobian of G_j(y) = y + sd * MLP(y / sx, j / S) at lambda_j.  The chain of
-// each state is sequential in the slices but independent of every other
-// state's, so one launch carries NS states per CTA through all S slices, no
-// grid-wide step: per slice the forward pass at lambda_j (for GELU' of each
-// hidden layer) and the tangent of (e_j / sx, 0) go through the layers
-// together, thread t holding hidden unit t, each weight of W2 and W3 read
-// once (the bf16 transposed copies, coalesced) and applied to the NS states'
-// activations and tangents.  float32 arithmetic: the tangent only steers the
-// correction, whose fixed point the float64 defects set.
-template <int NS>
-__global__ void __launch_bounds__(256) tangent_sweep_kernel(const float* P, const __nv_bfloat16* W2t,
-                                                            const __nv_bfloat16* W3t, const float* sx_inv,
-                                                            const double* sd, int S, int64_t count, double* lam,
-                                                            const double* dfc) {
+// The learned composition and the correction chain, every state's chain in
+// one launch.  Both are sequential in the slices but independent from state
+// to state, so one launch carries all states through all S slices with no
+// grid-wide step.  A cluster of two CTAs takes NS states: CTA r owns hidden
+// units 128 r .. 128 r + 127 (thread t unit 128 r + t) and keeps its halves of
+// the bf16 layer-2 and layer-3 weights (W2^T and W3^T columns, 2 x 64 KB) in
+// shared memory for the whole launch; each layer's outputs go to both CTAs'
+// activation buffers (the partner's through distributed shared memory), one
+// cluster barrier per layer.  float32 activations and accumulation.
+//   TANGENT = false: lambda_{j+1} = G_j(lambda_j) = lambda_j + sd * MLP(lambda_j / sx, j / S)
+//                    (lambda_0 given), the learned composition;
+//   TANGENT = true:  e_0 = 0, e_{j+1} = J_j e_j + d_j, lambda_{j+1} += e_{j+1}, J_j the
+//                    Jacobian of G_j at lambda_j: per slice the forward pass at
+//                    lambda_j (for GELU' of each hidden layer) and the tangent
+//                    of (e_j / sx, 0) share every weight read.  The tangent
+//                    only steers the correction, whose fixed point the float64
+//                    defects d_j set.
+constexpr int kTanThreads = 128;       // hidden units per CTA of the pair
+constexpr size_t kTanWeightBytes = 2 * sizeof(__nv_bfloat16) * (size_t)H * kTanThreads;
+
+template <int NS, bool TANGENT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
+    learned_sweep_kernel(const float* P, const __nv_bfloat16* W2t, const __nv_bfloat16* W3t,
+                         const float* sx_inv, const double* sd, int S, int64_t count, double* lam,
+                         const double* dfc) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char tan_smem[];
+  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(tan_smem);   // [k][unit of this CTA]
+  __nv_bfloat16* W3s = W2s + H * kTanThreads;
+  float* hA = reinterpret_cast<float*>(W3s + H * kTanThreads);       // [NS][H] each
+  float* hB = hA + NS * H;
+  float* dA = hB + NS * H;                                           // tangents (TANGENT only)
+  float* dB = dA + NS * H;
   __shared__ float xin[NS][IN], xtan[NS][D];
-  __shared__ float hA[NS][H], dA[NS][H], hB[NS][H], dB[NS][H];
-  __shared__ float red[NS][8][D];
+  __shared__ float red[NS][kTanThreads / 32][D];
+  __shared__ float part[NS][D];
   __shared__ double e[NS][D];
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t s0 = (int64_t)blockIdx.x * NS;
+  const int u = kTanThreads * (int)rank + t;                           // this thread's hidden unit
+  const int64_t s0 = (int64_t)(blockIdx.x >> 1) * NS;
+  float* hA_p = cl.map_shared_rank(hA, rank ^ 1u);
+  float* dA_p = cl.map_shared_rank(dA, rank ^ 1u);
+  float* hB_p = cl.map_shared_rank(hB, rank ^ 1u);
+  float* dB_p = cl.map_shared_rank(dB, rank ^ 1u);
+  float* part_p = cl.map_shared_rank(&part[0][0], rank ^ 1u);
+  double* e_p = cl.map_shared_rank(&e[0][0], rank ^ 1u);
+  for (int i = t; i < H * kTanThreads; i += kTanThreads) {
+    const int k = i / kTanThreads, c = i - k * kTanThreads;
+    W2s[i] = W2t[k * H + kTanThreads * rank + c];
+    W3s[i] = W3t[k * H + kTanThreads * rank + c];
+  }
   if (t < NS * D) e[t / D][t % D] = 0.0;
   float w1[IN], w4[D];
 #pragma unroll
-  for (int k = 0; k < IN; ++k) w1[k] = P[oW1 + t * IN + k];
+  for (int k = 0; k < IN; ++k) w1[k] = P[oW1 + u * IN + k];
 #pragma unroll
-  for (int c = 0; c < D; ++c) w4[c] = P[oW4 + c * H + t];
-  const float b1 = P[ob1 + t], b2 = P[ob2 + t], b3 = P[ob3 + t];
-  __syncthreads();
+  for (int c = 0; c < D; ++c) w4[c] = P[oW4 + c * H + u];
+  const float b1 = P[ob1 + u], b2 = P[ob2 + u], b3 = P[ob3 + u];
+  cl.sync();
   for (int j = 0; j < S; ++j) {
     const double* lj = lam + (size_t)j * count * D;
     if (t < NS * D) {
@@ -171,82 +203,115 @@ __global__ void __launch_bounds__(256) tangent_sweep_kernel(const float* P, cons
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {             // layer 1: base and tangent
-      float z = b1, dz = 0.f;
+    for (int q = 0; q < NS; ++q) {             // layer 1
+      float z = b1;
 #pragma unroll
       for (int k = 0; k < IN; ++k) z = fmaf(w1[k], xin[q][k], z);
-#pragma unroll
-      for (int k = 0; k < D; ++k) dz = fmaf(w1[k], xtan[q][k], dz);
       float g;
-      hA[q][t] = gelu_with_grad(z, &g);
-      dA[q][t] = g * dz;
+      const float h = gelu_with_grad(z, &g);
+      hA[q * H + u] = h;
+      hA_p[q * H + u] = h;
+      if constexpr (TANGENT) {
+        float dz = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) dz = fmaf(w1[k], xtan[q][k], dz);
+        dA[q * H + u] = g * dz;
+        dA_p[q * H + u] = g * dz;
+      }
     }
-    __syncthreads();
+    cl.sync();
     {                                          // layer 2
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < H; ++k) {
-        const float w = __bfloat162float(W2t[k * H + t]);
+        const float w = __bfloat162float(W2s[k * kTanThreads + t]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-          z[q] = fmaf(w, hA[q][k], z[q]);
-          dz[q] = fmaf(w, dA[q][k], dz[q]);
+          z[q] = fmaf(w, hA[q * H + k], z[q]);
+          if constexpr (TANGENT) dz[q] = fmaf(w, dA[q * H + k], dz[q]);
         }
       }
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         float g;
-        hB[q][t] = gelu_with_grad(z[q] + b2, &g);
-        dB[q][t] = g * dz[q];
+        const float h = gelu_with_grad(z[q] + b2, &g);
+        hB[q * H + u] = h;
+        hB_p[q * H + u] = h;
+        if constexpr (TANGENT) {
+          dB[q * H + u] = g * dz[q];
+          dB_p[q * H + u] = g * dz[q];
+        }
       }
     }
-    __syncthreads();
-    float dh3[NS];
-    {                                          // layer 3: only GELU' of the base is needed
+    cl.sync();
+    {                                          // layer 3 and this unit's share of layer 4
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-#pragma unroll 4
+#pragma unroll 8
       for (int k = 0; k < H; ++k) {
-        const float w = __bfloat162float(W3t[k * H + t]);
+        const float w = __bfloat162float(W3s[k * kTanThreads + t]);
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-          z[q] = fmaf(w, hB[q][k], z[q]);
-          dz[q] = fmaf(w, dB[q][k], dz[q]);
+          z[q] = fmaf(w, hB[q * H + k], z[q]);
+          if constexpr (TANGENT) dz[q] = fmaf(w, dB[q * H + k], dz[q]);
         }
       }
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         float g;
-        gelu_with_grad(z[q] + b3, &g);
-        dh3[q] = g * dz[q];
-      }
-    }
+        const float h3 = gelu_with_grad(z[q] + b3, &g);
+        const float v = TANGENT ? g * dz[q] : h3;   // dh3 (tangent) or h3 (forward)
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {             // layer 4 tangent: dout = W4 dh3, summed over units
+        for (int c = 0; c < D; ++c) {
+          float p = w4[c] * v;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        float p = w4[c] * dh3[q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-        if (lane == 0) red[q][warp][c] = p;
+          for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+          if (lane == 0) red[q][warp][c] = p;
+        }
       }
     }
     __syncthreads();
-    if (t < NS * D) {                          // e_{j+1} = e_j + sd dout + d_j
+    if (t < NS * D) {                          // this CTA's half of W4 v
       const int q = t / D, c = t % D;
       float o = 0.f;
 #pragma unroll
-      for (int wv = 0; wv < 8; ++wv) o += red[q][wv][c];
-      const int64_t i = (s0 + q) * D + c;
-      const double en = e[q][c] + sd[c] * (double)o + dfc[(size_t)j * count * D + i];
-      e[q][c] = en;
-      lam[(size_t)(j + 1) * count * D + i] += en;
+      for (int wv = 0; wv < kTanThreads / 32; ++wv) o += red[q][wv][c];
+      part[q][c] = o;
     }
-    __syncthreads();
+    cl.sync();
+    if (rank == 0 && t < NS * D) {
+      const int q = t / D, c = t % D;
+      const float o = part[q][c] + part_p[q * D + c];
+      const int64_t i = (s0 + q) * D + c;
+      double* lj1 = lam + (size_t)(j + 1) * count * D;
+      if constexpr (TANGENT) {                 // e_{j+1} = e_j + sd dout + d_j, to both CTAs
+        const double en = e[q][c] + sd[c] * (double)o + dfc[(size_t)j * count * D + i];
+        e[q][c] = en;
+        e_p[q * D + c] = en;
+        lj1[i] += en;
+      } else {                                 // lambda_{j+1} = lambda_j + sd (W4 h3 + b4)
+        lj1[i] = lj[i] + sd[c] * (double)(o + P[ob4 + c]);
+      }
+    }
+    cl.sync();
   }
+}
+
+template <int NS, bool TANGENT>
+static nv_status launch_learned_sweep(const float* P, const __nv_bfloat16* W2t, const __nv_bfloat16* W3t,
+                                      const float* sx_inv, const double* sd, int S, int64_t count, double* lam,
+                                      const double* dfc, cudaStream_t s) {
+  const size_t smem = kTanWeightBytes + (TANGENT ? 4 : 2) * sizeof(float) * (size_t)NS * H;
+  nv_status st = nv_cuda_check(cudaFuncSetAttribute(learned_sweep_kernel<NS, TANGENT>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                               "learned sweep shared memory attribute");
+  if (st != NV_OK) return st;
+  learned_sweep_kernel<NS, TANGENT><<<(unsigned)(2 * (count / NS)), kTanThreads, smem, s>>>(
+      P, W2t, W3t, sx_inv, sd, S, count, lam, dfc);
+  return nv_cuda_check(cudaGetLastError(), "learned_sweep_kernel launch");
 }
 
 // ---- parameters
@@ -528,7 +593,7 @@ struct nv_mlp {
   int64_t pr_count;
   int pr_S;
   cudaGraphExec_t pr_graph;
-  int pr_iters, pr_rk4;
+  int pr_iters, pr_rk4, pr_form;
   int64_t pr_m;
   double pr_h, pr_p[3];
 };
@@ -920,24 +985,64 @@ extern "C" nv_status nv_propagate(const nv_rhs* rhs, double t0, double T, int32_
   return nv_cuda_check(cudaGetLastError(), "propagate_kernel launch");
 }
 
+// NS states per CTA pair: the fewest with which the pairs (one CTA per SM,
+// their weights filling its shared memory) fit the SMs at once.
+static nv_status run_learned_sweep(const nv_mlp* m, bool tangent, int S, int64_t count, double* lam,
+                                   const double* dfc, int sms, cudaStream_t s) {
+  const int64_t pairs = sms / 2;
+  const int ns = count <= 2 * pairs ? 2 : count <= 4 * pairs ? 4 : count <= 8 * pairs ? 8 : 16;
+#define NVPIT_SWEEP(NS, TG) \
+  launch_learned_sweep<NS, TG>(m->P, m->W2t, m->W3t, m->sx_inv, m->sd, S, count, lam, dfc, s)
+  if (tangent) {
+    if (ns == 2) return NVPIT_SWEEP(2, true);
+    if (ns == 4) return NVPIT_SWEEP(4, true);
+    if (ns == 8) return NVPIT_SWEEP(8, true);
+    return NVPIT_SWEEP(16, true);
+  }
+  if (ns == 2) return NVPIT_SWEEP(2, false);
+  if (ns == 4) return NVPIT_SWEEP(4, false);
+  if (ns == 8) return NVPIT_SWEEP(8, false);
+  return NVPIT_SWEEP(16, false);
+#undef NVPIT_SWEEP
+}
+
+// Iteration 0 of the learned correction through the fused sweep (float32
+// activations, one launch) rather than the per-slice tcgen05 forward of
+// nv_mlp_compose (bf16 activations, a few launches per slice): nv_tune_set
+// key 18, by default the sweep while every CTA pair of it fits the GPU at once.
+static bool learned_first_fused(int64_t count, int sms) {
+  if (g_tune.learned_first_form == 1) return false;
+  if (g_tune.learned_first_form == 2) return true;
+  return count <= 16 * (int64_t)(sms / 2);
+}
+
 // The schedule of the learned correction on the library-owned buffers, with
 // lambda_0 already in pr_lam: the learned composition, then `iters` rounds of
 // defects of every slice and the correction chain over the tangent maps.
 static nv_status parareal_schedule(nv_mlp* m, const RhsParams& pp, int64_t msteps, double h, int rk4, int S,
                                    int iters, int64_t count, cudaStream_t s) {
-  const int64_t per = count * D;
+  int dev = 0, sms = 0;
+  nv_status st0 = nv_cuda_check(cudaGetDevice(&dev), "current device");
+  if (st0 == NV_OK) st0 = nv_cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  if (st0 != NV_OK) return st0;
   double* lam = m->pr_lam;
   double* dfc = m->pr_dfc;
   nv_status st = NV_OK;
-  for (int j = 0; j < S && st == NV_OK; ++j) {   // iteration 0: lambda_{j+1} = G_j(lambda_j)
-    const double* lj = lam + (size_t)j * per;
-    double* lj1 = lam + (size_t)(j + 1) * per;
-    if ((st = nv_cuda_check(cudaMemcpyAsync(lj1, lj, sizeof(double) * per, cudaMemcpyDeviceToDevice, s),
-                            "state copy")) != NV_OK)
-      break;
-    if ((st = mlp_infer(m, lj1, count, j, S, s)) != NV_OK) break;
-    advance_kernel<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(lj1, count, m->out, m->sd);
-    st = nv_cuda_check(cudaGetLastError(), "advance");
+  // iteration 0: the learned composition lambda_{j+1} = G_j(lambda_j)
+  if (learned_first_fused(count, sms)) {
+    st = run_learned_sweep(m, false, S, count, lam, nullptr, sms, s);
+  } else {                                       // per slice, the tcgen05 forward of nv_mlp_compose
+    const int64_t per = count * D;
+    for (int j = 0; j < S && st == NV_OK; ++j) {
+      const double* lj = lam + (size_t)j * per;
+      double* lj1 = lam + (size_t)(j + 1) * per;
+      if ((st = nv_cuda_check(cudaMemcpyAsync(lj1, lj, sizeof(double) * per, cudaMemcpyDeviceToDevice, s),
+                              "state copy")) != NV_OK)
+        break;
+      if ((st = mlp_infer(m, lj1, count, j, S, s)) != NV_OK) break;
+      advance_kernel<<<(unsigned)((per + 255) / 256), 256, 0, s>>>(lj1, count, m->out, m->sd);
+      st = nv_cuda_check(cudaGetLastError(), "advance");
+    }
   }
   for (int k = 1; k <= iters && st == NV_OK; ++k) {
     // defects of the previous iterate, every slice and state at once
@@ -946,13 +1051,7 @@ static nv_status parareal_schedule(nv_mlp* m, const RhsParams& pp, int64_t mstep
                                                                                          count, lam, dfc);
     if ((st = nv_cuda_check(cudaGetLastError(), "slice_defect_kernel launch")) != NV_OK) break;
     // the correction chain over the tangent maps, every state's chain in one launch
-    if (count <= 512)
-      tangent_sweep_kernel<1><<<(unsigned)count, 256, 0, s>>>(m->P, m->W2t, m->W3t, m->sx_inv, m->sd, S, count,
-                                                             lam, dfc);
-    else
-      tangent_sweep_kernel<4><<<(unsigned)(count / 4), 256, 0, s>>>(m->P, m->W2t, m->W3t, m->sx_inv, m->sd, S,
-                                                                    count, lam, dfc);
-    st = nv_cuda_check(cudaGetLastError(), "tangent_sweep_kernel launch");
+    st = run_learned_sweep(m, true, S, count, lam, dfc, sms, s);
   }
   return st;
 }
@@ -991,7 +1090,9 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
   // counts the learned composition's kernels are launch-bound when issued
   // one by one
   const int rk4 = steps->scheme == NV_RK4;
-  const bool same = m->pr_graph && m->pr_iters == iters && m->pr_rk4 == rk4 && m->pr_m == msteps &&
+  const int form = g_tune.learned_first_form;
+  const bool same = m->pr_graph && m->pr_iters == iters && m->pr_rk4 == rk4 && m->pr_form == form &&
+                    m->pr_m == msteps &&
                     m->pr_h == h && m->pr_p[0] == pp.p[0] && m->pr_p[1] == pp.p[1] && m->pr_p[2] == pp.p[2];
   if (!same) {
     if (m->pr_graph) {
@@ -1017,6 +1118,7 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
     }
     m->pr_iters = iters;
     m->pr_rk4 = rk4;
+    m->pr_form = form;
     m->pr_m = msteps;
     m->pr_h = h;
     for (int i = 0; i < 3; ++i) m->pr_p[i] = pp.p[i];

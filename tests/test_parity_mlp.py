@@ -276,7 +276,7 @@ def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error(
         net.parareal(r, w.t0, w.T, S, st64, k, y0, yT, lambdas=lam)
         torch.cuda.synchronize()
         yk = yT.cpu().numpy()
-        if k == 0:
+        if k == 0:                # 4096 states: nv_mlp_compose's per-slice path by default
             assert np.array_equal(yk, comp.cpu().numpy())
         if 1 <= k <= 3:
             ref = y0.clone()
@@ -314,26 +314,49 @@ def test_learned_parareal_reaches_the_fine_solution_and_its_cost_at_equal_error(
 
 
 
-def test_parareal_rejects_bad_arguments_and_keeps_iteration_zero_exact():
+def test_parareal_rejects_bad_arguments_and_its_iteration_zero_is_the_learned_map():
     """count must be a positive multiple of 128 and iters >= 0 (checked before
-    any launch); with iters = 0 the result is the learned composition of
-    nv_mlp_compose bit for bit, on 256 states of 3 slices."""
+    any launch).  With iters = 0 the result is the learned composition, on 256
+    states of 3 slices: through nv_mlp_compose's per-slice path (nv_tune_set
+    key 18 = 1) bit for bit nv_mlp_compose's states; through the fused sweep
+    (the default at this count, and key 18 = 2) the oracle's map applied slice
+    by slice with the network's bf16 layer-2 and layer-3 weights, to float32
+    rounding of the activations (1e-5; the bf16 activations of the per-slice
+    path are held only to 1e-3)."""
     torch = need_gpu()
     S, count = 3, 256
     w = workloads.chain3(S=S, M=128, T=3 * 0.15625)
     net = nvp.MLP(seed=8)
-    net.set_scales([0.6] * 6, [0.05] * 6)
+    sx, sd = [0.6] * 6, [0.05] * 6
+    net.set_scales(sx, sd)
     r, st = nvp.rhs("chain3", 6), nvp.steps("rk4", w.dt)
-    y0 = torch.tensor(workloads.Stream(5).uniform(count * 6, -1.0, 1.0).reshape(count, 6), device="cuda")
+    Y0 = workloads.Stream(5).uniform(count * 6, -1.0, 1.0).reshape(count, 6)
+    y0 = torch.tensor(Y0, device="cuda")
     yT, yc = torch.empty_like(y0), torch.empty_like(y0)
     with pytest.raises(nvp.NvError):
         net.parareal(r, w.t0, w.T, S, st, -1, y0, yT)
     with pytest.raises(nvp.NvError):
         net.parareal(r, w.t0, w.T, S, st, 1, y0[:100].contiguous(), yT[:100].contiguous())
-    net.parareal(r, w.t0, w.T, S, st, 0, y0, yT)
     net.compose(r, w.t0, w.T, S, st, y0, yc)
-    torch.cuda.synchronize()
-    assert torch.equal(yT, yc)
+    p = unflatten(net.params())
+    p["W2"], p["W3"] = _bf16(p["W2"]), _bf16(p["W3"])
+    lam = Y0.copy()
+    for j in range(S):
+        lam = omlp.apply_map(p, lam, j / S, np.array(sx), np.array(sd))
+    out = {}
+    try:
+        for form in (1, 0, 2):
+            nvp.tune_set(18, form)
+            yT = torch.full_like(y0, float("nan"))
+            net.parareal(r, w.t0, w.T, S, st, 0, y0, yT)
+            torch.cuda.synchronize()
+            out[form] = yT.cpu().numpy()
+    finally:
+        nvp.tune_set(18, 0)
+    assert np.array_equal(out[1], yc.cpu().numpy())
+    assert rel_l2(out[1], lam) <= 1e-3
+    assert np.array_equal(out[0], out[2])
+    assert rel_l2(out[0], lam) <= 1e-5, rel_l2(out[0], lam)
     net.destroy()
 
 
