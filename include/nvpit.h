@@ -501,10 +501,12 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          in the float64 advection-diffusion window build (16: 256-thread
  *          CTAs, 8: 512-thread CTAs, 32: 128-thread CTAs); the same maps bit
  *          for bit.
- *   key 17: 0 (default, = 1), 1 or 2: lanes per column in the first of the
- *          float32 heat build's three windows (22, 44, 88 rows): 1 lane of 22
- *          rows (then 2 and 4), or 2 lanes of 11 rows (then 4 and 8, the
- *          float64 shape); the same maps bit for bit.
+ *   key 17: 0..4: form of the float32 heat build's three windows (22, 44,
+ *          88 rows): 1 one lane of 22 rows per column (then 2 and 4), 2 two
+ *          lanes of 11 rows (then 4 and 8, the float64 shape), 3 and 4 the
+ *          same shapes with column c of two slices in the two halves of each
+ *          register, every stencil operation one packed f32x2 instruction for
+ *          both (S > 1); 0 (default) = 4.  The same maps bit for bit.
  *   key 18: 0 (default), 1 or 2: iteration 0 of nv_mlp_parareal: 0 the
  *          fused one-launch sweep while count <= 16 x (SMs / 2), else the
  *          per-slice path of nv_mlp_compose; 1 always that per-slice path;

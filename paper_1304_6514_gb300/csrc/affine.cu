@@ -484,6 +484,208 @@ __global__ void __launch_bounds__(128) heat_window3_kernel(HeatArgs a, int m1, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed float32 pairs.  The homogeneous heat columns are the same arithmetic
+// in every slice (the operator does not depend on time), so the float32 build
+// can carry column c of slices 2p and 2p+1 in the low and high halves of one
+// 64-bit register and issue each stencil operation once for both: the
+// Blackwell packed add / mul / fma on .f32x2 (round to nearest, no flush to
+// zero), each half the IEEE operation of the scalar code, so every entry is
+// the scalar kernel's bit for bit.  Half the arithmetic instructions per
+// row-step; the shuffles and window-edge selects stay one per value.
+typedef unsigned long long f32x2_t;
+
+__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) {
+  f32x2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) {
+  f32x2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {   // a*b + c
+  f32x2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2_t f2_splat(float x) {
+  f32x2_t d;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(f32x2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2_t f2_neg(f32x2_t a) { return a ^ 0x8000000080000000ull; }   // sign flips
+
+// window_step on packed pairs: the same halo rules and the same expression.
+template <int G, int R>
+__device__ __forceinline__ void window_step_x2(f32x2_t (&y)[R], int gl, bool lo_end, bool hi_end, f32x2_t c0,
+                                               f32x2_t c1, f32x2_t c2, f32x2_t c3, f32x2_t c4) {
+  f32x2_t e[R + 8];
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      e[k] = __shfl_up_sync(0xffffffffu, y[R - 4 + k], 1, G);
+      e[R + 4 + k] = __shfl_down_sync(0xffffffffu, y[k], 1, G);
+    }
+  }
+  if (gl == 0) {
+    e[0] = lo_end ? f2_neg(y[2]) : 0ull;
+    e[1] = lo_end ? f2_neg(y[1]) : 0ull;
+    e[2] = lo_end ? f2_neg(y[0]) : 0ull;
+    e[3] = 0ull;
+  }
+  if (gl == G - 1) {
+    e[R + 4] = 0ull;
+    e[R + 5] = hi_end ? f2_neg(y[R - 1]) : 0ull;
+    e[R + 6] = hi_end ? f2_neg(y[R - 2]) : 0ull;
+    e[R + 7] = hi_end ? f2_neg(y[R - 3]) : 0ull;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) e[i + 4] = y[i];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    f32x2_t acc = f2_mul(c4, f2_add(e[i], e[i + 8]));
+    acc = f2_fma(c3, f2_add(e[i + 1], e[i + 7]), acc);
+    acc = f2_fma(c2, f2_add(e[i + 2], e[i + 6]), acc);
+    acc = f2_fma(c1, f2_add(e[i + 3], e[i + 5]), acc);
+    y[i] = f2_fma(c0, e[i + 4], acc);
+  }
+}
+
+// store_windows for packed pairs: pair index id = p*n + c-1 holds column c of
+// slices 2p (low halves) and 2p+1 (high halves; absent when 2p+1 = S).
+template <int G, int R, bool TF32OUT>
+__device__ __forceinline__ void store_windows_x2(const f32x2_t* buf, float* out, int64_t first, int64_t total,
+                                                 int n, int reach, int lane, int S) {
+  constexpr int W = G * R, CPW = 32 / G, SW = G * (R + 1);
+  const int cols = n + 1;
+#pragma unroll 1
+  for (int g = 0; g < CPW; ++g) {
+    const int64_t id = first + g;
+    if (id >= total) break;                         // warp-uniform
+    const int jp = (int)(id / n);
+    const int cg = 1 + (int)(id - (int64_t)jp * n);
+    const int v0 = window_origin(cg, reach, n, W);
+    const bool has_hi = 2 * jp + 1 < S;
+    float* colA = out + ((int64_t)(2 * jp) * cols + cg) * n;
+    float* colB = colA + (int64_t)cols * n;
+    const f32x2_t* win = buf + g * SW;
+    if (n % 4 == 0) {
+      for (int r0 = lane * 4; r0 < n; r0 += 128) {
+        float va[4], vb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int o = r0 + q - v0;
+          f2_unpack((unsigned)o < (unsigned)W ? win[o] : 0ull, va[q], vb[q]);
+          if constexpr (TF32OUT) {
+            va[q] = round_tf32(va[q]);
+            vb[q] = round_tf32(vb[q]);
+          }
+        }
+        *reinterpret_cast<float4*>(colA + r0) = make_float4(va[0], va[1], va[2], va[3]);
+        if (has_hi) *reinterpret_cast<float4*>(colB + r0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
+      }
+    } else {
+      for (int r = lane; r < n; r += 32) {
+        const int o = r - v0;
+        float va, vb;
+        f2_unpack((unsigned)o < (unsigned)W ? win[o] : 0ull, va, vb);
+        if constexpr (TF32OUT) {
+          va = round_tf32(va);
+          vb = round_tf32(vb);
+        }
+        colA[r] = va;
+        if (has_hi) colB[r] = vb;
+      }
+    }
+  }
+}
+
+// heat_window3_kernel in float32 on packed slice pairs: the same three
+// windows, phases and staging (shared memory of 8-byte pairs, dynamic: four
+// warps x three buffers of 32*(R+1) pairs), over ceil(S/2)*n pair columns.
+template <int G1, int R, bool TF32OUT>
+__global__ void __launch_bounds__(128) heat_window3_x2_kernel(HeatArgs a, int m1, int m2) {
+  constexpr int G2 = 2 * G1, G3 = 4 * G1, W1 = G1 * R, W2 = G2 * R, W3 = G3 * R;
+  constexpr int C1 = 32 / G1, C2 = 32 / G2, C3 = 32 / G3;
+  static_assert(R >= 4 && G1 >= 1 && 32 % G3 == 0, "R >= 4 rows per lane, 4*G1 lanes dividing the warp");
+  extern __shared__ __align__(16) unsigned char x2_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  f32x2_t* b1 = reinterpret_cast<f32x2_t*>(x2_smem) + warp * 3 * 32 * (R + 1);
+  f32x2_t* b2 = b1 + 32 * (R + 1);
+  f32x2_t* stage = b2 + 32 * (R + 1);
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n = a.n;
+  const int reach1 = 4 * m1, reach2 = 4 * m2, reach = (int)(4 * a.m);   // launcher: 8m+1 <= W3 <= n
+  const int64_t total = (int64_t)((a.S + 1) / 2) * n;                   // pair columns
+  const f32x2_t c0 = f2_splat(poly9_weight<float>(a, 0)), c1 = f2_splat(poly9_weight<float>(a, 1)),
+                c2 = f2_splat(poly9_weight<float>(a, 2)), c3 = f2_splat(poly9_weight<float>(a, 3)),
+                c4 = f2_splat(poly9_weight<float>(a, 4));
+  const f32x2_t one = f2_splat(1.0f);
+  float* out = reinterpret_cast<float*>(a.out);
+  auto column = [&](int64_t idx) {              // column of pair index idx
+    const int jp = idx < total ? (int)(idx / n) : 0;
+    return idx < total ? 1 + (int)(idx - (int64_t)jp * n) : 1;
+  };
+  for (int64_t w = warp0; w * C1 < total; w += nwarps) {
+    {                                           // phase 1: C1 pair columns, G1 lanes each
+      const int gl = lane % G1;
+      const int c = column(w * C1 + lane / G1);
+      const int w0 = window_origin(c, reach1, n, W1);
+      f32x2_t y[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) y[i] = (w0 + gl * R + i == c - 1) ? one : 0ull;
+      for (int step = 0; step < m1; ++step)
+        window_step_x2<G1, R>(y, gl, w0 == 0, w0 + W1 == n, c0, c1, c2, c3, c4);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < R; ++i) b1[window_slot<G1, R>(lane) + i] = y[i];
+      __syncwarp();
+    }
+#pragma unroll 1
+    for (int r2 = 0; r2 < C1 / C2; ++r2) {      // phase 2
+      const int64_t first2 = w * C1 + r2 * C2;
+      if (first2 >= total) break;               // warp-uniform
+      {
+        const int gl = lane % G2, q = r2 * C2 + lane / G2;
+        const int c = column(w * C1 + q);
+        const int wa = window_origin(c, reach1, n, W1), wb = window_origin(c, reach2, n, W2);
+        f32x2_t y[R];
+        widen_window<f32x2_t, G1, R>(y, b1, q, wa, W1, wb, gl);
+        for (int step = m1; step < m2; ++step)
+          window_step_x2<G2, R>(y, gl, wb == 0, wb + W2 == n, c0, c1, c2, c3, c4);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) b2[window_slot<G2, R>(lane) + i] = y[i];
+        __syncwarp();
+      }
+#pragma unroll 1
+      for (int r3 = 0; r3 < C2 / C3; ++r3) {    // phase 3
+        const int64_t first3 = first2 + r3 * C3;
+        if (first3 >= total) break;             // warp-uniform
+        const int gl = lane % G3, q = r3 * C3 + lane / G3;
+        const int c = column(first2 + q);
+        const int wb = window_origin(c, reach2, n, W2), wc = window_origin(c, reach, n, W3);
+        f32x2_t y[R];
+        widen_window<f32x2_t, G2, R>(y, b2, q, wb, W2, wc, gl);
+        for (int64_t step = m2; step < a.m; ++step)
+          window_step_x2<G3, R>(y, gl, wc == 0, wc + W3 == n, c0, c1, c2, c3, c4);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < R; ++i) stage[window_slot<G3, R>(lane) + i] = y[i];
+        __syncwarp();
+        store_windows_x2<G3, R, TF32OUT>(stage, out, first3, total, n, reach, lane, a.S);
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // Columns that take the four RK4 stages literally: the forcing column c = 0
 // of every slice, and for a time-dependent operator every column.
 template <typename T, int R>
@@ -497,6 +699,8 @@ __global__ void __launch_bounds__(256) heat_literal_kernel(HeatArgs a, int all_c
   const double dx = 1.0 / (double)(n + 1);
   const T cdx = (T)(a.kappa / (dx * dx));
   T* out = reinterpret_cast<T*>(a.out);
+  __shared__ double sxt[32 * R];
+  forcing_table(sxt, min(n, 32 * R));
   for (int64_t w = warp0; w < total; w += nwarps) {
     const int j = (int)(w / per_slice);
     const int c = (int)(w - (int64_t)j * per_slice);
@@ -513,7 +717,7 @@ __global__ void __launch_bounds__(256) heat_literal_kernel(HeatArgs a, int all_c
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         const int r = lane * R + i;
-        if (r < n) sx[i] = (T)sin(M_PI * ((double)(r + 1) / (double)(n + 1)));
+        if (r < n) sx[i] = (T)sxt[r];
       }
     }
     HalfStepCoefs hc{};
@@ -573,11 +777,13 @@ __global__ void __launch_bounds__(256) heat_forcing_kernel(HeatArgs a) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int n = a.n;
   double* out = reinterpret_cast<double*>(a.out);
+  __shared__ double sxt[32 * R];
+  forcing_table(sxt, min(n, 32 * R));
   for (int64_t j = warp0; j < a.S; j += nwarps) {
     double y[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) y[i] = 0.0;
-    heat_forced_solve<R>(a, y, j, lane);
+    heat_forced_solve<R>(a, y, j, lane, sxt);
     store_column<R, false>(y, column_stage<R, double>(), out + j * (int64_t)(n + 1) * n, lane, n);
   }
 }
@@ -587,7 +793,9 @@ __global__ void __launch_bounds__(256) heat_defect_kernel(HeatArgs a, const doub
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp0; j < a.S; j += nwarps) heat_defect_slice<R>(a, lt, d, j, lane);
+  __shared__ double sxt[32 * R];
+  forcing_table(sxt, min(a.n, 32 * R));
+  for (int64_t j = warp0; j < a.S; j += nwarps) heat_defect_slice<R>(a, lt, d, j, lane, sxt);
 }
 
 }  // namespace nvpit
@@ -713,6 +921,31 @@ static nv_status launch_window3(const HeatArgs& a, int m1, int m2, cudaStream_t 
   return nv_cuda_check(cudaGetLastError(), "heat_window3_kernel launch");
 }
 
+template <int G1, int R>
+static nv_status launch_window3_x2(const HeatArgs& a, int m1, int m2, cudaStream_t s, bool tf32out) {
+  const int block = 128;
+  const size_t smem = sizeof(f32x2_t) * 4 * 3 * 32 * (R + 1);
+  const int64_t warps = ((int64_t)((a.S + 1) / 2) * a.n + 32 / G1 - 1) / (32 / G1);
+  int grid = 0;
+  nv_status st;
+  if (tf32out) {
+    st = nv_cuda_check(cudaFuncSetAttribute(heat_window3_x2_kernel<G1, R, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "heat_window3_x2_kernel shared memory");
+    if (st == NV_OK) st = persistent_grid(heat_window3_x2_kernel<G1, R, true>, block, warps, &grid, smem);
+    if (st != NV_OK) return st;
+    heat_window3_x2_kernel<G1, R, true><<<grid, block, smem, s>>>(a, m1, m2);
+    return nv_cuda_check(cudaGetLastError(), "heat_window3_x2_kernel launch");
+  }
+  st = nv_cuda_check(cudaFuncSetAttribute(heat_window3_x2_kernel<G1, R, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                     "heat_window3_x2_kernel shared memory");
+  if (st == NV_OK) st = persistent_grid(heat_window3_x2_kernel<G1, R, false>, block, warps, &grid, smem);
+  if (st != NV_OK) return st;
+  heat_window3_x2_kernel<G1, R, false><<<grid, block, smem, s>>>(a, m1, m2);
+  return nv_cuda_check(cudaGetLastError(), "heat_window3_x2_kernel launch");
+}
+
 // Built window shapes: one window of G lanes x R rows (W = G*R >= 8m+1); two
 // (GA x R for the first m1 = (GA*R-1)/8 steps, 2*GA x R for the rest); or
 // three (G1, 2*G1, 4*G1 lanes of R rows, switching after m1 = (G1*R-1)/8 and
@@ -748,6 +981,10 @@ static const int kWindow2[][2] = {{4, 11}, {8, 8}};
 // window edges, not the arithmetic, set the pace); key 17 picks for float32
 static const int kWindow3[][2] = {{2, 11}, {1, 22}};
 
+// float32 three-window build on packed slice pairs: nv_tune_set key 17 = 0
+// (default: two lanes of 11 rows), 3 or 4
+static bool heat_f32_packed() { return g_tune.heat_f32_lanes == 0 || g_tune.heat_f32_lanes >= 3; }
+
 template <typename T>
 static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s, bool tf32out, int form,
                                     BuildInfo* bi) {
@@ -770,7 +1007,8 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
     }
   }
   if (form == 0 || form == 5) {
-    const int k3 = sizeof(T) == 4 && g_tune.heat_f32_lanes != 2 ? 1 : 0;
+    const int lanes = g_tune.heat_f32_lanes;
+    const int k3 = sizeof(T) == 4 && (lanes == 1 || lanes == 3) ? 1 : 0;
     for (int k = k3; k <= k3; ++k) {
       const int W1 = kWindow3[k][0] * kWindow3[k][1], W2 = 2 * W1, W3 = 4 * W1;
       const int k1 = (W1 - 1) / 8, k2 = (W2 - 1) / 8;
@@ -785,9 +1023,15 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
   else if (pick >= 6 && pick < 8)
     note_build(bi, best, "heat_window2_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow2[pick - 6][0],
                kWindow2[pick - 6][1], t32);
+  // float32 three windows on packed slice pairs (key 17 = 3 or 4) where S > 1
+  const bool x2 = sizeof(T) == 4 && pick >= 8 && a.S > 1 && heat_f32_packed();
+  if (x2)
+    note_build(bi, best, "heat_window3_x2_kernel<%d,%d,%d>", kWindow3[pick - 8][0], kWindow3[pick - 8][1], t32);
   else if (pick >= 8)
     note_build(bi, best, "heat_window3_kernel<%s,%d,%d,%d>", type_name<T>(), kWindow3[pick - 8][0],
                kWindow3[pick - 8][1], t32);
+  if (x2) return pick == 8 ? launch_window3_x2<2, 11>(a, m1, m2, s, tf32out)
+                           : launch_window3_x2<1, 22>(a, m1, m2, s, tf32out);
   switch (pick) {
     case 0: return launch_window_GR<T, 8, 4>(a, block, s, tf32out);
     case 1: return launch_window_GR<T, 8, 8>(a, block, s, tf32out);

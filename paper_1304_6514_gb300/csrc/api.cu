@@ -475,7 +475,7 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       g_tune.adv_build_form = value;
       break;
     case 17:
-      if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "float32 heat window lanes are 0, 1 or 2");
+      if (value < 0 || value > 4) return nv_fail(NV_EINVAL, "float32 heat window form is 0..4");
       g_tune.heat_f32_lanes = value;
       break;
     case 18:

@@ -126,6 +126,20 @@ struct StageCoefs {
 // evaluates the half-step time q = 2 i0 + l (l <= 30; l = 31 idles) once, and
 // the steps read them by shuffle, so the trigonometric calls run once per
 // warp instead of once per lane.
+// Spatial shape of the forcing, sin(pi x_r) at x_r = (r+1)/(n+1): the same
+// for every slice and column, so the kernels that integrate many forced
+// columns tabulate it once per CTA (forcing_table) instead of per lane and
+// column: float64 sines run at the FP64 rate.
+__device__ __forceinline__ double forcing_shape(int r, int n) {
+  return sin(M_PI * ((double)(r + 1) / (double)(n + 1)));
+}
+
+// Fill tab[0 .. n-1] with forcing_shape; every thread of the CTA must call it.
+__device__ __forceinline__ void forcing_table(double* tab, int n) {
+  for (int r = threadIdx.x; r < n; r += blockDim.x) tab[r] = forcing_shape(r, n);
+  __syncthreads();
+}
+
 struct HalfStepCoefs {
   double g, a;
 };
@@ -250,7 +264,8 @@ __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync
 // i0 .. i0+14 are computed one step per lane and broadcast by shuffle);
 // otherwise the literal stages.
 template <int R>
-__device__ __forceinline__ void heat_forced_solve(const HeatArgs& a, double (&y)[R], int64_t j, int lane) {
+__device__ __forceinline__ void heat_forced_solve(const HeatArgs& a, double (&y)[R], int64_t j, int lane,
+                                                  const double* sxt = nullptr) {
   const int n = a.n;
   const double dx = 1.0 / (double)(n + 1);
   const double cdx = a.kappa / (dx * dx);
@@ -259,7 +274,7 @@ __device__ __forceinline__ void heat_forced_solve(const HeatArgs& a, double (&y)
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = lane * R + i;
-    sx[i] = r < n ? sin(M_PI * ((double)(r + 1) / (double)(n + 1))) : 0.0;
+    sx[i] = r < n ? (sxt ? sxt[r] : forcing_shape(r, n)) : 0.0;
   }
   HalfStepCoefs hc{};
   // (R = 16, d > 256: the nine-point halo would not fit the registers)
@@ -330,7 +345,7 @@ __device__ __forceinline__ void heat_forced_solve(const HeatArgs& a, double (&y)
 // proposes): d_j = g^j(lt_j) - lt_{j+1}, the forced solve from lt_j.
 template <int R>
 __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const double* lt, double* d, int64_t j,
-                                                  int lane) {
+                                                  int lane, const double* sxt = nullptr) {
   const int n = a.n;
   double y[R];
 #pragma unroll
@@ -338,7 +353,7 @@ __device__ __forceinline__ void heat_defect_slice(const HeatArgs& a, const doubl
     const int r = lane * R + i;
     y[i] = r < n ? lt[j * n + r] : 0.0;
   }
-  heat_forced_solve<R>(a, y, j, lane);
+  heat_forced_solve<R>(a, y, j, lane, sxt);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int r = lane * R + i;

@@ -148,7 +148,8 @@ struct nv_tunables {
   int chain_dense;           // 1: the d <= 256 cluster chains read every column even of banded maps
   int adv_build_form;        // advection-diffusion build: 0 auto (windows first), 1 whole grid only
   int adv_fp64_rows;         // float64 advection-diffusion window build: rows per thread, 0 (= 16), 8 or 32
-  int heat_f32_lanes;        // float32 heat three-window build: 0 auto (= 1), 1: one lane of 22 rows, 2: two of 11
+  int heat_f32_lanes;        // float32 heat three-window build: 0 auto, 1 / 2: one lane of 22 rows / two of 11,
+                             // 3 / 4: the same with two slices per packed f32x2 register
   int learned_first_form;    // iteration 0 of nv_mlp_parareal: 0 auto, 1 per-slice tcgen05 forward, 2 fused sweep
 };
 extern nv_tunables g_tune;
@@ -157,11 +158,11 @@ extern nv_tunables g_tune;
 // occupancy of `kernel` with `block` threads), or fewer when work_warps warps
 // need fewer.
 template <typename K>
-inline nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* grid_out) {
+inline nv_status persistent_grid(K kernel, int block, int64_t work_warps, int* grid_out, size_t smem = 0) {
   int sms = 152, dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  nv_status st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0),
+  nv_status st = nv_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem),
                                "occupancy query");
   if (st != NV_OK) return st;
   int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);

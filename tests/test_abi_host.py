@@ -134,7 +134,8 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(16, 4) == nvp.NV_EINVAL          # strip height is 0, 8, 16 or 32
     assert lib.nv_tune_set(16, 8) == nvp.NV_OK
     assert lib.nv_tune_set(16, 0) == nvp.NV_OK
-    assert lib.nv_tune_set(17, 3) == nvp.NV_EINVAL          # float32 heat window lanes are 0, 1 or 2
+    assert lib.nv_tune_set(17, 5) == nvp.NV_EINVAL          # float32 heat window form is 0..4
+    assert lib.nv_tune_set(17, 4) == nvp.NV_OK
     assert lib.nv_tune_set(17, 2) == nvp.NV_OK
     assert lib.nv_tune_set(17, 0) == nvp.NV_OK
     assert lib.nv_tune_set(18, 3) == nvp.NV_EINVAL          # learned iteration-0 form is 0, 1 or 2

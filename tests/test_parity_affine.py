@@ -111,27 +111,39 @@ def test_heat_window_matches_full_width(n, S, steps, form, prec):
     assert not np.any(A[:, outside])
 
 
-@pytest.mark.parametrize("n,S,steps", [(256, 1024, 10), (256, 6, 8), (200, 4, 9), (88, 3, 10)])
-def test_heat_f32_three_window_lane_shapes_agree(n, S, steps):
+@pytest.mark.parametrize("prec", ["fp32", "tf32_refine"])
+@pytest.mark.parametrize("n,S,steps", [(256, 1024, 10), (256, 6, 8), (200, 4, 9), (88, 3, 10), (90, 5, 10),
+                                       (256, 1, 10)])
+def test_heat_f32_three_window_lane_shapes_agree(n, S, steps, prec):
     """The float32 three-window build runs its 22/44/88-row windows on 1/2/4
-    lanes of 22 rows (the default, key 17 = 1) or on 2/4/8 lanes of 11 rows
-    (key 17 = 2, the float64 shape): every row is the same expression on the
-    same values, so the maps and the composed states agree bit for bit."""
+    lanes of 22 rows (key 17 = 1) or on 2/4/8 lanes of 11 rows (key 17 = 2,
+    the float64 shape), each either one slice per register or two slices per
+    packed f32x2 register (keys 3 and 4; an odd S leaves the last pair's high
+    half unused, S = 1 takes the scalar kernel): every row is the same
+    expression on the same values, so the maps and the composed states agree
+    bit for bit, also with the TF32 rounding of the stored maps (the TF32
+    scan's input).  n = 90 takes the row-by-row store (n not a multiple of
+    four floats)."""
     torch = need_gpu()
+    if prec == "tf32_refine" and n % 4:
+        pytest.skip("the TF32 scan takes d a multiple of 4")
     T = 0.1 if (n, S) == (256, 1024) else S * steps * 2.0 / (5.0 * (n + 1) ** 2)
     w = workloads.heat1d(n=n, S=S, T=T, dt=T / (S * steps))
     got = {}
-    for lanes in (1, 2):
+    for lanes in (1, 2, 3, 4):
         nvp.tune_set(6, 5)
         nvp.tune_set(17, lanes)
         try:
-            _, A, b, yT, lam = _heat(torch, w, "fp32")
+            maps, A, b, yT, lam = _heat(torch, w, prec)
+            kernel = nvp.maps_info(maps).build_kernel.decode()
         finally:
             nvp.tune_set(6, 0)
             nvp.tune_set(17, 0)
+        assert ("x2" in kernel) == (lanes >= 3 and S > 1), (lanes, kernel)
         got[lanes] = (A, b, lam)
-    for k in range(3):
-        assert np.array_equal(got[1][k], got[2][k])
+    for lanes in (2, 3, 4):
+        for k in range(3):
+            assert np.array_equal(got[1][k], got[lanes][k]), (lanes, k)
 
 
 @pytest.mark.parametrize("n,S,steps,rhs_name", [(256, 1024, 10, "heat1d"), (256, 7, 3, "heat1d"),
