@@ -365,9 +365,9 @@ def test_learned_correction_beats_float64_integration_of_few_states():
     (20 096 dependent RK4 steps per state, whatever the count), while the
     correction's defects run every slice at once (157 steps deep) and its
     chains one launch for all states: at the float64 fine solve's error level
-    (1e-11) the learned form is faster.  Measured on a GB300: 29 ms in six
-    iterations against 81 ms (256 states: 33 ms; 1024: 60 ms; 4096: 198 ms,
-    where it loses)."""
+    (1e-11) the learned form is faster.  Measured on a GB300: 11.1 ms in six
+    iterations against 80.6 ms (256 states: 16.9 ms; 1024: 52.4 ms; 4096:
+    232 ms, where it loses)."""
     torch = need_gpu()
     t = _trained(torch)
     w, r, net = t["w"], t["r"], t["net"]
