@@ -1331,8 +1331,8 @@ def run_chain3_mlp(args):
             "equal_error": equal_error,
             "equal_error_note": ("time to solution of initial states at equal final-state error: the trained "
                                  "network as the coarse map of a float64 correction (k iterations: float64 "
-                                 "defects of every slice, the correction chained over the network's tangent "
-                                 "map) against the plain float64 / float32 fine integration of the same states, "
+                                 "defects of every slice, the correction chained over the network's 6 x 6 "
+                                 "Jacobians at the learned composition) against the plain float64 / float32 fine integration of the same states, "
                                  "and the learned map alone against plain RK4 with the coarsest step that "
                                  "reaches its error; amortised = training + pair generation + the correction")}
     if rank == 0:

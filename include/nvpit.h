@@ -367,12 +367,13 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  * (bf16 activations between the layers), then bit for bit its states.  Iteration k >= 1:
  *   d_j = F_j(lambda_j) - lambda_{j+1}      float64 fine solve per slice, for
  *                                           every slice and state at once
- *   e_0 = 0, e_{j+1} = J_j e_j + d_j        J_j the network's tangent map at
- *                                           lambda_j (a forward-mode derivative
- *                                           through its layers, float32, each
- *                                           state's chain in one launch)
+ *   e_0 = 0, e_{j+1} = J_j e_j + d_j        J_j the network's Jacobian (6 x 6)
+ *                                           at slice j's state of the learned
+ *                                           composition, computed once for all
+ *                                           iterations (nv_tune_set key 19 has
+ *                                           the other forms)
  *   lambda_{j+1} <- lambda_{j+1} + e_{j+1}  written by the chain as it goes
- * i.e. an approximate Newton step on the multiple-shooting equations
+ * i.e. a simplified Newton step on the multiple-shooting equations
  * lambda_{j+1} = F_j(lambda_j), with the learned Jacobian in place of F_j's.
  * After k iterations the first k boundary states equal the float64 fine
  * solution's; the iterates converge to the float64 fine integration of every
@@ -382,8 +383,10 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  *   y0_dev       count x 6 doubles (input); yT_dev count x 6 (output)
  *   lambdas_dev  (S+1) x count x 6 doubles (output, may be NULL): every
  *                boundary state of the last iterate
- * steps->prec must be NV_FP64.  The network owns the boundary states and
- * defects ((2 S + 1) count 6 doubles): the first call for a (count, S)
+ * steps->prec must be NV_FP64.  The network owns the boundary states, defects
+ * and Jacobians ((2 S + 1) count 6 doubles, S count 36 floats, and the
+ * scratch of one chunk of at most 65536 (slice, state) items, about 0.7 GB):
+ * the first call for a (count, S)
  * synchronises `stream` and allocates them, and the first call for a schedule
  * (count, S, iters, steps, rhs parameters) captures the whole schedule into a
  * CUDA graph, later calls replay it (at small counts the learned composition's
@@ -514,8 +517,17 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          network's activations (bf16 between layers on the per-slice path,
  *          float32 in the sweep); the corrected iterates converge to the same
  *          float64 fine solution either way.
+ *   key 19: 0 (default), 1 or 2: the corrections of nv_mlp_parareal.  0: the
+ *          network's Jacobians at the learned composition (iteration 0's
+ *          states), for every slice and state at once (reverse mode through
+ *          tcgen05 GEMMs, bf16 adjoints), computed once and used by every
+ *          iteration's 6 x 6 correction chain; 2: the same Jacobians
+ *          recomputed at each previous iterate; 1: the tangent of the
+ *          network at the iterate as the chain corrects it, every state's
+ *          chain in one launch across all slices (float32).  All converge to
+ *          the same float64 fine solution.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17 and 18. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18 and 19. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Measured fused multiply-add throughput of the current device's float64

@@ -16,8 +16,9 @@
 //   kAtomic   out32[m, n] += D                     (weight gradients, split-K)
 //   kFwdTrain GELU'(z) saved (fp32, for the backward pass), h = GELU(z) stored
 //             bf16 row-major and transposed (one erf serves both)
-//   kBwd      dz = D * zin (zin = the saved GELU') stored bf16 row-major and
-//             transposed, column sums of dz added to dbias
+//   kBwd      dz = D * zin (zin = the saved GELU', row r / zdiv for row r of
+//             D) stored bf16 row-major and, unless NULL, transposed; column
+//             sums of dz added to dbias unless NULL
 //   kFwdInfer h = GELU(z) stored bf16 row-major
 #include <cuda_bf16.h>
 
@@ -39,6 +40,7 @@ enum Mode { kAtomic = 0, kFwdTrain = 1, kBwd = 2, kFwdInfer = 3 };
 
 struct Args {
   int M, K, k_per_split, mode;
+  int zdiv;            // kBwd: row r of D takes zin row r / zdiv
   float* out32;
   const float* bias;
   float* zsave;
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float gp = 0.f;
           const float h = MODE == kFwdTrain ? gelu_with_grad(z, &gp) : gelu_f(z);
           const __nv_bfloat16 hb = __float2bfloat16(h);
-          if (MODE == kFwdTrain && row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
+          if (MODE == kFwdTrain && row < a.M && a.out_bfT) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = hb;
           t[lane * 33 + i] = __bfloat162float(hb);      // exact: hb is a bf16 value
           if (MODE == kFwdTrain) t2[lane * 33 + i] = gp;
         }
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float zr[16];
 #pragma unroll
           for (int r = 0; r < 16; ++r)
-            zr[r] = a.zin[(int64_t)(wrow0 + min(h + r, nrows - 1)) * kBN + c0 + lane];
+            zr[r] = a.zin[(int64_t)((wrow0 + min(h + r, nrows - 1)) / a.zdiv) * kBN + c0 + lane];
 #pragma unroll
           for (int r = 0; r < 16; ++r) t[(h + r) * 33 + lane] = zr[r];
         }
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float dz = row < a.M ? v[i] * t[lane * 33 + i] : 0.f;
-          if (row < a.M) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = __float2bfloat16(dz);
+          if (row < a.M && a.out_bfT) a.out_bfT[(int64_t)(c0 + i) * a.M + row] = __float2bfloat16(dz);
           v[i] = dz;
         }
         __syncwarp();
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           colsum += dz;
           if (r < nrows) a.out_bf[(int64_t)(wrow0 + r) * kBN + c0 + lane] = __float2bfloat16(dz);
         }
-        atomicAdd(a.dbias + c0 + lane, colsum);
+        if (a.dbias) atomicAdd(a.dbias + c0 + lane, colsum);
         __syncwarp();
       }
     }
@@ -289,9 +291,9 @@ nv_status gemm_bf16_prepare() {
 // D[M x 256] = A[M x K] B[256 x K]^T with epilogue `mode`; splits > 1 divides K.
 nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int splits, int mode, float* out32,
                            const float* bias, float* zsave, const float* zin, void* out_bf, void* out_bfT,
-                           float* dbias, int* status, cudaStream_t s) {
-  if (M % gemm::kBM || K % gemm::kBK || splits < 1 || (K / gemm::kBK) % splits)
-    return nv_fail(NV_EINVAL, "gemm shape M=%d K=%d splits=%d not tiled", M, K, splits);
+                           float* dbias, int* status, cudaStream_t s, int zdiv) {
+  if (M % gemm::kBM || K % gemm::kBK || splits < 1 || (K / gemm::kBK) % splits || zdiv < 1)
+    return nv_fail(NV_EINVAL, "gemm shape M=%d K=%d splits=%d zdiv=%d not tiled", M, K, splits, zdiv);
   CUtensorMap ta, tb;
   nv_status st = bf16_map(&ta, A, M, K, gemm::kBM);
   if (st != NV_OK) return st;
@@ -301,6 +303,7 @@ nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int split
   a.K = K;
   a.k_per_split = K / splits;
   a.mode = mode;
+  a.zdiv = zdiv;
   a.out32 = out32;
   a.bias = bias;
   a.zsave = zsave;

@@ -151,6 +151,8 @@ struct nv_tunables {
   int heat_f32_lanes;        // float32 heat three-window build: 0 auto, 1 / 2: one lane of 22 rows / two of 11,
                              // 3 / 4: the same with two slices per packed f32x2 register
   int learned_first_form;    // iteration 0 of nv_mlp_parareal: 0 auto, 1 per-slice tcgen05 forward, 2 fused sweep
+  int learned_correction_form;  // nv_mlp_parareal corrections: 0 Jacobians of the learned composition,
+                                // 1 tangent sweep, 2 Jacobians at each previous iterate
 };
 extern nv_tunables g_tune;
 

@@ -26,7 +26,7 @@
 
 nv_status launch_gemm_bf16(const void* A, const void* B, int M, int K, int splits, int mode, float* out32,
                            const float* bias, float* zsave, const float* zin, void* out_bf, void* out_bfT,
-                           float* dbias, int* status, cudaStream_t s);
+                           float* dbias, int* status, cudaStream_t s, int zdiv = 1);
 nv_status gemm_bf16_prepare();
 
 namespace nvpit {
@@ -36,6 +36,7 @@ constexpr int H = 256, IN = 8, OUT = 8, D = 6;
 constexpr int64_t oW1 = 0, ob1 = oW1 + H * IN, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
                   ob3 = oW3 + H * H, oW4 = ob3 + H, ob4 = oW4 + OUT * H, NP = ob4 + OUT;
 constexpr int kModeAtomic = 0, kModeFwdTrain = 1, kModeBwd = 2, kModeFwdInfer = 3;
+constexpr int64_t kJacChunk = 65536;   // items per chunk of the learned Jacobians
 
 __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
@@ -373,7 +374,7 @@ __global__ void l1_fwd_kernel(const float* P, const float* X, int B, float* Z1, 
   H1[i] = hb;
   if (train) {
     Z1[i] = gp;                                   // GELU'(z), what the backward pass needs
-    H1t[(int64_t)n * B + b] = hb;
+    if (H1t) H1t[(int64_t)n * B + b] = hb;
   }
 }
 
@@ -539,6 +540,123 @@ __global__ void advance_kernel(double* lam, int64_t count, const float* out, con
   lam[i] += sd[c] * (double)out[b * OUT + c];
 }
 
+// ---- the learned Jacobians of every (slice, state) at once (reverse mode)
+// Item i = j * count + s is state s at slice j.  For the items of one chunk
+// [first, first + n): the features of lambda_j, the training-form forward
+// pass (saving GELU' of each hidden layer), then six adjoint rows per item,
+// one per output c, through layers 3, 2, 1 as tcgen05 GEMMs in their
+// backward epilogue (product x the item's saved GELU', zdiv = 6), and
+//   N_i[c][k] = dG_j(lambda)_c / dlambda_k - delta_ck
+//             = sd_c sum_u (adjoint row c at layer 1)_u W1[u][k] / sx_k.
+__global__ void items_features_kernel(const double* lam, int64_t count, int S, int64_t first, int n,
+                                      const float* sx_inv, float* X) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int64_t i = first + b;
+  const int j = (int)(i / count);
+  for (int c = 0; c < D; ++c) X[(int64_t)b * IN + c] = (float)lam[i * D + c] * sx_inv[c];
+  X[(int64_t)b * IN + 6] = (float)j / (float)S;
+  X[(int64_t)b * IN + 7] = 0.f;
+}
+
+// adjoint seeds at layer 3: row 6b + c, unit u: sd_c W4[c][u] GELU'(z3)[b][u];
+// a thread writes 8 consecutive units (one 16-byte store)
+__global__ void jac_seed_kernel(const float* P, const double* sd, const float* Z3, int n, __nv_bfloat16* A6) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * D * (H / 8)) return;
+  const int u0 = (int)(t % (H / 8)) * 8;
+  const int64_t r = t / (H / 8);
+  const int c = (int)(r % D);
+  const int64_t b = r / D;
+  const float sc = (float)sd[c];
+  const float4 z0 = *reinterpret_cast<const float4*>(Z3 + b * H + u0);
+  const float4 z1 = *reinterpret_cast<const float4*>(Z3 + b * H + u0 + 4);
+  const float* w = P + oW4 + c * H + u0;
+  const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+  __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __float2bfloat16(sc * w[q] * z[q]);
+  *reinterpret_cast<uint4*>(A6 + r * H + u0) = *reinterpret_cast<const uint4*>(v);
+}
+
+// one thread per adjoint row r (item b = r / 6, output c = r % 6):
+// N[first + b][c][k] = sum_u row_u W1[u][k] / sx_k for k < 6, with W1 / sx in
+// shared memory and the row read 8 units (16 bytes) at a time
+__global__ void __launch_bounds__(256) jac_assemble_kernel(const float* P, const float* sx_inv,
+                                                           const __nv_bfloat16* C6, int n, int64_t first,
+                                                           float* N) {
+  __shared__ float w1[H][D];
+  for (int i = threadIdx.x; i < H * D; i += blockDim.x) {
+    const int u = i / D, k = i % D;
+    w1[u][k] = P[oW1 + u * IN + k] * sx_inv[k];
+  }
+  __syncthreads();
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= (int64_t)n * D) return;
+  float acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.f;
+  const uint4* row = reinterpret_cast<const uint4*>(C6 + r * H);
+#pragma unroll 4
+  for (int q = 0; q < H / 8; ++q) {
+    const uint4 pk = row[q];
+    const __nv_bfloat16* v = reinterpret_cast<const __nv_bfloat16*>(&pk);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float a = __bfloat162float(v[e]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fmaf(a, w1[q * 8 + e][k], acc[k]);
+    }
+  }
+  float* out = N + (first * D + r) * D;            // row c of item first + r / 6
+#pragma unroll
+  for (int k = 0; k < D; k += 2) *reinterpret_cast<float2*>(out + k) = make_float2(acc[k], acc[k + 1]);
+}
+
+// The correction chain over the Jacobians, eight lanes per state (lane c < 6
+// owns component c; the group exchanges e by shuffles), one warp per CTA so
+// that the warps spread over the SMs: e_0 = 0, e_{j+1} = e_j + N_j e_j + d_j,
+// lambda_{j+1} += e_{j+1}.  N_j e_j in float32 (its rounding is relative to e,
+// which the iterations drive to zero), the sums in float64; slice j+1's row
+// of N and defect are loaded while slice j is chained.
+__global__ void __launch_bounds__(32) jac_chain_kernel(const float* N, const double* dfc, int64_t count, int S,
+                                                        double* lam) {
+  const int lane = threadIdx.x & 31, g = lane >> 3, c = lane & 7;
+  const int64_t st = (int64_t)blockIdx.x * 4 + g;
+  const bool live = st < count && c < D;
+  const int cc = c < D ? c : 0;
+  const int64_t s0 = st < count ? st : 0;
+  double e = 0.0;
+  float nrow[D] = {};
+  double d = 0.0;
+  auto load = [&](int j, float (&nr)[D], double& dd) {
+    const int64_t i = (int64_t)j * count + s0;
+    const float2* src = reinterpret_cast<const float2*>(N + (i * D + cc) * D);
+#pragma unroll
+    for (int k = 0; k < D; k += 2) {
+      const float2 v = src[k / 2];
+      nr[k] = v.x;
+      nr[k + 1] = v.y;
+    }
+    dd = dfc[i * D + cc];
+  };
+  if (live) load(0, nrow, d);
+  for (int j = 0; j < S; ++j) {
+    float nnext[D] = {};
+    double dnext = 0.0;
+    if (live && j + 1 < S) load(j + 1, nnext, dnext);
+    const float ef = (float)e;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) v = fmaf(nrow[k], __shfl_sync(0xffffffffu, ef, (lane & ~7) + k), v);
+    e = e + (double)v + d;
+    if (live) lam[((int64_t)(j + 1) * count + st) * D + c] += e;
+#pragma unroll
+    for (int k = 0; k < D; ++k) nrow[k] = nnext[k];
+    d = dnext;
+  }
+}
+
 // per-slice relative error of the learned map against float64 end states
 __global__ void val_err_kernel(const double* y0, const double* ye, const float* out, const double* sd,
                                int64_t n, double* num, double* den) {
@@ -590,10 +708,12 @@ struct nv_mlp {
   // defects, sized for (pr_count, pr_S), and the captured graph of its whole
   // schedule for the key below
   double *pr_lam, *pr_dfc;
-  int64_t pr_count;
+  float *pr_N, *pr_X, *pr_Z;                  // Jacobians (S x count x 36); a chunk's features, GELU'
+  __nv_bfloat16 *pr_H, *pr_A6, *pr_B6;        // a chunk's activations and adjoint rows
+  int64_t pr_count, pr_chunk;
   int pr_S;
   cudaGraphExec_t pr_graph;
-  int pr_iters, pr_rk4, pr_form;
+  int pr_iters, pr_rk4, pr_form, pr_corr;
   int64_t pr_m;
   double pr_h, pr_p[3];
 };
@@ -622,11 +742,13 @@ static void mlp_free_parareal(nv_mlp* m) {
     cudaGraphExecDestroy(m->pr_graph);
     m->pr_graph = nullptr;
   }
-  void* bufs[] = {m->pr_lam, m->pr_dfc};
+  void* bufs[] = {m->pr_lam, m->pr_dfc, m->pr_N, m->pr_X, m->pr_Z, m->pr_H, m->pr_A6, m->pr_B6};
   for (void* b : bufs)
     if (b) cudaFree(b);
   m->pr_lam = m->pr_dfc = nullptr;
-  m->pr_count = 0;
+  m->pr_N = m->pr_X = m->pr_Z = nullptr;
+  m->pr_H = m->pr_A6 = m->pr_B6 = nullptr;
+  m->pr_count = m->pr_chunk = 0;
   m->pr_S = 0;
 }
 
@@ -1006,6 +1128,44 @@ static nv_status run_learned_sweep(const nv_mlp* m, bool tangent, int S, int64_t
 #undef NVPIT_SWEEP
 }
 
+// N_i = J_i - I for every item i = j * count + s (state s at slice j) of the
+// iterate in lam, in chunks of m->pr_chunk items.
+static nv_status learned_jacobians(nv_mlp* m, int S, int64_t count, const double* lam, cudaStream_t s) {
+  const int64_t items = (int64_t)S * count, chunk = m->pr_chunk;
+  float* Z1 = m->pr_Z;
+  float* Z2 = Z1 + chunk * H;
+  float* Z3 = Z2 + chunk * H;
+  __nv_bfloat16* H1 = m->pr_H;
+  __nv_bfloat16* H2 = H1 + chunk * H;
+  __nv_bfloat16* H3 = H2 + chunk * H;
+  nv_status st = NV_OK;
+  for (int64_t first = 0; first < items && st == NV_OK; first += chunk) {
+    const int n = (int)std::min<int64_t>(chunk, items - first);   // a multiple of 128
+    items_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lam, count, S, first, n, m->sx_inv, m->pr_X);
+    l1_fwd_kernel<<<(unsigned)(((int64_t)n * H + 255) / 256), 256, 0, s>>>(m->P, m->pr_X, n, Z1, H1, nullptr, 1);
+    if ((st = nv_cuda_check(cudaGetLastError(), "Jacobian features and layer 1")) != NV_OK) break;
+    if ((st = launch_gemm_bf16(H1, m->W2b, n, H, 1, kModeFwdTrain, nullptr, m->P + ob2, Z2, nullptr, H2, nullptr,
+                               nullptr, m->status, s)) != NV_OK)
+      break;
+    if ((st = launch_gemm_bf16(H2, m->W3b, n, H, 1, kModeFwdTrain, nullptr, m->P + ob3, Z3, nullptr, H3, nullptr,
+                               nullptr, m->status, s)) != NV_OK)
+      break;
+    jac_seed_kernel<<<(unsigned)(((int64_t)n * D * (H / 8) + 255) / 256), 256, 0, s>>>(m->P, m->sd, Z3, n,
+                                                                                        m->pr_A6);
+    if ((st = nv_cuda_check(cudaGetLastError(), "jac_seed_kernel launch")) != NV_OK) break;
+    if ((st = launch_gemm_bf16(m->pr_A6, m->W3t, D * n, H, 1, kModeBwd, nullptr, nullptr, nullptr, Z2, m->pr_B6,
+                               nullptr, nullptr, m->status, s, D)) != NV_OK)
+      break;
+    if ((st = launch_gemm_bf16(m->pr_B6, m->W2t, D * n, H, 1, kModeBwd, nullptr, nullptr, nullptr, Z1, m->pr_A6,
+                               nullptr, nullptr, m->status, s, D)) != NV_OK)
+      break;
+    jac_assemble_kernel<<<(unsigned)(((int64_t)n * D + 255) / 256), 256, 0, s>>>(m->P, m->sx_inv, m->pr_A6, n,
+                                                                               first, m->pr_N);
+    st = nv_cuda_check(cudaGetLastError(), "jac_assemble_kernel launch");
+  }
+  return st;
+}
+
 // Iteration 0 of the learned correction through the fused sweep (float32
 // activations, one launch) rather than the per-slice tcgen05 forward of
 // nv_mlp_compose (bf16 activations, a few launches per slice): nv_tune_set
@@ -1050,8 +1210,19 @@ static nv_status parareal_schedule(nv_mlp* m, const RhsParams& pp, int64_t mstep
     slice_defect_kernel<RhsChain3<double>><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pp, h, msteps, rk4, S,
                                                                                          count, lam, dfc);
     if ((st = nv_cuda_check(cudaGetLastError(), "slice_defect_kernel launch")) != NV_OK) break;
-    // the correction chain over the tangent maps, every state's chain in one launch
-    st = run_learned_sweep(m, true, S, count, lam, dfc, sms, s);
+    const int corr = g_tune.learned_correction_form;
+    if (corr == 1) {
+      // the correction chain over the tangent maps at the corrected iterate, every
+      // state's chain in one launch
+      st = run_learned_sweep(m, true, S, count, lam, dfc, sms, s);
+    } else {
+      // the Jacobians, every (slice, state) at once: at the previous iterate
+      // (corr = 2), or once, at the learned composition, for all iterations
+      if (corr == 2 || k == 1) st = learned_jacobians(m, S, count, lam, s);
+      if (st != NV_OK) break;
+      jac_chain_kernel<<<(unsigned)((count + 3) / 4), 32, 0, s>>>(m->pr_N, dfc, count, S, lam);
+      st = nv_cuda_check(cudaGetLastError(), "jac_chain_kernel launch");
+    }
   }
   return st;
 }
@@ -1074,9 +1245,17 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
   if (m->pr_count != count || m->pr_S != S) {     // library-owned buffers for this shape
     if ((st = nv_cuda_check(cudaStreamSynchronize(s), "synchronise")) != NV_OK) return st;
     mlp_free_parareal(m);
+    const int64_t items = (int64_t)S * count, chunk = std::min<int64_t>(items, kJacChunk);
+    const size_t f = sizeof(float), bf = sizeof(__nv_bfloat16);
     struct { void** p; size_t bytes; } req[] = {
         {(void**)&m->pr_lam, sizeof(double) * (size_t)(S + 1) * per},
-        {(void**)&m->pr_dfc, sizeof(double) * (size_t)S * per}};
+        {(void**)&m->pr_dfc, sizeof(double) * (size_t)S * per},
+        {(void**)&m->pr_N, f * (size_t)items * D * D},
+        {(void**)&m->pr_X, f * (size_t)chunk * IN},
+        {(void**)&m->pr_Z, f * 3 * (size_t)chunk * H},
+        {(void**)&m->pr_H, bf * 3 * (size_t)chunk * H},
+        {(void**)&m->pr_A6, bf * D * (size_t)chunk * H},
+        {(void**)&m->pr_B6, bf * D * (size_t)chunk * H}};
     for (auto& r : req) {
       if ((st = nv_cuda_check(cudaMalloc(r.p, r.bytes), "learned correction buffers")) != NV_OK) {
         mlp_free_parareal(m);
@@ -1084,14 +1263,16 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
       }
     }
     m->pr_count = count;
+    m->pr_chunk = chunk;
     m->pr_S = S;
   }
   // the whole schedule is captured once per shape and replayed: at small
   // counts the learned composition's kernels are launch-bound when issued
   // one by one
   const int rk4 = steps->scheme == NV_RK4;
-  const int form = g_tune.learned_first_form;
+  const int form = g_tune.learned_first_form, corr = g_tune.learned_correction_form;
   const bool same = m->pr_graph && m->pr_iters == iters && m->pr_rk4 == rk4 && m->pr_form == form &&
+                    m->pr_corr == corr &&
                     m->pr_m == msteps &&
                     m->pr_h == h && m->pr_p[0] == pp.p[0] && m->pr_p[1] == pp.p[1] && m->pr_p[2] == pp.p[2];
   if (!same) {
@@ -1119,6 +1300,7 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
     m->pr_iters = iters;
     m->pr_rk4 = rk4;
     m->pr_form = form;
+    m->pr_corr = corr;
     m->pr_m = msteps;
     m->pr_h = h;
     for (int i = 0; i < 3; ++i) m->pr_p[i] = pp.p[i];
