@@ -11,6 +11,12 @@
 // CUDA cores.  Adam keeps float32 master weights and refreshes the bf16 copies
 // (row-major for the forward GEMM, transposed for the backward one).
 //
+// The trained network is also the coarse map of a float64 residual
+// correction (the parareal combination of the Conclusion, nv_mlp_parareal):
+// float64 defects of every slice at once, and a correction chained over the
+// network's 6 x 6 Jacobians, which come for every (slice, state) at once in
+// reverse mode through the same GEMMs.
+//
 // Parameter vector (float32, [out][in] weights):
 //   W1 256x8 (column 7 zero) | b1 256 | W2 256x256 | b2 256 | W3 256x256 | b3 256
 //   | W4 8x256 (rows 6, 7 zero) | b4 8
