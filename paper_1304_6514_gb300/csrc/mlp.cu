@@ -171,7 +171,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   float* dB = dA + NS * H;
   __shared__ float xin[NS][IN], xtan[NS][D];
   __shared__ float red[NS][kTanThreads / 32][D];
-  __shared__ float part[NS][D];
+  __shared__ float part[2][NS][D];           // the halves of W4 v by source CTA
   __shared__ double e[NS][D];
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
@@ -182,14 +182,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   float* dA_p = cl.map_shared_rank(dA, rank ^ 1u);
   float* hB_p = cl.map_shared_rank(hB, rank ^ 1u);
   float* dB_p = cl.map_shared_rank(dB, rank ^ 1u);
-  float* part_p = cl.map_shared_rank(&part[0][0], rank ^ 1u);
-  double* e_p = cl.map_shared_rank(&e[0][0], rank ^ 1u);
+  float* part_p = cl.map_shared_rank(&part[0][0][0], rank ^ 1u);
   for (int i = t; i < H * kTanThreads; i += kTanThreads) {
     const int k = i / kTanThreads, c = i - k * kTanThreads;
     W2s[i] = W2t[k * H + kTanThreads * rank + c];
     W3s[i] = W3t[k * H + kTanThreads * rank + c];
   }
-  if (t < NS * D) e[t / D][t % D] = 0.0;
+  // tangent mode: the correction e (from 0); forward mode: the state itself,
+  // kept on chip from slice to slice (both CTAs hold it)
+  if (t < NS * D) e[t / D][t % D] = TANGENT ? 0.0 : lam[(s0 + t / D) * D + t % D];
   float w1[IN], w4[D];
 #pragma unroll
   for (int k = 0; k < IN; ++k) w1[k] = P[oW1 + u * IN + k];
@@ -201,8 +202,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
     const double* lj = lam + (size_t)j * count * D;
     if (t < NS * D) {
       const int q = t / D, c = t % D;
-      xin[q][c] = (float)lj[(s0 + q) * D + c] * sx_inv[c];
-      xtan[q][c] = (float)e[q][c] * sx_inv[c];
+      if constexpr (TANGENT) {
+        xin[q][c] = (float)lj[(s0 + q) * D + c] * sx_inv[c];
+        xtan[q][c] = (float)e[q][c] * sx_inv[c];
+      } else {
+        xin[q][c] = (float)e[q][c] * sx_inv[c];
+      }
     }
     if (t < NS) {
       xin[t][6] = (float)j / (float)S;
@@ -281,29 +286,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
       }
     }
     __syncthreads();
-    if (t < NS * D) {                          // this CTA's half of W4 v
+    if (t < NS * D) {                          // this CTA's half of W4 v, to both CTAs
       const int q = t / D, c = t % D;
       float o = 0.f;
 #pragma unroll
       for (int wv = 0; wv < kTanThreads / 32; ++wv) o += red[q][wv][c];
-      part[q][c] = o;
+      part[rank][q][c] = o;
+      part_p[(rank * NS + q) * D + c] = o;
     }
     cl.sync();
-    if (rank == 0 && t < NS * D) {
+    // both CTAs take the same update from the two halves (rank 0's first), so
+    // each keeps e (forward mode: the state) without a further cluster
+    // barrier; rank 0 writes lambda
+    if (t < NS * D) {
       const int q = t / D, c = t % D;
-      const float o = part[q][c] + part_p[q * D + c];
+      const float o = part[0][q][c] + part[1][q][c];
       const int64_t i = (s0 + q) * D + c;
       double* lj1 = lam + (size_t)(j + 1) * count * D;
-      if constexpr (TANGENT) {                 // e_{j+1} = e_j + sd dout + d_j, to both CTAs
+      if constexpr (TANGENT) {                 // e_{j+1} = e_j + sd dout + d_j
         const double en = e[q][c] + sd[c] * (double)o + dfc[(size_t)j * count * D + i];
         e[q][c] = en;
-        e_p[q * D + c] = en;
-        lj1[i] += en;
+        if (rank == 0) lj1[i] += en;
       } else {                                 // lambda_{j+1} = lambda_j + sd (W4 h3 + b4)
-        lj1[i] = lj[i] + sd[c] * (double)(o + P[ob4 + c]);
+        const double nv = e[q][c] + sd[c] * (double)(o + P[ob4 + c]);
+        e[q][c] = nv;
+        if (rank == 0) lj1[i] = nv;
       }
     }
-    cl.sync();
+    // the tangent's next slice reads lambda_{j+1} as rank 0 has just corrected it
+    if constexpr (TANGENT) cl.sync();
   }
 }
 
@@ -624,7 +635,8 @@ __global__ void __launch_bounds__(256) jac_assemble_kernel(const float* P, const
 // that the warps spread over the SMs: e_0 = 0, e_{j+1} = e_j + N_j e_j + d_j,
 // lambda_{j+1} += e_{j+1}.  N_j e_j in float32 (its rounding is relative to e,
 // which the iterations drive to zero), the sums in float64; slice j+1's row
-// of N and defect are loaded while slice j is chained.
+// of N, defect and state are loaded while slice j is chained (each state is
+// read before this thread writes it: slice j+1's row is not slice j's).
 __global__ void __launch_bounds__(32) jac_chain_kernel(const float* N, const double* dfc, int64_t count, int S,
                                                         double* lam) {
   const int lane = threadIdx.x & 31, g = lane >> 3, c = lane & 7;
@@ -634,8 +646,8 @@ __global__ void __launch_bounds__(32) jac_chain_kernel(const float* N, const dou
   const int64_t s0 = st < count ? st : 0;
   double e = 0.0;
   float nrow[D] = {};
-  double d = 0.0;
-  auto load = [&](int j, float (&nr)[D], double& dd) {
+  double d = 0.0, l = 0.0;
+  auto load = [&](int j, float (&nr)[D], double& dd, double& ll) {
     const int64_t i = (int64_t)j * count + s0;
     const float2* src = reinterpret_cast<const float2*>(N + (i * D + cc) * D);
 #pragma unroll
@@ -645,21 +657,23 @@ __global__ void __launch_bounds__(32) jac_chain_kernel(const float* N, const dou
       nr[k + 1] = v.y;
     }
     dd = dfc[i * D + cc];
+    ll = lam[(i + count) * D + cc];
   };
-  if (live) load(0, nrow, d);
+  if (live) load(0, nrow, d, l);
   for (int j = 0; j < S; ++j) {
     float nnext[D] = {};
-    double dnext = 0.0;
-    if (live && j + 1 < S) load(j + 1, nnext, dnext);
+    double dnext = 0.0, lnext = 0.0;
+    if (live && j + 1 < S) load(j + 1, nnext, dnext, lnext);
     const float ef = (float)e;
     float v = 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k) v = fmaf(nrow[k], __shfl_sync(0xffffffffu, ef, (lane & ~7) + k), v);
     e = e + (double)v + d;
-    if (live) lam[((int64_t)(j + 1) * count + st) * D + c] += e;
+    if (live) lam[((int64_t)(j + 1) * count + st) * D + c] = l + e;
 #pragma unroll
     for (int k = 0; k < D; ++k) nrow[k] = nnext[k];
     d = dnext;
+    l = lnext;
   }
 }
 
