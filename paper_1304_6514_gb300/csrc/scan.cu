@@ -22,9 +22,12 @@
 // column-major in HBM, which is exactly the K-major layout of the B operand;
 // TMA streams it in K-slabs of 32 (256 x 128 B boxes, SWIZZLE_128B) through a
 // three-stage mbarrier ring (the most that fits beside the 128 KB A operand),
-// the next map's first slabs streaming in during the epilogue.  One thread issues tcgen05.mma (kind::tf32,
-// M=128, N=256, K=8) into a 128 x 256 float32 accumulator in tensor memory;
-// four warps read it back with tcgen05.ld and write the next A operand (or,
+// one warp issuing the copies continuously across the products.  One thread
+// of another warp issues tcgen05.mma (kind::tf32, M=128, N=256, K=8) into one
+// of two 128 x 256 float32 accumulators in tensor memory, alternating by
+// product; four warps read the finished one back with tcgen05.ld and write
+// the next A operand slab by slab, each slab released to the MMAs on its own
+// mbarrier, so the next product starts while the epilogue runs (or,
 // after the last slice, the block total to global memory).  Every mbarrier
 // wait is bounded (1 s of globaltimer), after which the kernel records
 // NV_ETIMEOUT, waits (bounded) for its copies in flight, frees its tensor
@@ -49,7 +52,7 @@ constexpr int kStages = 3;                // 128 KB A operand + 96 KB of B stage
 constexpr int kMaxSlabs = 8;            // d <= 256
 constexpr int kSmemA = kMaxSlabs * kSlabBytesA;          // 128 KB
 constexpr int kSmemB = kStages * kSlabBytesB;            // 96 KB
-constexpr int kSmemBytes = kSmemA + kSmemB + 128 + 1024; // + barriers + alignment slack
+constexpr int kSmemBytes = kSmemA + kSmemB + 256 + 1024; // + barriers + alignment slack
 
 struct ScanArgs {
   int n, S, L, nblocks, nslabs;
@@ -62,7 +65,18 @@ __device__ __forceinline__ float4* arow_chunk(uint8_t* aop, int s, int m, int ch
   return reinterpret_cast<float4*>(aop + s * kSlabBytesA + m * 128 + ((chunk ^ (m & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Warp roles of the block-total kernel: warps 0-3 read the accumulator back
+// (tcgen05.ld reaches TMEM lanes 32w .. 32w+31 from warp w) and write the
+// next A operand or the block total; warp 4 streams the maps' K-slabs with
+// TMA; warp 5 issues the MMAs.  The accumulator alternates between two TMEM
+// buffers of 256 columns, so product k+1 accumulates into one while the
+// epilogue of product k reads the other, and it reads A slab s as soon as the
+// epilogue has written that slab (one mbarrier per slab): the epilogue and
+// the B stream overlap the MMAs instead of following them.
+constexpr int kEpiWarps = 4, kTmaWarp = 4, kMmaWarp = 5;
+constexpr int kScanThreads = 32 * (kMmaWarp + 1);
+
+__global__ void __launch_bounds__(kScanThreads, 1)
     scan_block_totals_kernel(const __grid_constant__ CUtensorMap tmB, ScanArgs a) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -70,35 +84,37 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* bst = base + kSmemA;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + kSmemA + kSmemB);
   uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* done = empty + kStages;         // [2]: product into accumulator buffer b complete
+  uint64_t* aready = done + 2;              // [kMaxSlabs]: the epilogue wrote A slab s
+  uint64_t* tfree = aready + kMaxSlabs;     // [2]: the epilogue read accumulator buffer b
+  uint64_t* fin = tfree + 2;                // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int h = blockIdx.x, blk = blockIdx.y;
-  const int n = a.n;
+  const int n = a.n, ns = a.nslabs;
   const int j0 = blk * a.L;
   const int len = min(a.L, a.S - j0);
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * kN);
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&done[b], 1);
+      mbar_init(&tfree[b], kEpiWarps);
+    }
+    for (int s = 0; s < kMaxSlabs; ++s) mbar_init(&aready[s], kEpiWarps);
+    mbar_init(fin, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // A operand = rows [128h, 128h+128) of the identity (zero beyond d)
-  {
-    const int m = tid;                      // 128 threads, one row each
+  if (warp < kEpiWarps) {
+    const int m = tid;                      // one row per epilogue thread
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s = 0; s < kMaxSlabs; ++s)
       for (int c = 0; c < 8; ++c) *arow_chunk(aop, s, m, c) = z;
@@ -114,116 +130,105 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_tf32(kRows, kN);
-  const uint32_t aop_addr = smem_u32(aop), bst_addr = smem_u32(bst);
+  const int total = len * ns;               // K-slabs of B over all products of this block
+  volatile int* vabort = &abort_flag;
+  int issued = 0;                           // the TMA lane: slabs whose copies were issued
 
-  uint32_t fph[kStages] = {}, eph[kStages] = {}, dph = 0;
-  bool pending[kStages] = {};
-  bool ok = true;
-  bool prefetched = false;                  // the first slabs of this step's map are already in flight
-  for (int step = 0; step < len && !abort_flag; ++step) {
-    const int j = j0 + len - 1 - step;      // suffix product: last slice of the block first
-    if (tid == 0) {
-      const int ns = a.nslabs;
-      if (!prefetched)
-        for (int s = 0; s < min(kStages, ns); ++s) {
-          mbar_expect_tx(&full[s], kSlabBytesB);
-          tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j);
-          pending[s] = true;
-        }
-      prefetched = false;
-      for (int s = 0; s < ns && ok; ++s) {
-        const int st = s % kStages;
-        ok = mbar_wait(&full[st], fph[st]);
-        fph[st] ^= 1;
-        pending[st] = false;
+  if (warp == kTmaWarp && lane == 0) {
+    // slab g of the stream is slab s = g % ns of product k = g / ns (map j0 + len - 1 - k:
+    // the suffix product runs from the block's last slice down)
+    for (; issued < total && !*vabort; ++issued) {
+      const int g = issued, st = g % kStages;
+      if (g >= kStages && !mbar_wait(&empty[st], (uint32_t)(((g / kStages) - 1) & 1))) {
+        *vabort = 1;
+        break;
+      }
+      const int k = g / ns, s = g - k * ns;
+      mbar_expect_tx(&full[st], kSlabBytesB);
+      tma_load_3d(bst + st * kSlabBytesB, &tmB, &full[st], s * kSlab, 1, j0 + len - 1 - k);
+    }
+  } else if (warp == kMmaWarp && lane == 0) {
+    const uint32_t idesc = idesc_tf32(kRows, kN);
+    const uint32_t aop_addr = smem_u32(aop), bst_addr = smem_u32(bst);
+    bool ok = true;
+    int g = 0;
+    for (int k = 0; k < len && ok; ++k) {
+      const uint32_t d = tmem + (uint32_t)((k & 1) * kN);
+      if (k >= 2) {                         // the epilogue of product k-2 has read buffer k & 1
+        ok = mbar_wait(&tfree[k & 1], (uint32_t)(((k - 2) >> 1) & 1));
         if (!ok) break;
+        fence_after();
+      }
+      for (int s = 0; s < ns; ++s, ++g) {
+        const int st = g % kStages;
+        ok = mbar_wait(&full[st], (uint32_t)((g / kStages) & 1));
+        if (ok && k >= 1) ok = mbar_wait(&aready[s], (uint32_t)((k - 1) & 1));
+        if (!ok || *vabort) {
+          ok = false;
+          break;
+        }
         fence_after();
 #pragma unroll
         for (int kk = 0; kk < kSlab / 8; ++kk) {
           const uint64_t ad = sdesc_k_sw128(aop_addr + s * kSlabBytesA + kk * 32);
           const uint64_t bd = sdesc_k_sw128(bst_addr + st * kSlabBytesB + kk * 32);
-          mma_tf32(tmem, ad, bd, idesc, (s | kk) != 0);
+          mma_tf32(d, ad, bd, idesc, (s | kk) != 0);
         }
-        mma_commit(&empty[st]);
-        if (s + kStages < ns) {
-          ok = mbar_wait(&empty[st], eph[st]);
-          eph[st] ^= 1;
-          if (!ok) break;
-          mbar_expect_tx(&full[st], kSlabBytesB);
-          tma_load_3d(bst + st * kSlabBytesB, &tmB, &full[st], (s + kStages) * kSlab, 1, j);
-          pending[st] = true;
-        }
+        mma_commit(&empty[st]);             // the stage is free once these MMAs are done
       }
-      if (ok) {
-        mma_commit(done);
-        // the last stages' release arrivals complete with the MMAs
-        for (int s = max(0, ns - kStages); s < ns && ok; ++s) {
-          const int st = s % kStages;
-          ok = mbar_wait(&empty[st], eph[st]);
-          eph[st] ^= 1;
-        }
-        // every MMA of this step has read its B slabs: the first slabs of the
-        // next map stream in while the epilogue turns the accumulator into
-        // the next A operand (stage s % kStages again takes slab s)
-        if (ok && step + 1 < len) {
-          for (int s = 0; s < min(kStages, ns); ++s) {
-            mbar_expect_tx(&full[s], kSlabBytesB);
-            tma_load_3d(bst + s * kSlabBytesB, &tmB, &full[s], s * kSlab, 1, j - 1);
-            pending[s] = true;
-          }
-          prefetched = true;
-        }
-      }
-      if (!ok) abort_flag = 1;
+      if (ok) mma_commit(&done[k & 1]);
     }
-    __syncthreads();
-    if (abort_flag) break;
-    if (!mbar_wait(done, dph)) {
-      abort_flag = 1;
-    }
-    dph ^= 1;
-    __syncthreads();
-    if (abort_flag) break;
-    fence_after();
-    // epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w+31
+    if (!ok) *vabort = 1;
+    mma_commit(fin);                        // completes with every MMA issued above
+    mbar_wait(fin, 0);
+  } else if (warp < kEpiWarps) {
+    // warp w owns accumulator rows (TMEM lanes) 32w .. 32w+31
     const int m = warp * 32 + lane;
     const int gm = kRows * h + m;
-    const bool last = (step == len - 1);
-    for (int s = 0; s < a.nslabs; ++s) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kSlab), v);
-      if (!last) {
+    for (int k = 0; k < len; ++k) {
+      if (!mbar_wait(&done[k & 1], (uint32_t)((k >> 1) & 1))) {
+        *vabort = 1;
+        break;
+      }
+      if (*vabort) break;
+      fence_after();
+      const uint32_t t = tmem + (uint32_t)((k & 1) * kN) + ((uint32_t)(warp * 32) << 16);
+      const bool last = (k == len - 1);
+      for (int s = 0; s < ns; ++s) {
+        float v[32];
+        tmem_ld32(t + (uint32_t)(s * kSlab), v);
+        if (!last) {                          // slab s of the next product's A operand
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          *arow_chunk(aop, s, m, c) = make_float4(round_tf32(v[4 * c]), round_tf32(v[4 * c + 1]),
-                                                  round_tf32(v[4 * c + 2]), round_tf32(v[4 * c + 3]));
-      } else if (gm < n) {
-        float* Rb = a.R + (int64_t)blk * n * n;
+          for (int c = 0; c < 8; ++c)
+            *arow_chunk(aop, s, m, c) = make_float4(round_tf32(v[4 * c]), round_tf32(v[4 * c + 1]),
+                                                    round_tf32(v[4 * c + 2]), round_tf32(v[4 * c + 3]));
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&aready[s]);
+        } else if (gm < n) {
+          float* Rb = a.R + (int64_t)blk * n * n;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = s * kSlab + i;
-          if (col < n) Rb[(int64_t)col * n + gm] = v[i];
+          for (int i = 0; i < 32; ++i) {
+            const int col = s * kSlab + i;
+            if (col < n) Rb[(int64_t)col * n + gm] = v[i];
+          }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[k & 1]);   // the MMAs of product k+2 may overwrite it
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before();
-    __syncthreads();
-    fence_after();
   }
-  if (abort_flag) {
-    if (tid == 0) {
-      record_status(a.status, NV_ETIMEOUT);
-      for (int st = 0; st < kStages; ++st)   // let copies in flight land (bounded)
-        if (pending[st]) mbar_wait(&full[st], fph[st]);
-    }
-    __syncthreads();
+  __syncthreads();
+  if (*vabort) {
+    if (tid == 0) record_status(a.status, NV_ETIMEOUT);
+    if (warp == kTmaWarp && lane == 0)      // let copies in flight land (bounded)
+      for (int g = max(0, issued - kStages); g < issued; ++g)
+        mbar_wait(&full[g % kStages], (uint32_t)((g / kStages) & 1));
   }
   fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN) : "memory");
+  if (warp == 0) tmem_dealloc(tmem, 2 * kN);
 }
 
 }  // namespace tc
@@ -347,7 +352,7 @@ nv_status launch_scan_refine(nv_maps* M, const double* y0, double* yT, double* l
                      "scan smem attribute");
   if (st != NV_OK) return st;
   const int halves = (n + tc::kRows - 1) / tc::kRows;
-  tc::scan_block_totals_kernel<<<dim3(halves, B), 128, tc::kSmemBytes, s>>>(tmap, sa);
+  tc::scan_block_totals_kernel<<<dim3(halves, B), tc::kScanThreads, tc::kSmemBytes, s>>>(tmap, sa);
   st = nv_cuda_check(cudaGetLastError(), "scan_block_totals_kernel launch");
   if (st != NV_OK) return st;
 
