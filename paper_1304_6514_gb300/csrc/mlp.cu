@@ -634,46 +634,48 @@ __global__ void __launch_bounds__(256) jac_assemble_kernel(const float* P, const
 // owns component c; the group exchanges e by shuffles), one warp per CTA so
 // that the warps spread over the SMs: e_0 = 0, e_{j+1} = e_j + N_j e_j + d_j,
 // lambda_{j+1} += e_{j+1}.  N_j e_j in float32 (its rounding is relative to e,
-// which the iterations drive to zero), the sums in float64; slice j+1's row
-// of N, defect and state are loaded while slice j is chained (each state is
-// read before this thread writes it: slice j+1's row is not slice j's).
+// which the iterations drive to zero), the sums in float64.  The rows of N,
+// defects and states of the next four slices are in flight while slice j is
+// chained (the state of slice j+4 is read before this thread writes it).
 __global__ void __launch_bounds__(32) jac_chain_kernel(const float* N, const double* dfc, int64_t count, int S,
                                                         double* lam) {
+  constexpr int P = 4;                                  // slices loaded ahead
   const int lane = threadIdx.x & 31, g = lane >> 3, c = lane & 7;
   const int64_t st = (int64_t)blockIdx.x * 4 + g;
   const bool live = st < count && c < D;
   const int cc = c < D ? c : 0;
   const int64_t s0 = st < count ? st : 0;
-  double e = 0.0;
-  float nrow[D] = {};
-  double d = 0.0, l = 0.0;
-  auto load = [&](int j, float (&nr)[D], double& dd, double& ll) {
+  float nr[P][D] = {};
+  double dd[P] = {}, ll[P] = {};
+  auto load = [&](int j, float (&n)[D], double& d, double& l) {
+    if (!live || j >= S) return;
     const int64_t i = (int64_t)j * count + s0;
     const float2* src = reinterpret_cast<const float2*>(N + (i * D + cc) * D);
 #pragma unroll
     for (int k = 0; k < D; k += 2) {
       const float2 v = src[k / 2];
-      nr[k] = v.x;
-      nr[k + 1] = v.y;
+      n[k] = v.x;
+      n[k + 1] = v.y;
     }
-    dd = dfc[i * D + cc];
-    ll = lam[(i + count) * D + cc];
+    d = dfc[i * D + cc];
+    l = lam[(i + count) * D + cc];
   };
-  if (live) load(0, nrow, d, l);
-  for (int j = 0; j < S; ++j) {
-    float nnext[D] = {};
-    double dnext = 0.0, lnext = 0.0;
-    if (live && j + 1 < S) load(j + 1, nnext, dnext, lnext);
-    const float ef = (float)e;
-    float v = 0.f;
 #pragma unroll
-    for (int k = 0; k < D; ++k) v = fmaf(nrow[k], __shfl_sync(0xffffffffu, ef, (lane & ~7) + k), v);
-    e = e + (double)v + d;
-    if (live) lam[((int64_t)(j + 1) * count + st) * D + c] = l + e;
+  for (int u = 0; u < P; ++u) load(u, nr[u], dd[u], ll[u]);
+  double e = 0.0;
+  for (int j0 = 0; j0 < S; j0 += P) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) nrow[k] = nnext[k];
-    d = dnext;
-    l = lnext;
+    for (int u = 0; u < P; ++u) {                       // slot u holds slice j0 + u
+      const int j = j0 + u;
+      if (j >= S) break;                                // uniform over the warp
+      const float ef = (float)e;
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) v = fmaf(nr[u][k], __shfl_sync(0xffffffffu, ef, (lane & ~7) + k), v);
+      e = e + (double)v + dd[u];
+      if (live) lam[((int64_t)(j + 1) * count + st) * D + c] = ll[u] + e;
+      load(j + P, nr[u], dd[u], ll[u]);                 // slice j + P into the freed slot
+    }
   }
 }
 
