@@ -485,7 +485,9 @@ class MLP:
                                              _ptr(yT), _stream(stream)))
 
     def parareal(self, rhs_, t0, T, S, steps_, iters, y0, yT, lambdas=None, stream=None):
-        """Parareal with this network as the coarse propagator (nv_mlp_parareal)."""
+        """nv_mlp_parareal: this network as the coarse map of a float64 residual
+        correction (float64 defects of every slice, a correction chained over
+        the network's Jacobians), `iters` iterations."""
         _check(load_library().nv_mlp_parareal(self.handle, byref(rhs_), t0, T, S, byref(steps_), iters,
                                               y0.shape[0], _ptr(y0), _ptr(yT),
                                               _ptr(lambdas) if lambdas is not None else None, _stream(stream)))

@@ -1200,7 +1200,8 @@ static bool learned_first_fused(int64_t count, int sms) {
 
 // The schedule of the learned correction on the library-owned buffers, with
 // lambda_0 already in pr_lam: the learned composition, then `iters` rounds of
-// defects of every slice and the correction chain over the tangent maps.
+// defects of every slice and the correction chain over the network's
+// Jacobians (nv_tune_set key 19 for the other forms).
 static nv_status parareal_schedule(nv_mlp* m, const RhsParams& pp, int64_t msteps, double h, int rk4, int S,
                                    int iters, int64_t count, cudaStream_t s) {
   int dev = 0, sms = 0;
