@@ -142,9 +142,10 @@ __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, 
 // grid-wide step.  A cluster of two CTAs takes NS states: CTA r owns hidden
 // units 128 r .. 128 r + 127 (thread t unit 128 r + t) and keeps its halves of
 // the bf16 layer-2 and layer-3 weights (W2^T and W3^T columns, 2 x 64 KB) in
-// shared memory for the whole launch; each layer's outputs go to both CTAs'
-// activation buffers (the partner's through distributed shared memory), one
-// cluster barrier per layer.  float32 activations and accumulation.
+// shared memory for the whole launch; layer 1 (K = 8) runs whole in both
+// CTAs, layer 2's outputs and layer 4's two halves go to both CTAs' buffers
+// (the partner's through distributed shared memory), one cluster barrier
+// each.  float32 activations and accumulation.
 //   TANGENT = false: lambda_{j+1} = G_j(lambda_j) = lambda_j + sd * MLP(lambda_j / sx, j / S)
 //                    (lambda_0 given), the learned composition;
 //   TANGENT = true:  e_0 = 0, e_{j+1} = J_j e_j + d_j, lambda_{j+1} += e_{j+1}, J_j the
@@ -156,6 +157,28 @@ __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, 
 constexpr int kTanThreads = 128;       // hidden units per CTA of the pair
 constexpr size_t kTanWeightBytes = 2 * sizeof(__nv_bfloat16) * (size_t)H * kTanThreads;
 
+// z[q] += sum_k W[k][t] act[q][k] (and dz[q] with dact) for k = 0 .. H-1 in
+// order: the weights as bf16 pairs (k, k + 1), the activations four k at a
+// time.
+template <int NS, bool TANGENT>
+__device__ __forceinline__ void sweep_layer(const __nv_bfloat162* Ws, const float* act, const float* dact, int t,
+                                            float (&z)[NS], float (&dz)[NS]) {
+#pragma unroll 2
+  for (int k = 0; k < H; k += 4) {
+    const float2 w01 = __bfloat1622float2(Ws[(k / 2) * kTanThreads + t]);
+    const float2 w23 = __bfloat1622float2(Ws[(k / 2 + 1) * kTanThreads + t]);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const float4 a = *reinterpret_cast<const float4*>(act + q * H + k);
+      z[q] = fmaf(w23.y, a.w, fmaf(w23.x, a.z, fmaf(w01.y, a.y, fmaf(w01.x, a.x, z[q]))));
+      if constexpr (TANGENT) {
+        const float4 b = *reinterpret_cast<const float4*>(dact + q * H + k);
+        dz[q] = fmaf(w23.y, b.w, fmaf(w23.x, b.z, fmaf(w01.y, b.y, fmaf(w01.x, b.x, dz[q]))));
+      }
+    }
+  }
+}
+
 template <int NS, bool TANGENT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
     learned_sweep_kernel(const float* P, const __nv_bfloat16* W2t, const __nv_bfloat16* W3t,
@@ -163,9 +186,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
                          const double* dfc) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char tan_smem[];
-  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(tan_smem);   // [k][unit of this CTA]
-  __nv_bfloat16* W3s = W2s + H * kTanThreads;
-  float* hA = reinterpret_cast<float*>(W3s + H * kTanThreads);       // [NS][H] each
+  // [k / 2][unit of this CTA]: the weights of k and k + 1 in one 32-bit word
+  __nv_bfloat162* W2s = reinterpret_cast<__nv_bfloat162*>(tan_smem);
+  __nv_bfloat162* W3s = W2s + (H / 2) * kTanThreads;
+  float* hA = reinterpret_cast<float*>(W3s + (H / 2) * kTanThreads);  // [NS][H] each
   float* hB = hA + NS * H;
   float* dA = hB + NS * H;                                           // tangents (TANGENT only)
   float* dB = dA + NS * H;
@@ -178,25 +202,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int u = kTanThreads * (int)rank + t;                           // this thread's hidden unit
   const int64_t s0 = (int64_t)(blockIdx.x >> 1) * NS;
-  float* hA_p = cl.map_shared_rank(hA, rank ^ 1u);
-  float* dA_p = cl.map_shared_rank(dA, rank ^ 1u);
   float* hB_p = cl.map_shared_rank(hB, rank ^ 1u);
   float* dB_p = cl.map_shared_rank(dB, rank ^ 1u);
   float* part_p = cl.map_shared_rank(&part[0][0][0], rank ^ 1u);
-  for (int i = t; i < H * kTanThreads; i += kTanThreads) {
-    const int k = i / kTanThreads, c = i - k * kTanThreads;
-    W2s[i] = W2t[k * H + kTanThreads * rank + c];
-    W3s[i] = W3t[k * H + kTanThreads * rank + c];
+  for (int i = t; i < (H / 2) * kTanThreads; i += kTanThreads) {
+    const int k2 = i / kTanThreads, c = i - k2 * kTanThreads;
+    const int64_t o = (int64_t)(2 * k2) * H + kTanThreads * rank + c;
+    W2s[i] = __halves2bfloat162(W2t[o], W2t[o + H]);
+    W3s[i] = __halves2bfloat162(W3t[o], W3t[o + H]);
   }
   // tangent mode: the correction e (from 0); forward mode: the state itself,
   // kept on chip from slice to slice (both CTAs hold it)
   if (t < NS * D) e[t / D][t % D] = TANGENT ? 0.0 : lam[(s0 + t / D) * D + t % D];
-  float w1[IN], w4[D];
+  // layer 1 is cheap (K = 8): each CTA computes all 256 units itself (thread t:
+  // units t and t + 128), so its activations need no exchange and no cluster
+  // barrier
+  float w1[2][IN], w4[D], b1[2];
 #pragma unroll
-  for (int k = 0; k < IN; ++k) w1[k] = P[oW1 + u * IN + k];
+  for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+    for (int k = 0; k < IN; ++k) w1[hh][k] = P[oW1 + (t + kTanThreads * hh) * IN + k];
+    b1[hh] = P[ob1 + t + kTanThreads * hh];
+  }
 #pragma unroll
   for (int c = 0; c < D; ++c) w4[c] = P[oW4 + c * H + u];
-  const float b1 = P[ob1 + u], b2 = P[ob2 + u], b3 = P[ob3 + u];
+  const float b2 = P[ob2 + u], b3 = P[ob3 + u];
   cl.sync();
   for (int j = 0; j < S; ++j) {
     const double* lj = lam + (size_t)j * count * D;
@@ -215,36 +245,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {             // layer 1
-      float z = b1;
+    for (int q = 0; q < NS; ++q) {             // layer 1, all units
 #pragma unroll
-      for (int k = 0; k < IN; ++k) z = fmaf(w1[k], xin[q][k], z);
-      float g;
-      const float h = gelu_with_grad(z, &g);
-      hA[q * H + u] = h;
-      hA_p[q * H + u] = h;
-      if constexpr (TANGENT) {
-        float dz = 0.f;
+      for (int hh = 0; hh < 2; ++hh) {
+        const int uu = t + kTanThreads * hh;
+        float z = b1[hh];
 #pragma unroll
-        for (int k = 0; k < D; ++k) dz = fmaf(w1[k], xtan[q][k], dz);
-        dA[q * H + u] = g * dz;
-        dA_p[q * H + u] = g * dz;
+        for (int k = 0; k < IN; ++k) z = fmaf(w1[hh][k], xin[q][k], z);
+        float g;
+        const float h = gelu_with_grad(z, &g);
+        hA[q * H + uu] = h;
+        if constexpr (TANGENT) {
+          float dz = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) dz = fmaf(w1[hh][k], xtan[q][k], dz);
+          dA[q * H + uu] = g * dz;
+        }
       }
     }
-    cl.sync();
+    __syncthreads();
     {                                          // layer 2
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < H; ++k) {
-        const float w = __bfloat162float(W2s[k * kTanThreads + t]);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          z[q] = fmaf(w, hA[q * H + k], z[q]);
-          if constexpr (TANGENT) dz[q] = fmaf(w, dA[q * H + k], dz[q]);
-        }
-      }
+      sweep_layer<NS, TANGENT>(W2s, hA, dA, t, z, dz);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         float g;
@@ -262,15 +286,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < H; ++k) {
-        const float w = __bfloat162float(W3s[k * kTanThreads + t]);
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-          z[q] = fmaf(w, hB[q * H + k], z[q]);
-          if constexpr (TANGENT) dz[q] = fmaf(w, dB[q * H + k], dz[q]);
-        }
-      }
+      sweep_layer<NS, TANGENT>(W3s, hB, dB, t, z, dz);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         float g;
