@@ -125,15 +125,15 @@ struct ChainNoHooks {
 
 // Banded maps (ChainsArgs::band > 0): the 16 rows r0 .. r0+15 of a CTA meet
 // nonzero entries only in columns r0-(band-1) .. r0+15+(band-1).  The CTA
-// reads columns r0-bw .. r0+15+bw, bw = band-1 rounded up to a multiple of 16,
-// so that each thread's columns (those congruent to its column group modulo
-// 16) keep their order and the products are the dense chain's, less terms that
-// are exactly zero.  chain_band_lo is bw, or 0 when that window is not
-// narrower than d (the CTA then reads all d columns); chain_band_cols the
-// columns read.
+// reads exactly those columns, r0-bw .. r0+15+bw with bw = band-1; each thread
+// takes the window's columns whose global index is congruent to its column
+// group modulo 16, in increasing order, so that the products are the dense
+// chain's, less terms that are exactly zero.  chain_band_lo is bw, or 0 when
+// that window is not narrower than d (the CTA then reads all d columns);
+// chain_band_cols the columns read.
 __host__ __device__ inline int chain_band_lo(int n, int band) {
   if (band <= 0) return 0;
-  const int bw = (band - 1 + 15) & ~15;
+  const int bw = band - 1;
   return kChainRpc + 2 * bw < n ? bw : 0;
 }
 __host__ __device__ inline int chain_band_cols(int n, int band) {
@@ -187,7 +187,7 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
   // so it receives the state rows of those CTAs only, and sends its own rows
   // to the same CTAs (the relation is symmetric, which keeps the ordering
   // argument of the state buffers below).  Dense: every CTA that owns rows.
-  const int hops = bw / rpc;
+  const int hops = (bw + rpc - 1) / rpc;
   const unsigned src_lo = bw > 0 ? (unsigned)max((int)rank - hops, 0) : 0u;
   const unsigned src_hi = bw > 0 ? min(rank + (unsigned)hops, owners - 1u) : owners - 1u;
   const uint32_t state_bytes = (uint32_t)((src_hi - src_lo + 1u) * rpc * sizeof(AT));
@@ -269,8 +269,10 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     rb1 = cluster_addr(cta_smem_u32(&xbar[1]), peer);
   }
 
-  // the window's columns inside 0 .. d-1 (those outside are the copy's zero fill)
+  // the window's columns inside 0 .. d-1 (those outside are the copy's zero
+  // fill); this thread's first one: global index congruent to its group mod 16
   const int cb = max(0, -col0), ce = min(wcols, n - col0);
+  const int cfirst = cb + ((cgi - col0 - cb) % ncg + ncg) % ncg;
   int consumed = len;
   for (int k = 0; has_rows && k < len; ++k) {
     const int j = j0 + k;
@@ -295,7 +297,7 @@ __device__ __forceinline__ void cluster_chain_run(const CUtensorMap* tmA, const 
     const MT* Aj = ring + st * stage_elems;
     AT acc = 0;
     if (active)
-      for (int c = cb + cgi; c < ce; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[col0 + c], acc);
+      for (int c = cfirst; c < ce; c += ncg) acc = fma((AT)Aj[c * rpc + r], x[col0 + c], acc);
     // lanes l and l ^ 16 hold the same row (rpc = 16)
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     AT* redk = red + (k & 1) * blockDim.x;
