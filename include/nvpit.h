@@ -526,8 +526,16 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          network at the iterate as the chain corrects it, every state's
  *          chain in one launch across all slices (float32).  All converge to
  *          the same float64 fine solution.
+ *   key 20: 0..1000 (default 0): the first `value` iterations of
+ *          nv_mlp_parareal compute their defects with float32 fine solves
+ *          (Kahan-compensated updates from the float32-rounded states), the
+ *          rest with float64 ones.  The float32 iterations converge towards
+ *          the float32 fine solution, about 1e-6 from the float64 one, at a
+ *          fraction of the float64 solves' cost; the float64 iterations then
+ *          continue to the float64 fine solution.  The leading boundary states
+ *          are exact only for the float64 iterations.
  * A value of 0 restores the default (and <= 0 for keys 0-2).  Returns NV_EINVAL for an unknown key
- * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18 and 19. */
+ * or an out-of-range value of keys 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19 and 20. */
 nv_status nv_tune_set(int32_t key, int32_t value);
 
 /* Measured fused multiply-add throughput of the current device's float64

@@ -486,6 +486,10 @@ extern "C" nv_status nv_tune_set(int32_t key, int32_t value) {
       if (value < 0 || value > 2) return nv_fail(NV_EINVAL, "learned correction form is 0, 1 or 2");
       g_tune.learned_correction_form = value;
       break;
+    case 20:
+      if (value < 0 || value > 1000) return nv_fail(NV_EINVAL, "float32 learned iterations are 0..1000");
+      g_tune.learned_f32_iters = value;
+      break;
     case 16:
       if (value != 0 && value != 8 && value != 16 && value != 32)
         return nv_fail(NV_EINVAL, "strip height is 0 (16), 8, 16 or 32");

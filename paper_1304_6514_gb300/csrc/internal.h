@@ -153,6 +153,7 @@ struct nv_tunables {
   int learned_first_form;    // iteration 0 of nv_mlp_parareal: 0 auto, 1 per-slice tcgen05 forward, 2 fused sweep
   int learned_correction_form;  // nv_mlp_parareal corrections: 0 Jacobians of the learned composition,
                                 // 1 tangent sweep, 2 Jacobians at each previous iterate
+  int learned_f32_iters;        // nv_mlp_parareal: leading iterations with float32 fine solves (0: none)
 };
 extern nv_tunables g_tune;
 

@@ -116,24 +116,27 @@ __global__ void propagate32_kernel(RhsParams pp, double h, int64_t m, int ns, in
   for (int c = 0; c < R::D; ++c) y[idx * R::D + c] = (double)s[c];
 }
 
-// ---- parareal with the learned map as the coarse propagator and float64
+// ---- the learned map as the coarse propagator of a residual correction with
 // fine integration F.  Fine pass: F_j = F(lam_j) for every slice j and state
 // at once (lam: (S+1) x count x D, F: S x count x D; the chain is autonomous,
 // so a slice's start time does not enter); it writes the defects
-// d_j = F_j - lam_{j+1}.
-template <class R>
+// d_j = F_j - lam_{j+1} in float64.  T = double: the float64 fine solve;
+// T = float: the same steps in float32 from the float32-rounded state
+// (Kahan-compensated updates), for the first, cheap iterations.
+template <class R, typename T>
 __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, int S, int64_t count,
                                     const double* lam, double* dfc) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)S * count) return;
   const R rhs(pp.p);
-  double s[R::D], comp[R::D];
-  for (int c = 0; c < R::D; ++c) { s[c] = lam[idx * R::D + c]; comp[c] = 0.0; }
+  T s[R::D], comp[R::D];
+  for (int c = 0; c < R::D; ++c) { s[c] = (T)lam[idx * R::D + c]; comp[c] = (T)0; }
+  const T ht = (T)h;
   for (int64_t i = 0; i < m; ++i) {
-    if (rk4) rk4_step(rhs, 0.0, 0.0, 0.0, h, s, comp);
-    else euler_step(rhs, 0.0, h, s, comp);
+    if (rk4) rk4_step(rhs, (T)0, (T)0, (T)0, ht, s, comp);
+    else euler_step(rhs, (T)0, ht, s, comp);
   }
-  for (int c = 0; c < R::D; ++c) dfc[idx * R::D + c] = s[c] - lam[(idx + count) * R::D + c];
+  for (int c = 0; c < R::D; ++c) dfc[idx * R::D + c] = (double)s[c] - lam[(idx + count) * R::D + c];
 }
 
 // The learned composition and the correction chain, every state's chain in
@@ -751,7 +754,7 @@ struct nv_mlp {
   int64_t pr_count, pr_chunk;
   int pr_S;
   cudaGraphExec_t pr_graph;
-  int pr_iters, pr_rk4, pr_form, pr_corr;
+  int pr_iters, pr_rk4, pr_form, pr_corr, pr_f32;
   int64_t pr_m;
   double pr_h, pr_p[3];
 };
@@ -1246,8 +1249,12 @@ static nv_status parareal_schedule(nv_mlp* m, const RhsParams& pp, int64_t mstep
   for (int k = 1; k <= iters && st == NV_OK; ++k) {
     // defects of the previous iterate, every slice and state at once
     const int64_t n = (int64_t)S * count;
-    slice_defect_kernel<RhsChain3<double>><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pp, h, msteps, rk4, S,
-                                                                                         count, lam, dfc);
+    if (k <= g_tune.learned_f32_iters)        // float32 fine solves for the first iterations
+      slice_defect_kernel<RhsChain3<float>, float><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+          pp, h, msteps, rk4, S, count, lam, dfc);
+    else
+      slice_defect_kernel<RhsChain3<double>, double><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+          pp, h, msteps, rk4, S, count, lam, dfc);
     if ((st = nv_cuda_check(cudaGetLastError(), "slice_defect_kernel launch")) != NV_OK) break;
     const int corr = g_tune.learned_correction_form;
     if (corr == 1) {
@@ -1310,8 +1317,9 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
   // one by one
   const int rk4 = steps->scheme == NV_RK4;
   const int form = g_tune.learned_first_form, corr = g_tune.learned_correction_form;
+  const int f32 = g_tune.learned_f32_iters;
   const bool same = m->pr_graph && m->pr_iters == iters && m->pr_rk4 == rk4 && m->pr_form == form &&
-                    m->pr_corr == corr &&
+                    m->pr_corr == corr && m->pr_f32 == f32 &&
                     m->pr_m == msteps &&
                     m->pr_h == h && m->pr_p[0] == pp.p[0] && m->pr_p[1] == pp.p[1] && m->pr_p[2] == pp.p[2];
   if (!same) {
@@ -1340,6 +1348,7 @@ extern "C" nv_status nv_mlp_parareal(nv_mlp* m, const nv_rhs* rhs, double t0, do
     m->pr_rk4 = rk4;
     m->pr_form = form;
     m->pr_corr = corr;
+    m->pr_f32 = f32;
     m->pr_m = msteps;
     m->pr_h = h;
     for (int i = 0; i < 3; ++i) m->pr_p[i] = pp.p[i];

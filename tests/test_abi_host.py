@@ -144,6 +144,9 @@ def test_null_handles(lib):
     assert lib.nv_tune_set(19, 3) == nvp.NV_EINVAL          # learned correction form is 0, 1 or 2
     assert lib.nv_tune_set(19, 1) == nvp.NV_OK
     assert lib.nv_tune_set(19, 0) == nvp.NV_OK
+    assert lib.nv_tune_set(20, -1) == nvp.NV_EINVAL         # float32 learned iterations are 0..1000
+    assert lib.nv_tune_set(20, 3) == nvp.NV_OK
+    assert lib.nv_tune_set(20, 0) == nvp.NV_OK
     assert lib.nv_alu_rate(0, None, None) == nvp.NV_EINVAL        # no output pointer
     rate = ctypes.c_double(0.0)
     assert lib.nv_alu_rate(3, ctypes.byref(rate), None) == nvp.NV_EINVAL   # float64 or float32 only

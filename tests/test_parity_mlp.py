@@ -408,3 +408,59 @@ def test_learned_correction_beats_float64_integration_of_few_states():
     t64 = _events_ms(torch, lambda: nvp.propagate(r, w.t0, w.T, S, st64, 0, S, y0.clone()))
     print(f"128 states at 1e-11: learned correction k={k_eq} {tp} ms, float64 fine {t64:.1f} ms")
     assert tp[0] < t64
+
+
+def test_learned_correction_with_float32_first_iterations():
+    """nv_tune_set key 20 = 3 on 1024 states: the first three iterations take
+    float32 fine solves (about a sixth of the float64 ones' cost) and converge
+    towards the float32 fine solution; the float64 iterations after them
+    reach the float64 fine solve's error (1e-11), each exact on one more
+    leading slice counted from the first float64 iteration.  Measured on a
+    GB300: 23.6 ms in 3 + 4 iterations against 36.8 ms with float64 solves
+    only and 80.9 ms for the plain float64 integration."""
+    torch = need_gpu()
+    t = _trained(torch)
+    w, r, net = t["w"], t["r"], t["net"]
+    S, count, f32 = w.S, 1024, 3
+    st64 = nvp.steps("rk4", w.dt)
+    Y0 = workloads.Stream(23).uniform(count * 6, -0.5, 0.5).reshape(count, 6)
+    y0 = torch.tensor(Y0, device="cuda")
+    fine = y0.clone()
+    nvp.propagate(r, w.t0, w.T, S, st64, 0, S, fine)
+    ref2 = y0.clone()
+    nvp.propagate(r, w.t0, w.T, S, st64, 0, 2, ref2)
+    torch.cuda.synchronize()
+    fine_h = fine.cpu().numpy()
+
+    def err(y):
+        return float(np.max(np.linalg.norm(y.cpu().numpy() - fine_h, axis=1) / np.linalg.norm(fine_h, axis=1)))
+
+    yT = torch.empty_like(y0)
+    lam = torch.empty((S + 1, count, 6), dtype=torch.float64, device="cuda")
+    k64 = None
+    for k in range(13):
+        net.parareal(r, w.t0, w.T, S, st64, k, y0, yT)
+        torch.cuda.synchronize()
+        if err(yT) <= 1e-11:
+            k64 = k
+            break
+    assert k64 is not None
+    nvp.tune_set(20, f32)
+    try:
+        km = None
+        for k in range(f32 + 1, 13):
+            net.parareal(r, w.t0, w.T, S, st64, k, y0, yT, lambdas=lam)
+            torch.cuda.synchronize()
+            if k == f32 + 2:                  # two float64 iterations: slices 1 and 2 exact
+                assert rel_max(lam[2].cpu().numpy(), ref2.cpu().numpy()) <= 1e-13
+            if err(yT) <= 1e-11:
+                km = k
+                break
+        assert km is not None and km <= f32 + 6, km
+        tm = _events_ms(torch, lambda: net.parareal(r, w.t0, w.T, S, st64, km, y0, yT))
+    finally:
+        nvp.tune_set(20, 0)
+    t64 = _events_ms(torch, lambda: net.parareal(r, w.t0, w.T, S, st64, k64, y0, yT))
+    print(f"1024 states at 1e-11: float64 defects only k={k64} {t64:.1f} ms, "
+          f"{f32} float32 iterations first k={km} {tm:.1f} ms")
+    assert tm < t64
