@@ -143,7 +143,8 @@ __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, 
 // one launch.  Both are sequential in the slices but independent from state
 // to state, so one launch carries all states through all S slices with no
 // grid-wide step.  A cluster of two CTAs takes NS states: CTA r owns hidden
-// units 128 r .. 128 r + 127 (thread t unit 128 r + t) and keeps its halves of
+// units 128 r .. 128 r + 127 (threads t and t + 128 share unit 128 r + t, one
+// half of each 256-deep sum each) and keeps its halves of
 // the bf16 layer-2 and layer-3 weights (W2^T and W3^T columns, 2 x 64 KB) in
 // shared memory for the whole launch; layer 1 (K = 8) runs whole in both
 // CTAs, layer 2's outputs and layer 4's two halves go to both CTAs' buffers
@@ -158,16 +159,17 @@ __global__ void slice_defect_kernel(RhsParams pp, double h, int64_t m, int rk4, 
 //                    only steers the correction, whose fixed point the float64
 //                    defects d_j set.
 constexpr int kTanThreads = 128;       // hidden units per CTA of the pair
+constexpr int kSweepThreads = 2 * kTanThreads;   // two threads per unit, each half of K
 constexpr size_t kTanWeightBytes = 2 * sizeof(__nv_bfloat16) * (size_t)H * kTanThreads;
 
-// z[q] += sum_k W[k][t] act[q][k] (and dz[q] with dact) for k = 0 .. H-1 in
-// order: the weights as bf16 pairs (k, k + 1), the activations four k at a
+// z[q] += sum_k W[k][t] act[q][k] (and dz[q] with dact) for k = k0 .. k0+H/2-1
+// in order: the weights as bf16 pairs (k, k + 1), the activations four k at a
 // time.
 template <int NS, bool TANGENT>
 __device__ __forceinline__ void sweep_layer(const __nv_bfloat162* Ws, const float* act, const float* dact, int t,
-                                            float (&z)[NS], float (&dz)[NS]) {
+                                            int k0, float (&z)[NS], float (&dz)[NS]) {
 #pragma unroll 2
-  for (int k = 0; k < H; k += 4) {
+  for (int k = k0; k < k0 + H / 2; k += 4) {
     const float2 w01 = __bfloat1622float2(Ws[(k / 2) * kTanThreads + t]);
     const float2 w23 = __bfloat1622float2(Ws[(k / 2 + 1) * kTanThreads + t]);
 #pragma unroll
@@ -182,8 +184,31 @@ __device__ __forceinline__ void sweep_layer(const __nv_bfloat162* Ws, const floa
   }
 }
 
+// The two K halves of a unit's sums: the upper half's threads leave theirs in
+// shared memory and the lower half's add them (every thread passes the
+// barrier; afterwards only khalf == 0 holds the full sums).
 template <int NS, bool TANGENT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
+__device__ __forceinline__ void sweep_halves(int khalf, int tt, float* zhi, float* dzhi, float (&z)[NS],
+                                             float (&dz)[NS]) {
+  if (khalf == 1) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      zhi[q * kTanThreads + tt] = z[q];
+      if constexpr (TANGENT) dzhi[q * kTanThreads + tt] = dz[q];
+    }
+  }
+  __syncthreads();
+  if (khalf == 0) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      z[q] += zhi[q * kTanThreads + tt];
+      if constexpr (TANGENT) dz[q] += dzhi[q * kTanThreads + tt];
+    }
+  }
+}
+
+template <int NS, bool TANGENT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kSweepThreads)
     learned_sweep_kernel(const float* P, const __nv_bfloat16* W2t, const __nv_bfloat16* W3t,
                          const float* sx_inv, const double* sd, int S, int64_t count, double* lam,
                          const double* dfc) {
@@ -196,6 +221,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   float* hB = hA + NS * H;
   float* dA = hB + NS * H;                                           // tangents (TANGENT only)
   float* dB = dA + NS * H;
+  // the upper K half's partial sums of layers 2 and 3, [NS][unit of this CTA]
+  float* zhi = hA + (TANGENT ? 4 : 2) * NS * H;
+  float* dzhi = zhi + NS * kTanThreads;
   __shared__ float xin[NS][IN], xtan[NS][D];
   __shared__ float red[NS][kTanThreads / 32][D];
   __shared__ float part[2][NS][D];           // the halves of W4 v by source CTA
@@ -203,12 +231,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int u = kTanThreads * (int)rank + t;                           // this thread's hidden unit
+  const int tt = t & (kTanThreads - 1), khalf = t / kTanThreads;       // unit in the CTA, K half
+  const int u = kTanThreads * (int)rank + tt;                          // this thread's hidden unit
   const int64_t s0 = (int64_t)(blockIdx.x >> 1) * NS;
   float* hB_p = cl.map_shared_rank(hB, rank ^ 1u);
   float* dB_p = cl.map_shared_rank(dB, rank ^ 1u);
   float* part_p = cl.map_shared_rank(&part[0][0][0], rank ^ 1u);
-  for (int i = t; i < (H / 2) * kTanThreads; i += kTanThreads) {
+  for (int i = t; i < (H / 2) * kTanThreads; i += kSweepThreads) {
     const int k2 = i / kTanThreads, c = i - k2 * kTanThreads;
     const int64_t o = (int64_t)(2 * k2) * H + kTanThreads * rank + c;
     W2s[i] = __halves2bfloat162(W2t[o], W2t[o + H]);
@@ -218,15 +247,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
   // kept on chip from slice to slice (both CTAs hold it)
   if (t < NS * D) e[t / D][t % D] = TANGENT ? 0.0 : lam[(s0 + t / D) * D + t % D];
   // layer 1 is cheap (K = 8): each CTA computes all 256 units itself (thread t:
-  // units t and t + 128), so its activations need no exchange and no cluster
-  // barrier
-  float w1[2][IN], w4[D], b1[2];
+  // unit t), so its activations need no exchange and no cluster barrier
+  float w1[IN], w4[D];
 #pragma unroll
-  for (int hh = 0; hh < 2; ++hh) {
-#pragma unroll
-    for (int k = 0; k < IN; ++k) w1[hh][k] = P[oW1 + (t + kTanThreads * hh) * IN + k];
-    b1[hh] = P[ob1 + t + kTanThreads * hh];
-  }
+  for (int k = 0; k < IN; ++k) w1[k] = P[oW1 + t * IN + k];
+  const float b1 = P[ob1 + t];
 #pragma unroll
   for (int c = 0; c < D; ++c) w4[c] = P[oW4 + c * H + u];
   const float b2 = P[ob2 + u], b3 = P[ob3 + u];
@@ -249,21 +274,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NS; ++q) {             // layer 1, all units
+      float z = b1;
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int uu = t + kTanThreads * hh;
-        float z = b1[hh];
+      for (int k = 0; k < IN; ++k) z = fmaf(w1[k], xin[q][k], z);
+      float g;
+      const float h = gelu_with_grad(z, &g);
+      hA[q * H + t] = h;
+      if constexpr (TANGENT) {
+        float dz = 0.f;
 #pragma unroll
-        for (int k = 0; k < IN; ++k) z = fmaf(w1[hh][k], xin[q][k], z);
-        float g;
-        const float h = gelu_with_grad(z, &g);
-        hA[q * H + uu] = h;
-        if constexpr (TANGENT) {
-          float dz = 0.f;
-#pragma unroll
-          for (int k = 0; k < D; ++k) dz = fmaf(w1[hh][k], xtan[q][k], dz);
-          dA[q * H + uu] = g * dz;
-        }
+        for (int k = 0; k < D; ++k) dz = fmaf(w1[k], xtan[q][k], dz);
+        dA[q * H + t] = g * dz;
       }
     }
     __syncthreads();
@@ -271,16 +292,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-      sweep_layer<NS, TANGENT>(W2s, hA, dA, t, z, dz);
+      sweep_layer<NS, TANGENT>(W2s, hA, dA, tt, khalf * (H / 2), z, dz);
+      sweep_halves<NS, TANGENT>(khalf, tt, zhi, dzhi, z, dz);
+      if (khalf == 0) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        float g;
-        const float h = gelu_with_grad(z[q] + b2, &g);
-        hB[q * H + u] = h;
-        hB_p[q * H + u] = h;
-        if constexpr (TANGENT) {
-          dB[q * H + u] = g * dz[q];
-          dB_p[q * H + u] = g * dz[q];
+        for (int q = 0; q < NS; ++q) {
+          float g;
+          const float h = gelu_with_grad(z[q] + b2, &g);
+          hB[q * H + u] = h;
+          hB_p[q * H + u] = h;
+          if constexpr (TANGENT) {
+            dB[q * H + u] = g * dz[q];
+            dB_p[q * H + u] = g * dz[q];
+          }
         }
       }
     }
@@ -289,18 +313,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTanThreads)
       float z[NS], dz[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) z[q] = dz[q] = 0.f;
-      sweep_layer<NS, TANGENT>(W3s, hB, dB, t, z, dz);
+      sweep_layer<NS, TANGENT>(W3s, hB, dB, tt, khalf * (H / 2), z, dz);
+      sweep_halves<NS, TANGENT>(khalf, tt, zhi, dzhi, z, dz);
+      if (khalf == 0) {                        // warps 0-3
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        float g;
-        const float h3 = gelu_with_grad(z[q] + b3, &g);
-        const float v = TANGENT ? g * dz[q] : h3;   // dh3 (tangent) or h3 (forward)
+        for (int q = 0; q < NS; ++q) {
+          float g;
+          const float h3 = gelu_with_grad(z[q] + b3, &g);
+          const float v = TANGENT ? g * dz[q] : h3;   // dh3 (tangent) or h3 (forward)
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float p = w4[c] * v;
+          for (int c = 0; c < D; ++c) {
+            float p = w4[c] * v;
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-          if (lane == 0) red[q][warp][c] = p;
+            for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+            if (lane == 0) red[q][warp][c] = p;
+          }
         }
       }
     }
@@ -341,12 +368,13 @@ template <int NS, bool TANGENT>
 static nv_status launch_learned_sweep(const float* P, const __nv_bfloat16* W2t, const __nv_bfloat16* W3t,
                                       const float* sx_inv, const double* sd, int S, int64_t count, double* lam,
                                       const double* dfc, cudaStream_t s) {
-  const size_t smem = kTanWeightBytes + (TANGENT ? 4 : 2) * sizeof(float) * (size_t)NS * H;
+  const size_t smem = kTanWeightBytes + (TANGENT ? 4 : 2) * sizeof(float) * (size_t)NS * H +
+                      (TANGENT ? 2 : 1) * sizeof(float) * (size_t)NS * kTanThreads;
   nv_status st = nv_cuda_check(cudaFuncSetAttribute(learned_sweep_kernel<NS, TANGENT>,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                "learned sweep shared memory attribute");
   if (st != NV_OK) return st;
-  learned_sweep_kernel<NS, TANGENT><<<(unsigned)(2 * (count / NS)), kTanThreads, smem, s>>>(
+  learned_sweep_kernel<NS, TANGENT><<<(unsigned)(2 * (count / NS)), kSweepThreads, smem, s>>>(
       P, W2t, W3t, sx_inv, sd, S, count, lam, dfc);
   return nv_cuda_check(cudaGetLastError(), "learned_sweep_kernel launch");
 }
