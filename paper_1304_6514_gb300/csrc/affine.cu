@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "heat.cuh"
@@ -1054,10 +1055,34 @@ static nv_status launch_heat_window(const HeatArgs& a, int block, cudaStream_t s
 }
 
 template <typename T, int R>
+static nv_status launch_heat_forcing(const HeatArgs& a, int block, cudaStream_t s);
+template <typename T, int R>
+static nv_status launch_heat_homogeneous(const HeatArgs& a, int block, cudaStream_t s, bool tf32out,
+                                         BuildInfo* bi);
+
+// A library-owned non-blocking stream per device for work that runs beside a
+// build on the caller's stream (created on first use, kept for the process;
+// not valid after a cudaDeviceReset of that device).
+static nv_status heat_side_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  nv_status st = nv_cuda_check(cudaGetDevice(&dev), "current device");
+  if (st != NV_OK) return st;
+  if (dev < 0 || dev >= 64) return nv_fail(NV_ENOTSUP, "device index %d too large", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev]) {
+    st = nv_cuda_check(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking), "side stream");
+    if (st != NV_OK) return st;
+  }
+  *out = streams[dev];
+  return NV_OK;
+}
+
+template <typename T, int R>
 static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out, BuildInfo* bi) {
   const int warps_per_cta = g_tune.affine_warps > 0 ? g_tune.affine_warps : 8;
   const int block = 32 * warps_per_cta;
-  const int t32 = tf32out ? 1 : 0;
   int grid = 0;
   nv_status st;
   if (a.varcoef) {
@@ -1067,18 +1092,49 @@ static nv_status launch_heat_R(const HeatArgs& a, cudaStream_t s, bool tf32out, 
     heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 1);
     return nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   }
-  if constexpr (sizeof(T) == 8) {              // the forcing columns
+  // The forcing columns (one forced solve per slice, latency-bound) run on a
+  // second stream beside the homogeneous build, submitted after it so that
+  // they take the SMs its last CTAs leave free.
+  cudaStream_t side = nullptr;
+  if ((st = heat_side_stream(&side)) != NV_OK) return st;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  st = nv_cuda_check(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "fork event");
+  if (st == NV_OK) st = nv_cuda_check(cudaEventCreateWithFlags(&join, cudaEventDisableTiming), "join event");
+  if (st == NV_OK) st = nv_cuda_check(cudaEventRecord(fork, s), "fork record");
+  if (st == NV_OK) st = launch_heat_homogeneous<T, R>(a, block, s, tf32out, bi);
+  if (st == NV_OK) st = nv_cuda_check(cudaStreamWaitEvent(side, fork, 0), "fork wait");
+  if (st == NV_OK) st = launch_heat_forcing<T, R>(a, block, side);
+  if (st == NV_OK) st = nv_cuda_check(cudaEventRecord(join, side), "join record");
+  if (st == NV_OK) st = nv_cuda_check(cudaStreamWaitEvent(s, join, 0), "join wait");
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  return st;
+}
+
+template <typename T, int R>
+static nv_status launch_heat_forcing(const HeatArgs& a, int block, cudaStream_t s) {
+  int grid = 0;
+  nv_status st;
+  if constexpr (sizeof(T) == 8) {
     st = persistent_grid(heat_forcing_kernel<R>, block, (int64_t)a.S, &grid);
     if (st != NV_OK) return st;
     heat_forcing_kernel<R><<<grid, block, 0, s>>>(a);
-    st = nv_cuda_check(cudaGetLastError(), "heat_forcing_kernel launch");
+    return nv_cuda_check(cudaGetLastError(), "heat_forcing_kernel launch");
   } else {
     st = persistent_grid(heat_literal_kernel<T, R>, block, (int64_t)a.S, &grid);
     if (st != NV_OK) return st;
     heat_literal_kernel<T, R><<<grid, block, 0, s>>>(a, 0);
-    st = nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
+    return nv_cuda_check(cudaGetLastError(), "heat_literal_kernel launch");
   }
-  if (st != NV_OK) return st;
+}
+
+// The homogeneous columns of a time-independent heat operator.
+template <typename T, int R>
+static nv_status launch_heat_homogeneous(const HeatArgs& a, int block, cudaStream_t s, bool tf32out,
+                                         BuildInfo* bi) {
+  const int t32 = tf32out ? 1 : 0;
+  int grid = 0;
+  nv_status st;
   const int form = g_tune.heat_step_form;
   if (form == 0 || form >= 3) {
     st = launch_heat_window<T>(a, block, s, tf32out, form, bi);
