@@ -169,6 +169,10 @@ typedef struct {
  * If *maps is non-NULL it must come from an earlier call with the same sizes,
  * map kind and precision; its storage is reused and nothing is allocated.
  * Otherwise a new object is allocated and returned in *maps.
+ * All work is ordered on `stream`.  The heat equations' forcing columns run
+ * on a library-owned second stream of the device, forked from and joined back
+ * to `stream` by events; that stream is created on first use and kept, so it
+ * is not valid after a cudaDeviceReset of the device.
  * Returns NV_EINVAL for inconsistent arguments (nothing launched), NV_ENOMEM,
  * NV_ENOTSUP for map/rhs combinations not built, NV_ECUDA on launch failure. */
 nv_status nv_build_propagators(const nv_rhs* rhs, double t0, double T, int32_t S,
