@@ -33,34 +33,39 @@ struct WaveArgs {
   double h2;          // h^2
 };
 
-// D (Gauss-Lobatto differentiation, (M+1)^2) into scratch, then the interior
-// block of D D transposed and zero-padded into d2t.  One CTA.
-__global__ void wave_operator_kernel(int M, int DP, double* D, double* d2t) {
-  const int N = M + 1;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx - i * N;
-    if (i == j) continue;
-    const double xi = cos((double)i * M_PI / (double)M), xj = cos((double)j * M_PI / (double)M);
-    const double ci = (i == 0 || i == M) ? 2.0 : 1.0, cj = (j == 0 || j == M) ? 2.0 : 1.0;
+// D (Gauss-Lobatto differentiation, (M+1)^2) into scratch, one CTA per row:
+// the off-diagonal entries, then the diagonal as minus the row's sum.
+__global__ void wave_dmat_kernel(int M, double* D) {
+  const int N = M + 1, i = blockIdx.x;
+  __shared__ double xs[kWaveMaxDP + 3];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) xs[q] = cos((double)q * M_PI / (double)M);
+  __syncthreads();
+  const double ci = (i == 0 || i == M) ? 2.0 : 1.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    if (j == i) continue;
+    const double cj = (j == 0 || j == M) ? 2.0 : 1.0;
     const double sign = ((i + j) & 1) ? -1.0 : 1.0;
-    D[idx] = (ci / cj) * sign / (xi - xj);
+    D[i * N + j] = (ci / cj) * sign / (xs[i] - xs[j]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {   // rows sum to zero
+  if (threadIdx.x == 0) {                               // rows sum to zero
     double s = 0.0;
     for (int j = 0; j < N; ++j)
       if (j != i) s += D[i * N + j];
     D[i * N + i] = -s;
   }
-  __syncthreads();
-  const int d = M - 1;
-  for (int idx = threadIdx.x; idx < DP * DP; idx += blockDim.x) {
-    const int k = idx / DP, i = idx - k * DP;
+}
+
+// The interior block of D D, transposed and zero-padded into d2t (DP x DP),
+// one CTA per row k of d2t.
+__global__ void wave_d2_kernel(int M, int DP, const double* D, double* d2t) {
+  const int N = M + 1, d = M - 1, k = blockIdx.x;
+  for (int i = threadIdx.x; i < DP; i += blockDim.x) {
     double v = 0.0;
     if (i < d && k < d) {
       for (int l = 0; l < N; ++l) v = fma(D[(i + 1) * N + l], D[l * N + (k + 1)], v);
     }
-    d2t[idx] = v;
+    d2t[k * DP + i] = v;
   }
 }
 
@@ -274,8 +279,11 @@ int64_t wave_aux_elems(int d) {
 
 static nv_status wave_operator(int d, double* aux, cudaStream_t s) {
   const int M = d + 1, DP = wave_dp(d);
-  wave_operator_kernel<<<1, 256, 0, s>>>(M, DP, aux, aux + (int64_t)(M + 1) * (M + 1));
-  return nv_cuda_check(cudaGetLastError(), "wave_operator_kernel launch");
+  wave_dmat_kernel<<<M + 1, 128, 0, s>>>(M, aux);
+  nv_status st = nv_cuda_check(cudaGetLastError(), "wave_dmat_kernel launch");
+  if (st != NV_OK) return st;
+  wave_d2_kernel<<<DP, 128, 0, s>>>(M, DP, aux, aux + (int64_t)(M + 1) * (M + 1));
+  return nv_cuda_check(cudaGetLastError(), "wave_d2_kernel launch");
 }
 
 nv_status launch_wave_build(const nv_maps* M, cudaStream_t s) {
