@@ -365,7 +365,7 @@ nv_status nv_mlp_compose(nv_mlp* mlp, const nv_rhs* rhs, double t0, double T, in
  * (the combination with parareal the Conclusion proposes), for nonlinear
  * problems.  Iteration 0 is the learned composition
  * lambda_{j+1} = G_j(lambda_j), G_j(y) = y + sd*MLP(y/sx, j/S): by default,
- * while count <= 16 x (SMs / 2), every state's chain in one launch with
+ * while count <= 32 x (SMs / 2), every state's chain in one launch with
  * float32 activations (the network's bf16 weights), else, or with
  * nv_tune_set key 18 = 1, slice by slice through nv_mlp_compose's path
  * (bf16 activations between the layers), then bit for bit its states.  Iteration k >= 1:
@@ -515,7 +515,7 @@ nv_status nv_compose_affine_noalloc(const void* maps_dev, int32_t prec, int32_t 
  *          register, every stencil operation one packed f32x2 instruction for
  *          both (S > 1); 0 (default) = 4.  The same maps bit for bit.
  *   key 18: 0 (default), 1 or 2: iteration 0 of nv_mlp_parareal: 0 the
- *          fused one-launch sweep while count <= 16 x (SMs / 2), else the
+ *          fused one-launch sweep while count <= 32 x (SMs / 2), else the
  *          per-slice path of nv_mlp_compose; 1 always that per-slice path;
  *          2 always the sweep.  The two differ in the rounding of the
  *          network's activations (bf16 between layers on the per-slice path,
